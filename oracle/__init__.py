@@ -1,0 +1,221 @@
+"""CPU oracle for Voronoi-grid straight-path traversal.
+
+TEST INFRASTRUCTURE. Plain FP64 code written from the paper (Camps, Baes &
+Saftly 2013, Sect. 2). Only the tests, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the GPU library never does.
+
+The arithmetic lives in ``voronoi_oracle.c`` (compiled with contraction off so
+results do not depend on the host's FMA support); this module only marshals
+numpy arrays and adds the plain numpy parts:
+
+* ``cells``    Voronoi cells by bisector clipping (Sect. 2.1, 2.3): neighbour
+               lists with walls as -1..-6, volumes, bounding boxes.
+* ``locate``   C(r) by brute-force nearest site (Sect. 2.3).
+* ``trace``    the straight-path loop of Sect. 2.2 (Eq. 1-5).
+* ``tau_grad`` gradient of a loss of tau with respect to cell densities:
+               tau_r = sum_c kappa rho_c l_rc is linear in rho, so
+               d tau_r / d rho_c = kappa l_rc (the segment bookkeeping of
+               Sect. 2.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "voronoi_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+WALL_IDS = (-1, -2, -3, -4, -5, -6)   # x=xmin, x=xmax, y=ymin, y=ymax, z=zmin, z=zmax
+TIE_REL = 1e-9                        # near-tie threshold on the decision margin
+STATUS = {0: "ok", 1: "outside", 2: "step_limit", 3: "capacity"}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C source with gcc (no contraction, -O2, pthreads)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-pthread", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        lib.oracle_cells.argtypes = [P, i64, P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, P, P, P, P, P, P, ctypes.c_int]
+        lib.oracle_cells.restype = ctypes.c_int
+        lib.oracle_locate.argtypes = [P, i64, P, P, i64, P, ctypes.c_int]
+        lib.oracle_locate.restype = None
+        lib.oracle_trace.argtypes = [P, i64, P, P, P, P, ctypes.c_double, P, P, i64, i64, P, P, P, P, P, P,
+                                     P, P, P, i64, ctypes.c_double, ctypes.c_int]
+        lib.oracle_trace.restype = None
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _threads(n):
+    if n is not None:
+        return int(n)
+    return int(os.environ.get("ORACLE_THREADS", "0"))
+
+
+def _f64c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def default_eps(box) -> float:
+    box = np.asarray(box, dtype=np.float64)
+    return 1e-12 * float(np.linalg.norm(box[3:] - box[:3]))
+
+
+@dataclasses.dataclass
+class Cells:
+    ids: np.ndarray       # (n,) site indices
+    nbr: list             # list of int32 arrays (ascending ids, walls negative)
+    area: list            # matching face areas
+    vol: np.ndarray       # (n,) volumes
+    bbox: np.ndarray      # (n, 6) xmin, ymin, zmin, xmax, ymax, zmax
+
+
+def cells(sites, box, ids=None, brute=False, maxdeg=256, eps=None, area_tol=None, threads=None) -> Cells:
+    """Voronoi cells of ``ids`` (default: all sites) clipped by the box."""
+    lib = _load()
+    S = _f64c(sites)
+    box = _f64c(box)
+    M = S.shape[0]
+    ids = np.arange(M, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    n = ids.size
+    eps = default_eps(box) if eps is None else float(eps)
+    diag = float(np.linalg.norm(box[3:] - box[:3]))
+    area_tol = (1e-20 * diag * diag) if area_tol is None else float(area_tol)
+    nbr = np.zeros((n, maxdeg), np.int32)
+    deg = np.zeros(n, np.int32)
+    area = np.zeros((n, maxdeg), np.float64)
+    vol = np.zeros(n, np.float64)
+    bbox = np.zeros((n, 6), np.float64)
+    err = np.zeros(n, np.int32)
+    rc = lib.oracle_cells(_p(S), M, _p(box), _p(ids), n, int(bool(brute)), maxdeg, eps, area_tol, _p(nbr),
+                          _p(deg), _p(area), _p(vol), _p(bbox), _p(err), _threads(threads))
+    if rc != 0:
+        bad = np.nonzero(err)[0]
+        raise RuntimeError(f"oracle_cells failed for {bad.size} cells (first {ids[bad[:5]]}, codes {err[bad[:5]]})")
+    return Cells(ids, [nbr[i, :deg[i]].copy() for i in range(n)], [area[i, :deg[i]].copy() for i in range(n)],
+                 vol, bbox)
+
+
+def csr(c: Cells, M: int):
+    """CSR (off int64[M+1], idx int32) from cells computed for all M sites."""
+    assert c.ids.size == M and np.array_equal(c.ids, np.arange(M))
+    deg = np.array([a.size for a in c.nbr], np.int64)
+    off = np.zeros(M + 1, np.int64)
+    np.cumsum(deg, out=off[1:])
+    idx = np.concatenate(c.nbr).astype(np.int32) if M else np.zeros(0, np.int32)
+    return off, idx
+
+
+def locate(sites, box, pts, threads=None) -> np.ndarray:
+    """Nearest site per point (lowest index on exact ties); -1 outside the box."""
+    lib = _load()
+    S = _f64c(sites)
+    box = _f64c(box)
+    P = _f64c(pts).reshape(-1, 3)
+    out = np.empty(P.shape[0], np.int64)
+    lib.oracle_locate(_p(S), S.shape[0], _p(box), _p(P), P.shape[0], _p(out), _threads(threads))
+    return out
+
+
+@dataclasses.dataclass
+class Trace:
+    nseg: np.ndarray
+    seg_cell: np.ndarray      # (N, cap) int32
+    seg_len: np.ndarray       # (N, cap) float64
+    tau: np.ndarray
+    length: np.ndarray
+    min_margin: np.ndarray
+    near_tie: np.ndarray
+    nfallback: np.ndarray
+    status: np.ndarray
+
+    def segments(self, i):
+        n = int(self.nseg[i])
+        return self.seg_cell[i, :n], self.seg_len[i, :n]
+
+
+def trace(sites, box, rho, origin, direction, off=None, idx=None, kappa=1.0, cap=1024, max_steps=1_000_000,
+          tie_rel=TIE_REL, threads=None) -> Trace:
+    """Trace rays with the paper's loop. With off/idx None every site and all
+    walls are candidates (the plain definition of the exit)."""
+    lib = _load()
+    S = _f64c(sites)
+    box = _f64c(box)
+    rho = _f64c(rho)
+    O = _f64c(origin).reshape(-1, 3)
+    D = _f64c(direction).reshape(-1, 3)
+    N = O.shape[0]
+    if off is not None:
+        off = np.ascontiguousarray(off, np.int64)
+        idx = np.ascontiguousarray(idx, np.int32)
+    cap = int(cap)
+    seg_cell = np.zeros((N, max(cap, 1)), np.int32)
+    seg_len = np.zeros((N, max(cap, 1)), np.float64)
+    out = {k: np.zeros(N, t) for k, t in [("nseg", np.int32), ("tau", np.float64), ("length", np.float64),
+                                         ("min_margin", np.float64), ("near_tie", np.int32),
+                                         ("nfallback", np.int32), ("status", np.int32)]}
+    lib.oracle_trace(_p(S), S.shape[0], _p(box), _p(off), _p(idx), _p(rho), float(kappa), _p(O), _p(D), N, cap,
+                     _p(seg_cell), _p(seg_len), _p(out["nseg"]), _p(out["tau"]), _p(out["length"]),
+                     _p(out["min_margin"]), _p(out["near_tie"]), _p(out["nfallback"]), _p(out["status"]),
+                     int(max_steps), float(tie_rel), _threads(threads))
+    return Trace(out["nseg"], seg_cell, seg_len, out["tau"], out["length"], out["min_margin"], out["near_tie"],
+                 out["nfallback"], out["status"])
+
+
+def tau_grad(tr: Trace, M: int, dL_dtau, kappa=1.0) -> np.ndarray:
+    """dL/drho_c = sum_r dL/dtau_r * kappa * l_rc, summed in FP64."""
+    dL = np.asarray(dL_dtau, np.float64)
+    N = tr.nseg.size
+    cap = tr.seg_cell.shape[1]
+    mask = np.arange(cap)[None, :] < tr.nseg[:, None]
+    cells_ = tr.seg_cell[mask]
+    w = (dL[:, None] * kappa * tr.seg_len)[mask]
+    assert cells_.size == int(tr.nseg.sum()), "segment capacity exceeded"
+    return np.bincount(cells_, weights=w, minlength=M)[:M] if N else np.zeros(M)
+
+
+def exp_loss(tau, target):
+    """Loss sum_r (exp(-tau_r) - target_r)^2 and dL/dtau_r."""
+    e = np.exp(-np.asarray(tau, np.float64))
+    t = np.asarray(target, np.float64)
+    return float(np.sum((e - t) ** 2)), -2.0 * (e - t) * e
+
+
+def in_domain_length(box, origin, direction) -> np.ndarray:
+    """Distance from each origin to the box boundary along its direction
+    (the smallest positive wall parameter of Eq. 5 over the three axes)."""
+    box = np.asarray(box, np.float64)
+    O = np.asarray(origin, np.float64).reshape(-1, 3)
+    D = np.asarray(direction, np.float64).reshape(-1, 3)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tmax = np.where(D > 0, (box[3:] - O) / D, np.where(D < 0, (box[:3] - O) / D, np.inf))
+    return tmax.min(axis=1)

@@ -1,0 +1,381 @@
+"""Pins of the CPU oracle against facts other than itself.
+
+Each test checks the oracle against a hand-worked example, a textbook or
+library routine, a closed form, an invariant or brute force, chosen so that a
+dropped term, a sign error, a wrong index or a transposed operand in the
+oracle fails at least one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests.helpers import dda_voxels, nearest_site, slab_length
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _full(sites, box):
+    c = oracle.cells(sites, box)
+    off, idx = oracle.csr(c, len(sites))
+    return c, off, idx
+
+
+# --------------------------------------------------------------------------
+# hand-worked examples (Sect. 2.2, Eq. 1-5)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _load("worked_examples.json")["cases"], ids=lambda c: c["name"])
+@pytest.mark.parametrize("mode", ["neighbours", "all_sites"])
+def test_worked_examples(case, mode):
+    S = np.array(case["sites"], np.float64)
+    box = np.array(case["box"], np.float64)
+    rho = np.array(case["rho"], np.float64)
+    O = np.array([case["origin"]], np.float64)
+    D = np.array([case["dir"]], np.float64)
+    kw = {}
+    if mode == "neighbours":
+        _, off, idx = _full(S, box)
+        kw = dict(off=off, idx=idx)
+    tr = oracle.trace(S, box, rho, O, D, kappa=case["kappa"], **kw)
+    cells, lens = tr.segments(0)
+    exp = case["segments"]
+    assert [int(c) for c in cells] == [e[0] for e in exp]
+    np.testing.assert_allclose(lens, [e[1] for e in exp], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr.tau[0], case["tau"], rtol=1e-12)
+    assert oracle.STATUS[int(tr.status[0])] == case.get("status", "ok")
+
+
+# --------------------------------------------------------------------------
+# cells: lattices with known cells, Delaunay adjacency, Monte Carlo volumes
+# --------------------------------------------------------------------------
+
+def test_cubic_lattice_cells_are_cubes():
+    n = 4  # spacing 0.5: the lattice is exact in float32
+    S = gen.cubic_lattice(n)
+    c = oracle.cells(S, gen.CUBE_BOX)
+    h = 2.0 / n
+    np.testing.assert_allclose(c.vol, h ** 3, rtol=1e-12)
+    idx = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    for m, (i, j, k) in enumerate(idx):
+        exp = set()
+        for a, (v, lo_wall, hi_wall) in enumerate([(i, -1, -2), (j, -3, -4), (k, -5, -6)]):
+            for dv, wall in ((-1, lo_wall), (1, hi_wall)):
+                w = v + dv
+                if 0 <= w < n:
+                    q = [i, j, k]
+                    q[a] = w
+                    exp.add(q[0] * n * n + q[1] * n + q[2])
+                else:
+                    exp.add(wall)
+        assert set(c.nbr[m].tolist()) == exp, m
+        np.testing.assert_allclose(c.bbox[m, :3], S[m] - h / 2, atol=1e-12)
+        np.testing.assert_allclose(c.bbox[m, 3:], S[m] + h / 2, atol=1e-12)
+
+
+def test_bcc_interior_cells_are_truncated_octahedra():
+    n = 8  # spacing 0.25: exact in float32
+    S = gen.bcc_lattice(n)
+    c = oracle.cells(S, gen.CUBE_BOX)
+    h = 2.0 / n
+    # points whose 14 lattice neighbours all exist (the lattice stops at the walls)
+    interior = np.all(np.abs(S) < 1 - 1.2 * h, axis=1)
+    assert interior.sum() > 10
+    deg = np.array([a.size for a in c.nbr])
+    assert np.all(deg[interior] == 14)
+    # two lattice points per cube of side h
+    np.testing.assert_allclose(c.vol[interior], h ** 3 / 2, rtol=1e-12)
+    # 8 hexagonal faces of area (3*sqrt(3)/2) a^2 and 6 squares of area a^2, a = h / (2 sqrt 2)
+    a = h / (2 * np.sqrt(2))
+    for m in np.nonzero(interior)[0][:5]:
+        ar = np.sort(c.area[m])
+        np.testing.assert_allclose(ar[:6], a * a, rtol=1e-10)
+        np.testing.assert_allclose(ar[6:], 1.5 * np.sqrt(3) * a * a, rtol=1e-10)
+    np.testing.assert_allclose(c.vol.sum(), 8.0, rtol=1e-12)
+
+
+@pytest.fixture(scope="module")
+def grid300():
+    g = gen.make_uniform_grid(300, 11)
+    c, off, idx = _full(g.sites, g.box)
+    return g, c, off, idx
+
+
+def test_symmetry_volume_and_bbox(grid300):
+    g, c, off, idx = grid300
+    M = len(g.sites)
+    pairs = {(m, int(j)) for m in range(M) for j in c.nbr[m] if j >= 0}
+    assert all((j, m) in pairs for (m, j) in pairs)
+    np.testing.assert_allclose(c.vol.sum(), 8.0, rtol=1e-12)
+    assert np.all(c.bbox[:, :3] <= g.sites + 1e-15) and np.all(c.bbox[:, 3:] >= g.sites - 1e-15)
+    assert np.all(c.bbox[:, :3] >= g.box[:3] - 1e-12) and np.all(c.bbox[:, 3:] <= g.box[3:] + 1e-12)
+
+
+def test_security_radius_equals_brute_force(grid300):
+    g, c, off, idx = grid300
+    b = oracle.cells(g.sites, g.box, brute=True)
+    for m in range(len(g.sites)):
+        assert np.array_equal(b.nbr[m], c.nbr[m])
+    np.testing.assert_allclose(b.vol, c.vol, rtol=1e-11)
+
+
+def test_neighbours_are_delaunay_edges(grid300):
+    spatial = pytest.importorskip("scipy.spatial")
+    g, c, off, idx = grid300
+    tri = spatial.Delaunay(g.sites)
+    edges = set()
+    for s in tri.simplices:
+        for a in range(4):
+            for b in range(a + 1, 4):
+                edges.add((min(s[a], s[b]), max(s[a], s[b])))
+    ours = {(min(m, int(j)), max(m, int(j))) for m in range(len(g.sites)) for j in c.nbr[m] if j >= 0}
+    assert ours <= edges
+    # cells far from the walls keep every Delaunay edge (their faces are not clipped)
+    far = np.nonzero(np.all(np.abs(g.sites) < 0.5, axis=1) & np.all(np.abs(c.bbox) < 0.95, axis=1))[0]
+    assert far.size > 5
+    for m in far:
+        dl = {b if a == m else a for (a, b) in edges if m in (a, b)}
+        assert dl == set(c.nbr[m].tolist())
+
+
+def test_volumes_match_monte_carlo(grid300):
+    g, c, off, idx = grid300
+    rng = gen.rng_for(77)
+    P = gen.uniform_points(200_000, rng)
+    owner = nearest_site(g.sites, P)
+    frac = np.bincount(owner, minlength=len(g.sites)) / P.shape[0]
+    est = frac * 8.0
+    # aggregate check over random groups of 30 cells (binomial error ~ 1.5 %)
+    perm = rng.permutation(len(g.sites))[:300].reshape(10, 30)
+    for grp in perm:
+        v = c.vol[grp].sum()
+        sd = np.sqrt(v / 8 * (1 - v / 8) / P.shape[0]) * 8
+        assert abs(est[grp].sum() - v) < 5 * sd
+
+
+def test_mean_degree_uniform_interior():
+    """Sect. 2.1: mean neighbour count 15.54 for uniform random sites."""
+    const = _load("paper_constants.json")["mean_neighbour_count_uniform"]["value"]
+    g = gen.make_uniform_grid(40_000, 12)
+    ids = np.nonzero(np.all(np.abs(g.sites) < 0.6, axis=1))[0][:3000]
+    c = oracle.cells(g.sites, g.box, ids=ids)
+    deg = np.array([a.size for a in c.nbr])
+    assert not np.any(np.concatenate(c.nbr) < 0)
+    se = deg.std() / np.sqrt(deg.size)
+    assert abs(deg.mean() - const) < 4 * se + 0.02, (deg.mean(), se)
+
+
+# --------------------------------------------------------------------------
+# locate
+# --------------------------------------------------------------------------
+
+def test_locate_matches_numpy_and_lattice():
+    g = gen.make_uniform_grid(500, 13)
+    rng = gen.rng_for(5)
+    P = gen.uniform_points(3000, rng)
+    np.testing.assert_array_equal(oracle.locate(g.sites, g.box, P), nearest_site(g.sites, P))
+    out = np.array([[1.5, 0, 0], [0, -1.0001, 0], [0, 0, 2]])
+    assert np.all(oracle.locate(g.sites, g.box, out) == -1)
+    # boundary points are inside (closed box)
+    assert oracle.locate(g.sites, g.box, np.array([[1.0, 1.0, -1.0]]))[0] >= 0
+    n = 4
+    S = gen.cubic_lattice(n)
+    P = gen.uniform_points(2000, rng)
+    v = np.minimum(np.floor((P + 1) / 0.5).astype(int), n - 1)
+    np.testing.assert_array_equal(oracle.locate(S, gen.CUBE_BOX, P), v[:, 0] * 16 + v[:, 1] * 4 + v[:, 2])
+
+
+# --------------------------------------------------------------------------
+# trace
+# --------------------------------------------------------------------------
+
+def test_cubic_lattice_trace_is_dda():
+    n = 8  # spacing 0.25: the lattice is exact in float32
+    S = gen.cubic_lattice(n)
+    box = gen.CUBE_BOX
+    c, off, idx = _full(S, box)
+    rays = gen.uniform_rays(200, 99)
+    rho = np.ones(len(S))
+    tr = oracle.trace(S, box, rho, rays.origin, rays.dir, off=off, idx=idx)
+    for i in range(200):
+        ref = dda_voxels(box, n, rays.origin[i], rays.dir[i])
+        cells, lens = tr.segments(i)
+        assert [int(c_) for c_ in cells] == [v[0] * n * n + v[1] * n + v[2] for v, _ in ref]
+        np.testing.assert_allclose(lens, [l for _, l in ref], rtol=1e-11, atol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def traced300(grid300):
+    g, c, off, idx = grid300
+    rays = gen.uniform_rays(2000, 21)
+    tr = oracle.trace(g.sites, g.box, g.rho, rays.origin, rays.dir, off=off, idx=idx)
+    return g, c, off, idx, rays, tr
+
+
+def test_lengths_sum_to_slab_length(traced300):
+    g, c, off, idx, rays, tr = traced300
+    L = slab_length(g.box, rays.origin, rays.dir)
+    assert np.all(tr.status == 0)
+    np.testing.assert_allclose(tr.length, L, rtol=1e-13, atol=1e-15)
+
+
+def test_segments_lie_in_their_cells(traced300):
+    """Midpoint of each segment is nearest to its cell's site; each exit point
+    is equidistant from the two sites it separates (bisector property)."""
+    g, c, off, idx, rays, tr = traced300
+    S = g.sites
+    diag = np.linalg.norm(g.box[3:] - g.box[:3])
+    mids, owners, exits, pairs = [], [], [], []
+    for i in range(300):
+        cells, lens = tr.segments(i)
+        t = np.concatenate([[0.0], np.cumsum(lens)])
+        for a in range(cells.size):
+            mids.append(rays.origin[i] + 0.5 * (t[a] + t[a + 1]) * rays.dir[i])
+            owners.append(cells[a])
+            if a + 1 < cells.size:
+                exits.append(rays.origin[i] + t[a + 1] * rays.dir[i])
+                pairs.append((cells[a], cells[a + 1]))
+    np.testing.assert_array_equal(nearest_site(S, np.array(mids)), np.array(owners))
+    q = np.array(exits)
+    pr = np.array(pairs)
+    d1 = np.linalg.norm(q - S[pr[:, 0]], axis=1)
+    d2 = np.linalg.norm(q - S[pr[:, 1]], axis=1)
+    assert np.max(np.abs(d1 - d2)) <= 1e-12 * diag
+
+
+def test_dense_sampling_reproduces_cell_sequence():
+    g = gen.make_uniform_grid(150, 31)
+    c, off, idx = _full(g.sites, g.box)
+    rays = gen.uniform_rays(60, 32)
+    tr = oracle.trace(g.sites, g.box, g.rho, rays.origin, rays.dir, off=off, idx=idx)
+    L = slab_length(g.box, rays.origin, rays.dir)
+    checked = 0
+    for i in range(60):
+        cells, lens = tr.segments(i)
+        if lens.min() < 2e-3:
+            continue  # a segment shorter than the sampling step cannot be resolved
+        ts = np.arange(0.0, L[i], 2.5e-4) + 1.25e-4
+        own = nearest_site(g.sites, rays.origin[i] + ts[:, None] * rays.dir[i])
+        runs = own[np.concatenate([[True], own[1:] != own[:-1]])]
+        assert [int(x) for x in runs] == [int(x) for x in cells]
+        checked += 1
+    assert checked > 40
+
+
+def test_neighbour_exit_equals_all_sites_exit(traced300):
+    g, c, off, idx, rays, tr = traced300
+    tr2 = oracle.trace(g.sites, g.box, g.rho, rays.origin[:400], rays.dir[:400])
+    for i in range(400):
+        a, la = tr.segments(i)
+        b, lb = tr2.segments(i)
+        assert np.array_equal(a, b)
+        np.testing.assert_array_equal(la, lb)
+
+
+def test_uniform_density_closed_form(grid300):
+    g, c, off, idx = grid300
+    rays = gen.uniform_rays(500, 41)
+    rho = np.full(len(g.sites), 1.75)
+    tr = oracle.trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, kappa=2.0)
+    L = slab_length(g.box, rays.origin, rays.dir)
+    np.testing.assert_allclose(tr.tau, 2.0 * 1.75 * L, rtol=1e-13)
+
+
+def test_tau_matches_midpoint_riemann_sum(grid300):
+    g, c, off, idx = grid300
+    rays = gen.uniform_rays(40, 42)
+    tr = oracle.trace(g.sites, g.box, g.rho, rays.origin, rays.dir, off=off, idx=idx)
+    L = slab_length(g.box, rays.origin, rays.dir)
+    for i in range(40):
+        K = 20000
+        h = L[i] / K
+        ts = (np.arange(K) + 0.5) * h
+        own = nearest_site(g.sites, rays.origin[i] + ts[:, None] * rays.dir[i])
+        riemann = h * g.rho[own].astype(np.float64).sum()
+        # each cell boundary contributes at most h * max|rho jump|
+        assert abs(riemann - tr.tau[i]) <= (tr.nseg[i] + 1) * h * 1.0 + 1e-12
+
+
+def test_gradient_matches_finite_differences(grid300):
+    g, c, off, idx = grid300
+    rays = gen.uniform_rays(400, 43)
+    rho = g.rho.astype(np.float64)
+    tr = oracle.trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3)
+    target = np.exp(-tr.tau * 0.9)
+    loss, dL = oracle.exp_loss(tr.tau, target)
+    grad = oracle.tau_grad(tr, len(g.sites), dL, kappa=1.3)
+    rng = gen.rng_for(3)
+    hit = np.unique(np.concatenate([tr.segments(i)[0] for i in range(400)]))
+    for cidx in rng.choice(hit, 15, replace=False):
+        hh = 1e-4 * rho[cidx]
+        rp = rho.copy(); rp[cidx] += hh
+        rm = rho.copy(); rm[cidx] -= hh
+        tp = oracle.trace(g.sites, g.box, rp, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3).tau
+        tm = oracle.trace(g.sites, g.box, rm, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3).tau
+        fd = (oracle.exp_loss(tp, target)[0] - oracle.exp_loss(tm, target)[0]) / (2 * hh)
+        assert abs(fd - grad[cidx]) <= 1e-6 * max(abs(fd), 1e-8), (cidx, fd, grad[cidx])
+    miss = np.setdiff1d(np.arange(len(g.sites)), hit)
+    assert np.all(grad[miss] == 0.0)
+
+
+def test_edge_ray_is_flagged_near_tie():
+    n = 4
+    S = gen.cubic_lattice(n)
+    c, off, idx = _full(S, gen.CUBE_BOX)
+    # a ray starting on the face plane y = 0: the start is equidistant from two sites
+    O = np.array([[-0.9, 0.0, 0.13]])
+    D = np.array([[0.8, 0.0, 0.6]])
+    tr = oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), O, D, off=off, idx=idx)
+    assert tr.near_tie[0] == 1
+    L = slab_length(gen.CUBE_BOX, O, D)
+    np.testing.assert_allclose(tr.length, L, rtol=1e-12)
+    # a ray aimed at the cell edge x = -0.5, y = 0: two exit planes tie
+    O = np.array([[-0.9, -0.1, 0.13]])
+    D = np.array([[0.4, 0.1, 0.07]])
+    D = D / np.linalg.norm(D)
+    tr = oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), O, D, off=off, idx=idx)
+    assert tr.near_tie[0] == 1 and tr.min_margin[0] <= 1e-9
+    np.testing.assert_allclose(tr.length, slab_length(gen.CUBE_BOX, O, D), rtol=1e-12)
+    # a generic ray is not
+    O = np.array([[-0.9, 0.0123, 0.13]])
+    D = np.array([[0.8, 0.1, 0.6]]) / np.linalg.norm([0.8, 0.1, 0.6])
+    assert oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), O, D, off=off, idx=idx).near_tie[0] == 0
+
+
+def test_vertex_ray_zero_length_steps():
+    """A ray through a lattice vertex (eight cubes meet) crosses several cells
+    at one point; zero-length steps emit nothing and the path still ends at
+    the wall."""
+    n = 4
+    S = gen.cubic_lattice(n)
+    c, off, idx = _full(S, gen.CUBE_BOX)
+    D = np.array([[1.0, 1.0, 1.0]]) / np.sqrt(3)
+    O = np.array([[-0.75, -0.75, -0.75]])
+    tr = oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), O, D, off=off, idx=idx)
+    assert tr.status[0] == 0 and tr.near_tie[0] == 1
+    np.testing.assert_allclose(tr.length, slab_length(gen.CUBE_BOX, O, D), rtol=1e-12)
+    cells, lens = tr.segments(0)
+    assert np.all(lens > 0)
+    # the diagonal visits the diagonal cubes (i, i, i)
+    diag = [i * 16 + i * 4 + i for i in range(n)]
+    assert [int(x) for x in cells] == diag
+
+
+def test_status_codes():
+    g = gen.make_uniform_grid(50, 51)
+    c, off, idx = _full(g.sites, g.box)
+    O = np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3], [3.0, 0.0, 0.0]])
+    D = np.array([[1.0, 0, 0], [1.0, 0, 0], [1.0, 0, 0]])
+    tr = oracle.trace(g.sites, g.box, g.rho, O, D, off=off, idx=idx, cap=1)
+    assert tr.status[2] == 1
+    assert tr.status[0] in (0, 3)
+    tr = oracle.trace(g.sites, g.box, g.rho, O[:1], D[:1], off=off, idx=idx, max_steps=1)
+    assert tr.status[0] == 2 or tr.nseg[0] == 1
