@@ -1,0 +1,375 @@
+"""Benchmark: Voronoi path segments per second on one GB300.
+
+Workload (N = 1): a 10^5-site exponential-disk grid (sites drawn from
+rho ~ exp(-R - |z|/0.1) in [-4,4]^2 x [-0.5,0.5], cell density = that rho)
+and 10^6 rays per GPU from the same distribution with isotropic directions.
+One step = start-cell location plus the traversal of every ray to the domain
+boundary, computing tau per ray, float32 plane tests with float64 rechecks.
+The float64 form runs on the same rays for comparison.
+
+With torchrun (N > 1) every rank traces its own 10^6 rays through a copy of
+the grid (weak scaling, no collective on the data path); the time is the
+maximum over ranks.
+
+--impl reference times the CPU oracle (plain float64 C, the paper's loop over
+neighbour lists) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Voronoi path segments/sec on 1 GB300 (FP32+recheck vs FP64) at ≤1e-5 rel tau err"
+UNIT = "segments/s"
+WORKLOAD = "exp-disk 1e5 sites, 1e6 rays/GPU, tau per ray, fp32 plane tests + fp64 recheck"
+L2_BYTES = 129 * 2 ** 20
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("trace.cuh", "kernels.h", "internal.h", "aux.cu"):
+        with open(os.path.join(ROOT, "paper_1310_1854_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per traversal launch from the committed ncu summary, if it
+    was taken from the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "trace_kernel_disk1e5.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    if m and t and m.group(1) == kernel_source_hash():
+        return float(t.group(1))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        load = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        parts = [p for p in vis.split(",") if p.strip()]
+        if local_rank < len(parts) and parts[local_rank].strip().isdigit():
+            return int(parts[local_rank])
+    return local_rank
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (rank 0, N = 1; and the --impl reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_setup(g):
+    import oracle
+    oracle.build()
+    t = time.time()
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    return off, idx, time.time() - t
+
+
+def oracle_sample(g, rays, off, idx, n, seed):
+    import oracle
+    sel = np.sort(np.random.default_rng(seed).choice(len(rays.origin), n, replace=False))
+    t = time.time()
+    tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sel], rays.dir[sel], off=off, idx=idx,
+                      cap=1)
+    dt = time.time() - t
+    return int(tr.nseg.sum()), dt
+
+
+def oracle_threads():
+    n = int(os.environ.get("ORACLE_THREADS", "0"))
+    return n if n > 0 else (os.cpu_count() or 1)
+
+
+def cpu_baseline(g, rays, target_s=10.0):
+    off, idx, setup_s = oracle_setup(g)
+    n = 2000
+    segs, dt = oracle_sample(g, rays, off, idx, n, 1)
+    if dt < target_s:
+        n = int(min(len(rays.origin), max(n, n * target_s / max(dt, 1e-3))))
+        segs, dt = oracle_sample(g, rays, off, idx, n, 2)
+    return {"value": segs / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"{n} of the {len(rays.origin)} rays (seeded), neighbour-list traversal with "
+                      f"brute-force C(r0), float64; cell construction ({setup_s:.1f} s) not timed",
+            "seconds": dt, "segments": segs}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import gen
+    g, rays = gen.config2()
+    off, idx, setup_s = oracle_setup(g)
+    n = 20000
+    for _ in range(args.warmup):
+        oracle_sample(g, rays, off, idx, 2000, 0)
+    segs_total, secs = 0, 0.0
+    for k in range(args.steps):
+        s, dt = oracle_sample(g, rays, off, idx, n, 100 + k)
+        segs_total += s
+        secs += dt
+    v = segs_total / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sites": len(g.sites), "rays": len(rays.origin)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                             "sample": f"{n} seeded rays per step of the {len(rays.origin)}; neighbour lists built "
+                                       f"by the oracle before timing ({setup_s:.1f} s)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--lanes", type=int, default=int(os.environ.get("VGRID_LANES", "0")))
+    ap.add_argument("--block", type=int, default=int(os.environ.get("VGRID_BLOCK", "0")))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rays", type=int, default=1_000_000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+    import torch.distributed as tdist
+
+    import gen
+    from paper_1310_1854_gb300 import VoronoiGrid
+
+    ws, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    g, _ = gen.config2(n_rays=1)
+    rays = gen.disk_rays(args.rays, gen.SEED_BASE + 2 + 1000 + 7919 * rank)
+    vg = VoronoiGrid(g.sites, g.box)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    if args.lanes or args.block:
+        cur = vg.get_launch()
+        vg.set_launch(args.lanes or cur["lanes_per_ray"], args.block or cur["block"])
+    launch = vg.get_launch()
+    info = vg.info()
+    O = torch.from_numpy(rays.origin).to(dev)
+    D = torch.from_numpy(rays.dir).to(dev)
+    N = O.shape[0]
+    tau = torch.empty(N, dtype=torch.float32, device=dev)
+    tau64 = torch.empty(N, dtype=torch.float64, device=dev)
+
+    st32 = vg.trace(O, D, precision="fp32", stats=True).stats
+    st64 = vg.trace(O, D, precision="fp64", stats=True).stats
+    crossings = st32["crossings"]
+    assert st64["crossings"] == crossings or abs(st64["crossings"] - crossings) <= 1e-6 * crossings
+
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(precision, out, steps, warm):
+        for _ in range(warm):
+            vg.trace(O, D, precision=precision, out_tau=out)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        vg.enable_timing(True)
+        vg.read_timing()
+        if ws > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()                      # L2 flushed between steps
+            ev[k][0].record()
+            vg.trace(O, D, precision=precision, out_tau=out)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        if ws > 1:
+            tdist.barrier()
+        step_ms = sum(a.elapsed_time(b) for a, b in ev)
+        loc_ms, tr_ms, launches = vg.read_timing()
+        vg.enable_timing(False)
+        return step_ms, loc_ms, tr_ms, launches
+
+    sampler = ClockSampler(gpu_index(local))
+    sampler.start()
+    step_ms, loc_ms, tr_ms, launches = timed("fp32", tau, args.steps, args.warmup)
+    clocks = sampler.stop()
+    k64 = max(3, args.steps // 4)
+    step64_ms, _, tr64_ms, launches64 = timed("fp64", tau64, k64, 2)
+
+    # accuracy of the float32 form against the float64 form on these rays
+    t32 = tau.double()
+    rel = ((t32 - tau64).abs() / tau64.clamp_min(1e-300))[tau64 > 0]
+    tau_err = {"max": float(rel.max()), "p99": float(torch.quantile(rel[:1_000_000].float(), 0.99)),
+               "mean": float(rel.mean())}
+
+    # end to end through the public call: pinned host inputs in, tau out, every step
+    Oh = torch.from_numpy(rays.origin).pin_memory()
+    Dh = torch.from_numpy(rays.dir).pin_memory()
+    Th = torch.empty(N, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        O.copy_(Oh, non_blocking=True)
+        D.copy_(Dh, non_blocking=True)
+        vg.trace(O, D, precision="fp32", out_tau=tau)
+        Th.copy_(tau, non_blocking=True)
+    if ws > 1:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        O.copy_(Oh, non_blocking=True)
+        D.copy_(Dh, non_blocking=True)
+        vg.trace(O, D, precision="fp32", out_tau=tau)
+        Th.copy_(tau, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+
+    def reduce_max(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    def reduce_sum(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.SUM)
+        return float(t.item())
+
+    step_ms_max = reduce_max(step_ms)
+    step64_max = reduce_max(step64_ms)
+    e2e_max = reduce_max(e2e_ms)
+    seg_all = reduce_sum(float(crossings))
+    rays_all = reduce_sum(float(N))
+    value = seg_all * args.steps / (step_ms_max / 1e3)
+    value64 = seg_all * k64 / (step64_max / 1e3)
+
+    # roofline of the traversal kernel: algorithmic bytes per crossing
+    deg = info["nnz"] / info["M"]
+    bytes_per_crossing = 28.0 + 20.0 * deg
+    per_launch_bytes = crossings * bytes_per_crossing
+    trace_launch_ms = tr_ms / max(launches, 1)
+    achieved = per_launch_bytes / (trace_launch_ms / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = profiled_traffic()
+
+    if rank != 0:
+        if ws > 1:
+            tdist.destroy_process_group()
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sites": info["M"], "rays_per_gpu": N, "mean_degree": round(deg, 3),
+                   "l2": "flushed between timed steps (2x L2 buffer written)",
+                   "launch": launch, "parallelism": f"rays sharded over {ws} GPU(s)"},
+        "rays_per_s": rays_all * args.steps / (step_ms_max / 1e3),
+        "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": step64_max / k64,
+                      "trace_ms_per_launch": tr64_ms / max(launches64, 1)},
+        "fp32_over_fp64": value / value64,
+        "tau_rel_err_vs_fp64": tau_err,
+        "stats_per_step": st32,
+        "recheck_rate": st32["rechecks"] / max(st32["decisions"], 1),
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "trace_kernel<LPR,false,TAU>",
+                     "algorithmic_bytes_per_crossing": bytes_per_crossing, "crossings_per_launch": crossings,
+                     "kernel_ms_per_launch": trace_launch_ms, "locate_ms_per_step": loc_ms / max(launches, 1),
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
+        "e2e": {"value": seg_all * args.steps / (e2e_max / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(O.numel() * 8 + D.numel() * 8), "d2h_bytes_per_step": int(N * 4)},
+        "clocks": clocks,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, rays)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

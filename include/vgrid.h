@@ -1,0 +1,267 @@
+/*
+ * vgrid - straight-path traversal of 3D Voronoi grids on one GPU.
+ *
+ * The method is that of Camps, Baes & Saftly (2013), "Using 3D Voronoi grids
+ * in radiative transfer simulations", Sect. 2: a ray (photon package) with
+ * start r0 inside a cuboidal domain D and unit direction k is followed cell by
+ * cell; in the current cell m the exit is the nearest bisector plane ahead of
+ * the ray among the cell's neighbours (Eq. 1-4) or a domain wall (Eq. 5);
+ * every crossing yields a segment (cell, length) and the optical depth is
+ * tau = sum over segments of kappa * rho_cell * length.
+ *
+ * Conventions for every entry point
+ *  - Return value: VGRID_OK (0) or a negative VGRID_ERR_* code. The message of
+ *    the most recent failure on the calling thread is vgrid_last_error().
+ *  - "device" pointers are CUDA global-memory pointers on the device that was
+ *    current when the grid was created; "host" pointers are ordinary memory.
+ *    The caller owns every buffer it passes and must keep it alive until the
+ *    work on `stream` has finished. The library owns a vgrid_t and its device
+ *    copies and frees them in vgrid_destroy().
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL is the legacy default
+ *    stream). Calls on one vgrid_t share its work buffers, so they must be
+ *    issued on one stream (or otherwise serialised).
+ *  - Cell ids in every input and output are the caller's site indices
+ *    0..M-1. Domain walls are -1 (x = xmin), -2 (x = xmax), -3 (y = ymin),
+ *    -4 (y = ymax), -5 (z = zmin), -6 (z = zmax), as in Sect. 2.2 item 3.
+ *  - There is no CPU fallback: without a usable CUDA device the calls fail
+ *    with VGRID_ERR_CUDA.
+ */
+#ifndef VGRID_H
+#define VGRID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vgrid vgrid_t;
+typedef struct vgrid_batch vgrid_batch_t;
+typedef struct CUstream_st *vgrid_stream_t; /* same type as cudaStream_t */
+
+enum {
+    VGRID_OK = 0,
+    VGRID_ERR_ARG = -1,        /* bad argument (null, size, non-finite, not unit) */
+    VGRID_ERR_DUP_SITE = -2,   /* two sites coincide (after float32 rounding) */
+    VGRID_ERR_OUTSIDE = -3,    /* a site, or a ray start, lies outside the domain */
+    VGRID_ERR_CAPACITY = -4,   /* segment buffer too small; seg_off holds the sizes */
+    VGRID_ERR_STEP_LIMIT = -5, /* some rays hit the step limit (see ray_status) */
+    VGRID_ERR_CUDA = -6,       /* CUDA runtime failure or no device */
+    VGRID_ERR_NOMEM = -7,      /* host or device allocation failed */
+    VGRID_ERR_BUILD = -8       /* the neighbour construction failed for a cell */
+};
+
+/* arithmetic of the exit search */
+enum {
+    VGRID_FP64 = 0,        /* Eq. 1-5 in float64, as written */
+    VGRID_FP32_RECHECK = 1 /* float32 plane tests with error bounds; a crossing
+                              whose two nearest exits are not separated by the
+                              bounds is recomputed in float64 */
+};
+
+/* what vgrid_trace writes */
+enum {
+    VGRID_TAU = 0,     /* tau per ray */
+    VGRID_SEGMENTS = 1 /* tau per ray and the segment list of every ray */
+};
+
+/* per-ray status codes written to ray_status */
+enum {
+    VGRID_RAY_OK = 0,
+    VGRID_RAY_OUTSIDE = 1,   /* start point outside the domain: no path */
+    VGRID_RAY_STEP_LIMIT = 2, /* the path was cut at opts.max_steps decisions */
+    VGRID_RAY_BAD_DIR = 3     /* |dir| differs from 1 by more than 1e-6: not traced */
+};
+
+typedef struct {
+    int32_t threads;           /* host threads for the build; 0 = all cores */
+    int32_t round_sites;       /* 1: round sites to float32; 0: reject sites that are
+                                  not exactly representable in float32 */
+    int32_t reorder;           /* 1 (default): store cells along a Morton curve */
+    double blocks_per_site;    /* locate block grid: blocks per site (default 0.5) */
+    int64_t max_steps;         /* exit decisions per ray before VGRID_RAY_STEP_LIMIT
+                                  (default 100,000) */
+    int32_t host_only;         /* 1: build the neighbour lists, volumes and block
+                                  lists on the host but copy nothing to a device;
+                                  only vgrid_info, vgrid_get_neighbors,
+                                  vgrid_get_cells and vgrid_destroy accept such a
+                                  grid (no GPU needed) */
+} vgrid_opts;
+
+typedef struct {
+    int64_t rays;          /* rays traced */
+    int64_t crossings;     /* segments of positive length */
+    int64_t decisions;     /* exit decisions (crossings, zero-length steps, wall exit) */
+    int64_t rechecks;      /* float64 rechecks of float32 decisions */
+    int64_t fallbacks;     /* epsilon nudges followed by a new C(r) (Sect. 2.2) */
+    int64_t zero_steps;    /* zero-length steps */
+    int64_t step_limit;    /* rays cut at max_steps */
+    int64_t outside;       /* rays starting outside the domain */
+} vgrid_stats;
+
+typedef struct {
+    int64_t M;             /* sites */
+    int64_t nnz;           /* neighbour entries including walls */
+    int64_t block_entries; /* entries of all block lists */
+    int32_t block_dim[3];  /* locate block grid */
+    double box[6];         /* xmin, ymin, zmin, xmax, ymax, zmax */
+    double build_seconds;  /* host time of vgrid_create */
+    int64_t device_bytes;  /* device memory held by the grid */
+} vgrid_info_t;
+
+/* launch shape of the traversal kernels */
+typedef struct {
+    int32_t lanes_per_ray; /* 1, 2, 4 or 8 lanes cooperate on one ray */
+    int32_t block;         /* threads per block (multiple of 32, 32..256) */
+    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit */
+} vgrid_launch;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *vgrid_last_error(void);
+
+/* Fill *opts with the defaults. */
+void vgrid_default_opts(vgrid_opts *opts);
+
+/*
+ * Build a grid (Sect. 2.2 setup items 1-3 and the block lists of Sect. 2.3).
+ *   sites  host, M x 3 float64 (x, y, z per site), all inside the closed box.
+ *   bbox   host, 6 float64: xmin, ymin, zmin, xmax, ymax, zmax.
+ *   opts   host, nullable (defaults).
+ * On the host: the cell of every site is cut from the box by the bisector
+ * half-spaces of nearby sites (Sect. 2.1), giving neighbour lists with walls,
+ * cell volumes and bounding boxes; the bounding boxes fill a regular block grid
+ * of candidate lists for C(r) (Sect. 2.3). The lists, the sites (float32) and
+ * a default density rho = 1, kappa = 1 are then copied to the current device.
+ * Errors: VGRID_ERR_ARG, VGRID_ERR_OUTSIDE (site outside box),
+ * VGRID_ERR_DUP_SITE, VGRID_ERR_BUILD, VGRID_ERR_NOMEM, VGRID_ERR_CUDA.
+ */
+int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgrid_opts *opts, vgrid_t **out);
+
+/* Free the grid and its device memory. NULL is accepted. */
+int vgrid_destroy(vgrid_t *g);
+
+/* Sizes and build facts. */
+int vgrid_info(const vgrid_t *g, vgrid_info_t *info);
+
+/*
+ * Host copies of the neighbour lists (Sect. 2.2 item 3) in the caller's ids:
+ * off host int64[M+1], idx host int32[info.nnz] (walls negative, ascending
+ * within a cell). Either pointer may be NULL to skip it.
+ */
+int vgrid_get_neighbors(const vgrid_t *g, int64_t *off, int32_t *idx);
+
+/* Host copies of cell volumes (host float64[M]) and bounding boxes
+ * (host float64[M*6]); either may be NULL. */
+int vgrid_get_cells(const vgrid_t *g, double *volume, double *bbox);
+
+/*
+ * Set the density per cell, rho (device float32[M], caller ids), and the
+ * opacity kappa used in tau = sum kappa rho l. The values are copied into the
+ * grid's own cell order on `stream`; later changes to rho are not seen.
+ */
+int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t stream);
+
+/*
+ * C(r) of Sect. 2.3 for N points: pts device float64[N*3]; cell device
+ * int32[N] receives the nearest site (caller id), or -1 for points outside the
+ * closed box. precision: VGRID_FP64 (distances in float64) or
+ * VGRID_FP32_RECHECK (float32 distances; near-equal candidates are compared
+ * again in float64). Exact ties go to the lowest site index.
+ */
+int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_t *cell, vgrid_stream_t stream);
+
+/*
+ * Trace N rays to the domain boundary (Sect. 2.2).
+ *   origin, dir   device float64[N*3]; every dir must have unit length
+ *                 within 1e-6 (checked on the device: such a ray gets tau 0,
+ *                 no segments and status VGRID_RAY_BAD_DIR).
+ *   precision     VGRID_FP64 or VGRID_FP32_RECHECK.
+ *   output        VGRID_TAU or VGRID_SEGMENTS.
+ *   tau           device float64[N] (FP64) or float32[N] (FP32_RECHECK);
+ *                 nullable in segment mode.
+ *   seg_off       device int64[N+1] (segment mode): exclusive prefix sum of
+ *                 the per-ray segment counts; seg_off[N] is the total.
+ *   seg_cell      device int32[seg_capacity]: cell id of each segment.
+ *   seg_len       device float64 (FP64) or float32 (FP32_RECHECK)
+ *                 [seg_capacity]: segment lengths.
+ *   ray_status    device int32[N] or NULL: VGRID_RAY_* per ray.
+ *   stats         host or NULL: counters of this call (synchronises `stream`).
+ * Segment mode traces twice (count, then fill) and reads the total back to
+ * the host; if seg_capacity is too small it returns VGRID_ERR_CAPACITY with
+ * seg_off filled so the caller can size the buffers and call again.
+ * Rays that start outside the domain get tau = 0, no segments and status
+ * VGRID_RAY_OUTSIDE (not an error). Whenever the call reads its counters back
+ * (stats non-NULL, or segment mode) it returns VGRID_ERR_ARG if some
+ * direction was not a unit vector and VGRID_ERR_STEP_LIMIT if some ray was
+ * cut at max_steps, after writing every output; in tau mode without stats
+ * the call does not synchronise and those rays show only in ray_status.
+ * The first call with more rays than any earlier call on this grid
+ * allocates a larger work buffer (N int32).
+ */
+int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, int output,
+                void *tau, int64_t *seg_off, int32_t *seg_cell, void *seg_len, int64_t seg_capacity,
+                int32_t *ray_status, vgrid_stats *stats, vgrid_stream_t stream);
+
+/*
+ * Adjoint of tau = sum kappa rho l with respect to rho: for every ray r and
+ * every segment (c, l) of its path, dL_drho[c] += dL_dtau[r] * kappa * l.
+ * The path is the one vgrid_trace finds with VGRID_FP32_RECHECK.
+ *   dL_dtau  device float32[N]; dL_drho device float32[M], accumulated into
+ *   (caller ids; zero it first for a plain gradient).
+ */
+int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *dL_dtau,
+                     float *dL_drho, vgrid_stream_t stream);
+
+/* Launch shape used by this grid's traversal kernels (NULL resets to the
+ * built-in default). */
+int vgrid_set_launch(vgrid_t *g, const vgrid_launch *launch);
+int vgrid_get_launch(const vgrid_t *g, vgrid_launch *launch);
+
+/*
+ * Many grids in one launch (uneven sizes and ray counts). Each set names a
+ * grid and its rays; tau (device float32[n]) and status (device int32[n],
+ * nullable) receive the results of VGRID_FP32_RECHECK tracing.
+ */
+typedef struct {
+    const vgrid_t *grid;
+    const double *origin; /* device float64[n*3] */
+    const double *dir;    /* device float64[n*3] */
+    int64_t n;
+    float *tau;           /* device float32[n] */
+    int32_t *status;      /* device int32[n] or NULL */
+} vgrid_rayset;
+
+/*
+ * Prepare a batch: copies the per-grid descriptors to the device and sizes
+ * its work buffers. The rays and outputs named in `sets` must stay valid for
+ * every later vgrid_batch_run. launch may be NULL (built-in default).
+ */
+int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *launch, vgrid_batch_t **out);
+
+/*
+ * Run the batch on `stream`: one locate launch and one persistent traversal
+ * launch over all (grid, ray) work items. With use_graph = 1 the sequence is
+ * captured into a CUDA graph on the first call and replayed afterwards.
+ */
+int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_stream_t stream);
+
+int vgrid_batch_destroy(vgrid_batch_t *b);
+
+/*
+ * Device-time accounting for benchmarks. With enable = 1, every later
+ * vgrid_trace / vgrid_trace_grad call on this grid records CUDA events on its
+ * stream around the start-cell launch (C(r0) for all rays) and around each
+ * traversal launch, without synchronising. vgrid_read_timing waits for those
+ * events, returns the summed milliseconds and the number of traversal
+ * launches since the previous read, and clears the record. Timing adds no
+ * work to the kernels themselves.
+ */
+int vgrid_enable_timing(vgrid_t *g, int enable);
+int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VGRID_H */

@@ -1,0 +1,274 @@
+"""Straight-path traversal of 3D Voronoi grids on one GB300 GPU.
+
+Python face of libvgrid (include/vgrid.h): argument marshalling only, every
+step of the path runs in the library's CUDA kernels. PyTorch supplies device
+memory and streams.
+
+The method is that of Camps, Baes & Saftly (2013), Sect. 2: rays are
+followed cell by cell through the Voronoi tessellation of a set of sites in
+a cuboidal domain; the exit from the current cell is the nearest bisector
+plane (Eq. 1-4) or domain wall (Eq. 5) ahead; the optical depth is
+tau = sum kappa rho_cell l.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import VGridError, check, load
+
+__all__ = ["VoronoiGrid", "Batch", "TraceResult", "optical_depth", "VGridError", "load"]
+
+_PREC = {"fp64": _lib.FP64, "fp32": _lib.FP32_RECHECK}
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else None
+
+
+def _rays(t, name, device):
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA float64 tensor of shape (N, 3)")
+    if t.dim() != 2 or t.shape[1] != 3:
+        raise ValueError(f"{name} must have shape (N, 3)")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the grid on {device}")
+    return t.contiguous()
+
+
+@dataclasses.dataclass
+class TraceResult:
+    tau: torch.Tensor | None
+    seg_off: torch.Tensor | None = None
+    seg_cell: torch.Tensor | None = None
+    seg_len: torch.Tensor | None = None
+    status: torch.Tensor | None = None
+    stats: dict | None = None
+
+    def segments(self, i):
+        a, b = int(self.seg_off[i]), int(self.seg_off[i + 1])
+        return self.seg_cell[a:b], self.seg_len[a:b]
+
+
+class VoronoiGrid:
+    """A Voronoi grid on the current CUDA device.
+
+    sites: (M, 3) array of float32-representable positions inside ``box``
+    (xmin, ymin, zmin, xmax, ymax, zmax). The neighbour lists, cell volumes,
+    bounding boxes and block lists are built on the host by the library.
+    """
+
+    def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=0.5,
+                 max_steps=100_000, threads=0, device=None, host_only=False):
+        lib = load()
+        S = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 3))
+        B = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(6))
+        opts = _lib.Opts()
+        lib.vgrid_default_opts(ctypes.byref(opts))
+        opts.threads = int(threads)
+        opts.round_sites = int(bool(round_sites))
+        opts.reorder = int(bool(reorder))
+        opts.blocks_per_site = float(blocks_per_site)
+        opts.max_steps = int(max_steps)
+        opts.host_only = int(bool(host_only))
+        h = ctypes.c_void_p()
+        args = (S.ctypes.data_as(ctypes.c_void_p), S.shape[0], B.ctypes.data_as(ctypes.c_void_p),
+                ctypes.byref(opts), ctypes.byref(h))
+        if host_only:
+            self.device = None
+            check(lib.vgrid_create(*args))
+        else:
+            self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+            with torch.cuda.device(self.device):
+                torch.cuda.init()
+                check(lib.vgrid_create(*args))
+        self._h = h
+        self.M = S.shape[0]
+        self.box = B.copy()
+        self.kappa = 1.0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().vgrid_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    # ------------------------------------------------------------------ info
+    def info(self) -> dict:
+        i = _lib.Info()
+        check(load().vgrid_info(self._h, ctypes.byref(i)))
+        return {"M": i.M, "nnz": i.nnz, "block_entries": i.block_entries, "block_dim": list(i.block_dim),
+                "box": list(i.box), "build_seconds": i.build_seconds, "device_bytes": i.device_bytes}
+
+    def neighbors(self):
+        """CSR (off int64[M+1], idx int32) in the caller's ids, walls -1..-6."""
+        nnz = self.info()["nnz"]
+        off = np.zeros(self.M + 1, np.int64)
+        idx = np.zeros(max(nnz, 1), np.int32)
+        check(load().vgrid_get_neighbors(self._h, off.ctypes.data_as(ctypes.c_void_p),
+                                         idx.ctypes.data_as(ctypes.c_void_p)))
+        return off, idx[:nnz]
+
+    def cells(self):
+        """(volume float64[M], bbox float64[M, 6])."""
+        vol = np.zeros(self.M, np.float64)
+        bb = np.zeros((self.M, 6), np.float64)
+        check(load().vgrid_get_cells(self._h, vol.ctypes.data_as(ctypes.c_void_p), bb.ctypes.data_as(ctypes.c_void_p)))
+        return vol, bb
+
+    # -------------------------------------------------------------- launch
+    def set_launch(self, lanes_per_ray=4, block=256, blocks_per_sm=0):
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm))
+        check(load().vgrid_set_launch(self._h, ctypes.byref(l)))
+
+    def get_launch(self):
+        l = _lib.Launch()
+        check(load().vgrid_get_launch(self._h, ctypes.byref(l)))
+        return {"lanes_per_ray": l.lanes_per_ray, "block": l.block, "blocks_per_sm": l.blocks_per_sm}
+
+    def enable_timing(self, enable=True):
+        check(load().vgrid_enable_timing(self._h, int(bool(enable))))
+
+    def read_timing(self):
+        """(locate_ms, trace_ms, traversal launches) since the last read."""
+        a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        check(load().vgrid_read_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(n)))
+        return a.value, b.value, n.value
+
+    # ------------------------------------------------------------- density
+    def set_density(self, rho: torch.Tensor, kappa: float = 1.0, stream=None):
+        if rho.dtype != torch.float32 or not rho.is_cuda or rho.numel() != self.M:
+            raise TypeError("rho must be a CUDA float32 tensor with one value per site")
+        rho = rho.contiguous()
+        check(load().vgrid_set_density(self._h, _ptr(rho), float(kappa), _stream(stream)))
+        self.kappa = float(kappa)
+
+    # ------------------------------------------------------------- compute
+    def locate(self, points: torch.Tensor, precision="fp32", stream=None) -> torch.Tensor:
+        P = _rays(points, "points", self.device)
+        out = torch.empty(P.shape[0], dtype=torch.int32, device=self.device)
+        check(load().vgrid_locate(self._h, _ptr(P), P.shape[0], _PREC[precision], _ptr(out), _stream(stream)))
+        return out
+
+    def trace(self, origin, direction, precision="fp32", segments=False, status=False, stats=False,
+              seg_capacity=None, stream=None, out_tau=None) -> TraceResult:
+        lib = load()
+        O = _rays(origin, "origin", self.device)
+        D = _rays(direction, "direction", self.device)
+        N = O.shape[0]
+        prec = _PREC[precision]
+        tdt = torch.float64 if prec == _lib.FP64 else torch.float32
+        tau = out_tau if out_tau is not None else torch.empty(N, dtype=tdt, device=self.device)
+        st = torch.empty(N, dtype=torch.int32, device=self.device) if status else None
+        cs = _lib.Stats() if (stats or segments) else None
+        sref = ctypes.byref(cs) if cs is not None else None
+        if not segments:
+            check(lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.TAU, _ptr(tau), None, None, None, 0,
+                                  _ptr(st), sref, _stream(stream)))
+            return TraceResult(tau, status=st, stats=cs.as_dict() if cs is not None else None)
+        seg_off = torch.empty(N + 1, dtype=torch.int64, device=self.device)
+        cap = int(seg_capacity) if seg_capacity is not None else 0
+        cells = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+        lens = torch.empty(max(cap, 1), dtype=tdt, device=self.device)
+        rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS, _ptr(tau), _ptr(seg_off),
+                             _ptr(cells), _ptr(lens), cap, _ptr(st), sref, _stream(stream))
+        if rc == _lib.ERR_CAPACITY and seg_capacity is None:
+            total = int(seg_off[N].item())
+            cells = torch.empty(max(total, 1), dtype=torch.int32, device=self.device)
+            lens = torch.empty(max(total, 1), dtype=tdt, device=self.device)
+            rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS, _ptr(tau), _ptr(seg_off),
+                                 _ptr(cells), _ptr(lens), total, _ptr(st), sref, _stream(stream))
+        check(rc)
+        total = int(seg_off[N].item())
+        return TraceResult(tau, seg_off, cells[:total], lens[:total], st, cs.as_dict())
+
+    def trace_grad(self, origin, direction, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """dL/drho (float32[M]) for dL/dtau per ray; accumulates into ``out``."""
+        O = _rays(origin, "origin", self.device)
+        D = _rays(direction, "direction", self.device)
+        g = dL_dtau.detach().to(torch.float32).contiguous()
+        if out is None:
+            out = torch.zeros(self.M, dtype=torch.float32, device=self.device)
+        check(load().vgrid_trace_grad(self._h, _ptr(O), _ptr(D), O.shape[0], _ptr(g), _ptr(out), _stream(stream)))
+        return out
+
+
+class Batch:
+    """Many (grid, rays) sets traced in one persistent launch, float32 form.
+
+    ``sets`` is a list of (VoronoiGrid, origin, direction); outputs are
+    allocated here. With ``graph=True`` the launch sequence is captured into a
+    CUDA graph on the first run and replayed afterwards.
+    """
+
+    def __init__(self, sets, lanes_per_ray=4, block=256, blocks_per_sm=0):
+        self._keep = []
+        arr = (_lib.Rayset * len(sets))()
+        self.tau = []
+        self.status = []
+        for i, (grid, o, d) in enumerate(sets):
+            O = _rays(o, "origin", grid.device)
+            D = _rays(d, "direction", grid.device)
+            t = torch.empty(O.shape[0], dtype=torch.float32, device=grid.device)
+            s = torch.empty(O.shape[0], dtype=torch.int32, device=grid.device)
+            self._keep += [grid, O, D, t, s]
+            self.tau.append(t)
+            self.status.append(s)
+            arr[i] = _lib.Rayset(grid._h.value, O.data_ptr() if O.numel() else None,
+                                 D.data_ptr() if D.numel() else None, O.shape[0],
+                                 t.data_ptr() if t.numel() else None, s.data_ptr() if s.numel() else None)
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm))
+        h = ctypes.c_void_p()
+        check(load().vgrid_batch_create(arr, len(sets), ctypes.byref(l), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, graph=False, stats=False, stream=None):
+        cs = _lib.Stats() if stats else None
+        check(load().vgrid_batch_run(self._h, int(bool(graph)), ctypes.byref(cs) if cs is not None else None,
+                                     _stream(stream)))
+        return cs.as_dict() if cs is not None else None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                load().vgrid_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+
+class _OpticalDepth(torch.autograd.Function):
+    """tau(rho) for fixed rays; backward is the library's adjoint traversal."""
+
+    @staticmethod
+    def forward(ctx, rho, grid, origin, direction, kappa):
+        grid.set_density(rho.detach().to(torch.float32).contiguous(), kappa)
+        res = grid.trace(origin, direction, precision="fp32")
+        ctx.grid = grid
+        ctx.save_for_backward(origin, direction)
+        return res.tau
+
+    @staticmethod
+    def backward(ctx, g):
+        origin, direction = ctx.saved_tensors
+        d = ctx.grid.trace_grad(origin, direction, g.contiguous())
+        return d, None, None, None, None
+
+
+def optical_depth(grid: VoronoiGrid, rho: torch.Tensor, origin: torch.Tensor, direction: torch.Tensor,
+                  kappa: float = 1.0) -> torch.Tensor:
+    """Differentiable tau per ray with respect to the per-cell densities rho."""
+    return _OpticalDepth.apply(rho, grid, origin, direction, kappa)

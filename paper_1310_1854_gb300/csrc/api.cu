@@ -1,0 +1,774 @@
+// C-ABI of libvgrid (declared in include/vgrid.h): grid construction and
+// upload, C(r), traversal in the float64 and float32-with-recheck forms,
+// segment lists, the adjoint, and batched launches over many grids.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+#include "vgrid.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define VG_CUDA(call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return fail(VGRID_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+const vg::KernelSet &kernels(int lpr) {
+    static vg::KernelSet t1, t2, t4, t8;
+    static bool init = [] {
+        vg::kernel_table_lpr1(t1);
+        vg::kernel_table_lpr2(t2);
+        vg::kernel_table_lpr4(t4);
+        vg::kernel_table_lpr8(t8);
+        return true;
+    }();
+    (void)init;
+    switch (lpr) {
+        case 1: return t1;
+        case 2: return t2;
+        case 8: return t8;
+        default: return t4;
+    }
+}
+
+bool valid_lpr(int l) { return l == 1 || l == 2 || l == 4 || l == 8; }
+
+template <class T>
+int dmalloc(T **p, size_t n, int64_t &total) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+    if (e != cudaSuccess) return fail(VGRID_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    total += (int64_t)(n * sizeof(T));
+    return VGRID_OK;
+}
+
+}  // namespace
+
+struct vgrid {
+    int device = 0;
+    int sms = 1;
+    int64_t M = 0;
+    vgrid_opts opts{};
+    vgrid_launch launch{4, 256, 0};
+    GridDev hd{};
+    GridDev *d_desc = nullptr;
+    float4 *d_site = nullptr;
+    int32_t *d_nbr = nullptr;
+    float *d_rho = nullptr;
+    int32_t *d_perm = nullptr;
+    int32_t *d_blk_off = nullptr;
+    int32_t *d_blk_idx = nullptr;
+    std::vector<int32_t> perm, inv;  // internal -> caller, caller -> internal
+    vg::CellsOut cells;              // internal order
+    vg::BlocksOut blocks;
+    // work buffers
+    unsigned long long *d_queue = nullptr;
+    StatsDev *d_stats = nullptr;
+    RaySetDev *d_set = nullptr;
+    int32_t *d_start = nullptr;
+    int64_t start_cap = 0;
+    int64_t *d_scan = nullptr;
+    int64_t scan_cap = 0;
+    double build_seconds = 0;
+    int64_t device_bytes = 0;
+    // optional event record: {locate start, locate end} or {trace start, trace end}
+    bool timing = false;
+    std::vector<std::array<cudaEvent_t, 2>> ev_loc, ev_trace;
+    size_t n_loc = 0, n_trace = 0;
+};
+
+struct vgrid_batch {
+    int device = 0;
+    int sms = 1;
+    int32_t G = 0;
+    int64_t total = 0;
+    vgrid_launch launch{4, 256, 0};
+    GridDev *d_grids = nullptr;
+    RaySetDev *d_sets = nullptr;
+    int32_t *d_start = nullptr;
+    unsigned long long *d_queue = nullptr;
+    StatsDev *d_stats = nullptr;
+    int ngrids = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+extern "C" {
+
+const char *vgrid_last_error(void) { return g_err.c_str(); }
+
+void vgrid_default_opts(vgrid_opts *o) {
+    if (!o) return;
+    o->threads = 0;
+    o->round_sites = 0;
+    o->reorder = 1;
+    o->blocks_per_site = 0.5;
+    o->max_steps = 100000;
+    o->host_only = 0;
+}
+
+static void free_events(vgrid_t *g) {
+    for (auto *v : {&g->ev_loc, &g->ev_trace})
+        for (auto &p : *v) {
+            cudaEventDestroy(p[0]);
+            cudaEventDestroy(p[1]);
+        }
+    g->ev_loc.clear();
+    g->ev_trace.clear();
+    g->n_loc = g->n_trace = 0;
+}
+
+static void free_grid(vgrid_t *g) {
+    if (!g) return;
+    free_events(g);
+    void *ptrs[] = {g->d_desc, g->d_site, g->d_nbr, g->d_rho, g->d_perm, g->d_blk_off, g->d_blk_idx,
+                    g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete g;
+}
+
+int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgrid_opts *opts, vgrid_t **out) {
+    g_err.clear();
+    if (!out) return fail(VGRID_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sites || !bbox) return fail(VGRID_ERR_ARG, "sites or bbox is NULL");
+    if (M < 1) return fail(VGRID_ERR_ARG, "need at least one site");
+    if (M > (int64_t)1 << 30) return fail(VGRID_ERR_ARG, "too many sites");
+    for (int c = 0; c < 3; c++)
+        if (!std::isfinite(bbox[c]) || !std::isfinite(bbox[3 + c]) || !(bbox[c] < bbox[3 + c]))
+            return fail(VGRID_ERR_ARG, "bbox must be finite with min < max on every axis");
+    vgrid_opts o;
+    vgrid_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.blocks_per_site > 0)) o.blocks_per_site = 0.5;
+    if (o.max_steps <= 0) o.max_steps = 100000;
+    const auto t0 = std::chrono::steady_clock::now();
+
+    // sites as float32 values (the device stores float4)
+    std::vector<double> S(3 * M);
+    for (int64_t i = 0; i < 3 * M; i++) {
+        const double v = sites[i];
+        if (!std::isfinite(v)) return fail(VGRID_ERR_ARG, "site " + std::to_string(i / 3) + " is not finite");
+        const double f = (double)(float)v;
+        if (f != v && !o.round_sites)
+            return fail(VGRID_ERR_ARG, "site " + std::to_string(i / 3) + " is not representable in float32");
+        S[i] = f;
+    }
+    for (int64_t i = 0; i < M; i++)
+        for (int c = 0; c < 3; c++)
+            if (!(S[3 * i + c] >= bbox[c] && S[3 * i + c] <= bbox[3 + c]))
+                return fail(VGRID_ERR_OUTSIDE, "site " + std::to_string(i) + " lies outside the box");
+    {
+        std::vector<int32_t> ord(M);
+        for (int64_t i = 0; i < M; i++) ord[i] = (int32_t)i;
+        std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+            return std::lexicographical_compare(&S[3 * (int64_t)a], &S[3 * (int64_t)a] + 3, &S[3 * (int64_t)b],
+                                                &S[3 * (int64_t)b] + 3);
+        });
+        for (int64_t i = 1; i < M; i++)
+            if (std::equal(&S[3 * (int64_t)ord[i]], &S[3 * (int64_t)ord[i]] + 3, &S[3 * (int64_t)ord[i - 1]]))
+                return fail(VGRID_ERR_DUP_SITE, "sites " + std::to_string(ord[i - 1]) + " and " +
+                                                    std::to_string(ord[i]) + " coincide");
+    }
+
+    vgrid_t *g = new vgrid();
+    g->M = M;
+    g->opts = o;
+    if (o.reorder) vg::morton_order(S.data(), M, bbox, g->perm);
+    else {
+        g->perm.resize(M);
+        for (int64_t i = 0; i < M; i++) g->perm[i] = (int32_t)i;
+    }
+    g->inv.resize(M);
+    for (int64_t i = 0; i < M; i++) g->inv[g->perm[i]] = (int32_t)i;
+    std::vector<double> Si(3 * M);
+    for (int64_t i = 0; i < M; i++)
+        for (int c = 0; c < 3; c++) Si[3 * i + c] = S[3 * (int64_t)g->perm[i] + c];
+
+    std::string err;
+    if (vg::build_cells(Si.data(), M, bbox, o.threads, g->cells, err) != 0) {
+        delete g;
+        return fail(VGRID_ERR_BUILD, err);
+    }
+    vg::build_blocks(bbox, g->cells.bbox, M, o.blocks_per_site, g->blocks);
+    if ((int64_t)g->blocks.idx.size() >= ((int64_t)1 << 31)) {
+        delete g;
+        return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
+    }
+
+    // neighbour lists: [count, ids..., padding to a multiple of 4], 16-byte aligned
+    std::vector<int32_t> lists;
+    std::vector<float> site4(4 * M);
+    lists.reserve(g->cells.idx.size() + 4 * M + 64);
+    for (int64_t i = 0; i < M; i++) {
+        const int64_t off = (int64_t)lists.size();
+        if (off >= ((int64_t)1 << 31) - 64) {
+            delete g;
+            return fail(VGRID_ERR_NOMEM, "neighbour lists exceed 2^31 entries");
+        }
+        const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
+        lists.push_back((int32_t)(e - b));
+        for (int64_t q = b; q < e; q++) lists.push_back(g->cells.idx[q]);
+        while (lists.size() % 4) lists.push_back(VG_PAD_ID);
+        int32_t offi = (int32_t)off;
+        site4[4 * i + 0] = (float)Si[3 * i + 0];
+        site4[4 * i + 1] = (float)Si[3 * i + 1];
+        site4[4 * i + 2] = (float)Si[3 * i + 2];
+        std::memcpy(&site4[4 * i + 3], &offi, 4);
+    }
+    for (int i = 0; i < 64; i++) lists.push_back(VG_PAD_ID);  // room for speculative chunk reads
+    std::vector<int32_t> boff(g->blocks.off.size());
+    for (size_t i = 0; i < boff.size(); i++) boff[i] = (int32_t)g->blocks.off[i];
+
+    if (o.host_only) {
+        g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int c = 0; c < 3; c++) {
+            g->hd.lo[c] = bbox[c];
+            g->hd.hi[c] = bbox[3 + c];
+        }
+        g->device = -1;
+        *out = g;
+        return VGRID_OK;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete g;
+        return fail(VGRID_ERR_CUDA, "no CUDA device");
+    }
+    g->device = dev;
+    cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev);
+    int rc = VGRID_OK;
+#define VG_ALLOC(p, n)                                              \
+    if ((rc = dmalloc(&(p), (size_t)(n), g->device_bytes)) != 0) { \
+        free_grid(g);                                               \
+        return rc;                                                  \
+    }
+    VG_ALLOC(g->d_site, M);
+    VG_ALLOC(g->d_nbr, lists.size());
+    VG_ALLOC(g->d_rho, M);
+    VG_ALLOC(g->d_perm, M);
+    VG_ALLOC(g->d_blk_off, boff.size());
+    VG_ALLOC(g->d_blk_idx, g->blocks.idx.size());
+    VG_ALLOC(g->d_desc, 1);
+    VG_ALLOC(g->d_queue, 1);
+    VG_ALLOC(g->d_stats, 1);
+    VG_ALLOC(g->d_set, 1);
+#undef VG_ALLOC
+    std::vector<float> ones(M, 1.0f);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_site, site4.data(), sizeof(float) * 4 * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_nbr, lists.data(), sizeof(int32_t) * lists.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rho, ones.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !g->blocks.idx.empty())
+        e = cudaMemcpy(g->d_blk_idx, g->blocks.idx.data(), sizeof(int32_t) * g->blocks.idx.size(), cudaMemcpyHostToDevice);
+
+    GridDev &hd = g->hd;
+    hd.site = g->d_site;
+    hd.nbr = g->d_nbr;
+    hd.rho = g->d_rho;
+    hd.perm = g->d_perm;
+    hd.blk_off = g->d_blk_off;
+    hd.blk_idx = g->d_blk_idx;
+    double dmax = 0;
+    for (int c = 0; c < 3; c++) {
+        hd.lo[c] = bbox[c];
+        hd.hi[c] = bbox[3 + c];
+        hd.bdim[c] = g->blocks.dim[c];
+        hd.bscale[c] = (double)g->blocks.dim[c] / (bbox[3 + c] - bbox[c]);
+        dmax = std::max(dmax, std::max(std::fabs(bbox[c]), std::fabs(bbox[3 + c])));
+    }
+    const double dx = bbox[3] - bbox[0], dy = bbox[4] - bbox[1], dz = bbox[5] - bbox[2];
+    const double diag = std::sqrt(dx * dx + dy * dy + dz * dz);
+    hd.M = (int32_t)M;
+    hd.kappa = 1.0f;
+    hd.eps64 = 1e-12 * diag;
+    hd.eps32 = 1e-6 * diag;
+    hd.scale = dmax + diag;
+    hd.max_steps = o.max_steps;
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_desc, &hd, sizeof(GridDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_grid(g);
+        return fail(VGRID_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
+    g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = g;
+    return VGRID_OK;
+}
+
+int vgrid_destroy(vgrid_t *g) {
+    if (!g) return VGRID_OK;
+    if (g->device < 0) {
+        delete g;
+        return VGRID_OK;
+    }
+    DeviceGuard dg(g->device);
+    free_grid(g);
+    return VGRID_OK;
+}
+
+int vgrid_info(const vgrid_t *g, vgrid_info_t *info) {
+    if (!g || !info) return fail(VGRID_ERR_ARG, "null argument");
+    info->M = g->M;
+    info->nnz = (int64_t)g->cells.idx.size();
+    info->block_entries = (int64_t)g->blocks.idx.size();
+    for (int c = 0; c < 3; c++) {
+        info->block_dim[c] = g->blocks.dim[c];
+        info->box[c] = g->hd.lo[c];
+        info->box[3 + c] = g->hd.hi[c];
+    }
+    info->build_seconds = g->build_seconds;
+    info->device_bytes = g->device_bytes;
+    return VGRID_OK;
+}
+
+int vgrid_get_neighbors(const vgrid_t *g, int64_t *off, int32_t *idx) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    int64_t pos = 0;
+    std::vector<int32_t> tmp;
+    for (int64_t c = 0; c < g->M; c++) {
+        const int32_t i = g->inv[c];
+        const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
+        if (off) off[c] = pos;
+        if (idx) {
+            tmp.clear();
+            for (int64_t q = b; q < e; q++) {
+                const int32_t j = g->cells.idx[q];
+                tmp.push_back(j >= 0 ? g->perm[j] : j);
+            }
+            std::sort(tmp.begin(), tmp.end());
+            std::copy(tmp.begin(), tmp.end(), idx + pos);
+        }
+        pos += e - b;
+    }
+    if (off) off[g->M] = pos;
+    return VGRID_OK;
+}
+
+int vgrid_get_cells(const vgrid_t *g, double *volume, double *bbox) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    for (int64_t c = 0; c < g->M; c++) {
+        const int32_t i = g->inv[c];
+        if (volume) volume[c] = g->cells.vol[i];
+        if (bbox)
+            for (int k = 0; k < 6; k++) bbox[6 * c + k] = g->cells.bbox[6 * (int64_t)i + k];
+    }
+    return VGRID_OK;
+}
+
+int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t stream) {
+    if (!g || !rho) return fail(VGRID_ERR_ARG, "null argument");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (!std::isfinite(kappa)) return fail(VGRID_ERR_ARG, "kappa is not finite");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    VG_CUDA(vg::launch_permute_density(rho, g->d_perm, g->M, g->d_rho, s));
+    g->hd.kappa = kappa;
+    VG_CUDA(vg::launch_put_grid(g->d_desc, g->hd, s));
+    return VGRID_OK;
+}
+
+int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (!l) {
+        g->launch = vgrid_launch{4, 256, 0};
+        return VGRID_OK;
+    }
+    if (!valid_lpr(l->lanes_per_ray)) return fail(VGRID_ERR_ARG, "lanes_per_ray must be 1, 2, 4 or 8");
+    if (l->block < 32 || l->block > 256 || l->block % 32) return fail(VGRID_ERR_ARG, "block must be 32..256, multiple of 32");
+    if (l->blocks_per_sm < 0) return fail(VGRID_ERR_ARG, "blocks_per_sm must be >= 0");
+    g->launch = *l;
+    return VGRID_OK;
+}
+
+int vgrid_get_launch(const vgrid_t *g, vgrid_launch *l) {
+    if (!g || !l) return fail(VGRID_ERR_ARG, "null argument");
+    *l = g->launch;
+    return VGRID_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// record event pair `which` (0: start cells, 1: traversal) around a launch
+cudaEvent_t next_event(vgrid_t *g, int which, int half) {
+    auto &v = which == 0 ? g->ev_loc : g->ev_trace;
+    size_t &n = which == 0 ? g->n_loc : g->n_trace;
+    if (half == 0 && n == v.size()) {
+        std::array<cudaEvent_t, 2> p{};
+        if (cudaEventCreate(&p[0]) != cudaSuccess || cudaEventCreate(&p[1]) != cudaSuccess) return nullptr;
+        v.push_back(p);
+    }
+    if (half == 0) return v[n][0];
+    return v[n++][1];
+}
+
+void mark(vgrid_t *g, int which, int half, cudaStream_t s) {
+    if (!g->timing) return;
+    cudaEvent_t e = next_event(g, which, half);
+    if (e) cudaEventRecord(e, s);
+}
+
+int ensure_start(vgrid_t *g, int64_t N) {
+    if (N <= g->start_cap) return VGRID_OK;
+    if (g->d_start) {
+        cudaFree(g->d_start);
+        g->device_bytes -= g->start_cap * (int64_t)sizeof(int32_t);
+        g->d_start = nullptr;
+        g->start_cap = 0;
+    }
+    int rc = dmalloc(&g->d_start, (size_t)N, g->device_bytes);
+    if (rc) return rc;
+    g->start_cap = N;
+    return VGRID_OK;
+}
+
+int ensure_scan(vgrid_t *g, int64_t N) {
+    const int64_t need = vg::scan_tmp_elems(N);
+    if (need <= g->scan_cap) return VGRID_OK;
+    if (g->d_scan) {
+        cudaFree(g->d_scan);
+        g->device_bytes -= g->scan_cap * (int64_t)sizeof(int64_t);
+        g->d_scan = nullptr;
+        g->scan_cap = 0;
+    }
+    int rc = dmalloc(&g->d_scan, (size_t)need, g->device_bytes);
+    if (rc) return rc;
+    g->scan_cap = need;
+    return VGRID_OK;
+}
+
+// persistent grid size for a trace kernel
+int persistent_blocks(const void *fn, const vgrid_launch &l, int sms, int64_t work_items) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, l.block, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    if (l.blocks_per_sm > 0 && l.blocks_per_sm < per_sm) per_sm = l.blocks_per_sm;
+    int64_t blocks = (int64_t)per_sm * sms;
+    const int64_t need = (work_items * l.lanes_per_ray + l.block - 1) / l.block;
+    if (need < blocks) blocks = need > 0 ? need : 1;
+    return (int)blocks;
+}
+
+int launch_trace(const void *fn, const vgrid_launch &l, int sms, int64_t total, vg::TraceArgs &a, cudaStream_t s) {
+    if (!fn) return fail(VGRID_ERR_ARG, "no kernel for this precision/mode");
+    const int blocks = persistent_blocks(fn, l, sms, total);
+    void *args[] = {&a};
+    VG_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(l.block), args, 0, s));
+    return VGRID_OK;
+}
+
+int read_stats(StatsDev *d, vgrid_stats *out, cudaStream_t s, StatsDev *host_copy = nullptr) {
+    StatsDev h{};
+    VG_CUDA(cudaMemcpyAsync(&h, d, sizeof(StatsDev), cudaMemcpyDeviceToHost, s));
+    VG_CUDA(cudaStreamSynchronize(s));
+    if (out) {
+        out->rays = (int64_t)h.rays;
+        out->crossings = (int64_t)h.crossings;
+        out->decisions = (int64_t)h.decisions;
+        out->rechecks = (int64_t)h.rechecks;
+        out->fallbacks = (int64_t)h.fallbacks;
+        out->zero_steps = (int64_t)h.zero_steps;
+        out->step_limit = (int64_t)h.step_limit;
+        out->outside = (int64_t)h.outside;
+    }
+    if (host_copy) *host_copy = h;
+    if (h.bad_dir) return fail(VGRID_ERR_ARG, std::to_string(h.bad_dir) + " ray directions are not unit vectors");
+    if (h.step_limit) return fail(VGRID_ERR_STEP_LIMIT, std::to_string(h.step_limit) + " rays hit the step limit");
+    return VGRID_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_t *cell, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (N < 0 || (N > 0 && (!pts || !cell))) return fail(VGRID_ERR_ARG, "bad points or output");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (N == 0) return VGRID_OK;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_start(g, N);
+    if (rc) return rc;
+    RaySetDev set{pts, pts, nullptr, nullptr, g->d_start, N, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, precision == VGRID_FP32_RECHECK, cell, g->sms, s));
+    return VGRID_OK;
+}
+
+int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, int output, void *tau,
+                int64_t *seg_off, int32_t *seg_cell, void *seg_len, int64_t seg_capacity, int32_t *ray_status,
+                vgrid_stats *stats, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (output != VGRID_TAU && output != VGRID_SEGMENTS) return fail(VGRID_ERR_ARG, "bad output");
+    if (N < 0 || (N > 0 && (!origin || !dir))) return fail(VGRID_ERR_ARG, "bad rays");
+    if (output == VGRID_TAU && N > 0 && !tau) return fail(VGRID_ERR_ARG, "tau is NULL");
+    if (output == VGRID_SEGMENTS && !seg_off) return fail(VGRID_ERR_ARG, "seg_off is NULL");
+    if (seg_capacity < 0) return fail(VGRID_ERR_ARG, "negative capacity");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) {
+        if (output == VGRID_SEGMENTS) VG_CUDA(cudaMemsetAsync(seg_off, 0, sizeof(int64_t), s));
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return VGRID_OK;
+    }
+    int rc = ensure_start(g, N);
+    if (rc) return rc;
+    const int fp64 = precision == VGRID_FP64;
+    const vg::KernelSet &ks = kernels(g->launch.lanes_per_ray);
+    RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
+    mark(g, 0, 0, s);
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, !fp64, nullptr, g->sms, s));
+    mark(g, 0, 1, s);
+    vg::TraceArgs a{};
+    a.grids = g->d_desc;
+    a.sets = g->d_set;
+    a.nsets = 1;
+    a.total = N;
+    a.queue = g->d_queue;
+    a.stats = g->d_stats;
+    if (output == VGRID_TAU) {
+        mark(g, 1, 0, s);
+        if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], g->launch, g->sms, N, a, s))) return rc;
+        mark(g, 1, 1, s);
+        if (stats) return read_stats(g->d_stats, stats, s);
+        return VGRID_OK;
+    }
+    // segment lists: count, prefix sum, capacity check, fill
+    if ((rc = ensure_scan(g, N))) return rc;
+    a.seg_off = seg_off;
+    mark(g, 1, 0, s);
+    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_COUNT], g->launch, g->sms, N, a, s))) return rc;
+    mark(g, 1, 1, s);
+    VG_CUDA(vg::launch_exclusive_scan(seg_off, N, g->d_scan, s));
+    int64_t total = 0;
+    VG_CUDA(cudaMemcpyAsync(&total, seg_off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VG_CUDA(cudaStreamSynchronize(s));
+    if (total > seg_capacity || (total > 0 && (!seg_cell || !seg_len)))
+        return fail(VGRID_ERR_CAPACITY, "segment buffers hold " + std::to_string(seg_capacity) + ", need " +
+                                            std::to_string(total));
+    VG_CUDA(vg::launch_prepare(nullptr, set, g->d_queue, g->d_stats, s));
+    a.seg_cell = seg_cell;
+    a.seg_len = seg_len;
+    a.seg_cap = total;
+    mark(g, 1, 0, s);
+    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_FILL], g->launch, g->sms, N, a, s))) return rc;
+    mark(g, 1, 1, s);
+    return read_stats(g->d_stats, stats, s);
+}
+
+int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *dL_dtau,
+                     float *dL_drho, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (N < 0 || (N > 0 && (!origin || !dir || !dL_dtau || !dL_drho))) return fail(VGRID_ERR_ARG, "bad arguments");
+    if (N == 0) return VGRID_OK;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_start(g, N);
+    if (rc) return rc;
+    RaySetDev set{origin, dir, nullptr, nullptr, g->d_start, N, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
+    mark(g, 0, 0, s);
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, 1, nullptr, g->sms, s));
+    mark(g, 0, 1, s);
+    vg::TraceArgs a{};
+    a.grids = g->d_desc;
+    a.sets = g->d_set;
+    a.nsets = 1;
+    a.total = N;
+    a.queue = g->d_queue;
+    a.stats = g->d_stats;
+    a.dL_dtau = dL_dtau;
+    a.dL_drho = dL_drho;
+    mark(g, 1, 0, s);
+    rc = launch_trace(kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_GRAD], g->launch, g->sms, N, a, s);
+    mark(g, 1, 1, s);
+    return rc;
+}
+
+int vgrid_enable_timing(vgrid_t *g, int enable) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    DeviceGuard dg(g->device);
+    g->timing = enable != 0;
+    g->n_loc = g->n_trace = 0;
+    return VGRID_OK;
+}
+
+int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *launches) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    DeviceGuard dg(g->device);
+    double tl = 0, tt = 0;
+    for (int which = 0; which < 2; which++) {
+        auto &v = which == 0 ? g->ev_loc : g->ev_trace;
+        size_t n = which == 0 ? g->n_loc : g->n_trace;
+        for (size_t i = 0; i < n; i++) {
+            VG_CUDA(cudaEventSynchronize(v[i][1]));
+            float ms = 0;
+            VG_CUDA(cudaEventElapsedTime(&ms, v[i][0], v[i][1]));
+            (which == 0 ? tl : tt) += ms;
+        }
+    }
+    if (locate_ms) *locate_ms = tl;
+    if (trace_ms) *trace_ms = tt;
+    if (launches) *launches = (int64_t)g->n_trace;
+    g->n_loc = g->n_trace = 0;
+    return VGRID_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+
+static void free_batch(vgrid_batch_t *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    void *ptrs[] = {b->d_grids, b->d_sets, b->d_start, b->d_queue, b->d_stats};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
+int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *launch, vgrid_batch_t **out) {
+    if (!out) return fail(VGRID_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!sets || G < 1) return fail(VGRID_ERR_ARG, "need at least one ray set");
+    if (launch && (!valid_lpr(launch->lanes_per_ray) || launch->block < 32 || launch->block > 256 ||
+                   launch->block % 32 || launch->blocks_per_sm < 0))
+        return fail(VGRID_ERR_ARG, "bad launch shape");
+    const int dev = sets[0].grid ? sets[0].grid->device : 0;
+    std::vector<const vgrid_t *> uniq;
+    std::vector<GridDev> descs;
+    std::vector<RaySetDev> rs(G);
+    int64_t total = 0;
+    for (int32_t i = 0; i < G; i++) {
+        const vgrid_rayset &q = sets[i];
+        if (!q.grid || q.grid->device < 0 || q.n < 0 || (q.n > 0 && (!q.origin || !q.dir || !q.tau)))
+            return fail(VGRID_ERR_ARG, "bad ray set " + std::to_string(i));
+        if (q.grid->device != dev) return fail(VGRID_ERR_ARG, "all grids of a batch must live on one device");
+        int gi = (int)(std::find(uniq.begin(), uniq.end(), q.grid) - uniq.begin());
+        if (gi == (int)uniq.size()) {
+            uniq.push_back(q.grid);
+            descs.push_back(q.grid->hd);
+        }
+        rs[i] = RaySetDev{q.origin, q.dir, q.tau, q.status, nullptr, q.n, total, gi, 0};
+        total += q.n;
+    }
+    DeviceGuard dg(dev);
+    vgrid_batch_t *b = new vgrid_batch();
+    b->device = dev;
+    b->G = G;
+    b->total = total;
+    b->ngrids = (int)uniq.size();
+    if (launch) b->launch = *launch;
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t bytes = 0;
+    int rc;
+    if ((rc = dmalloc(&b->d_grids, descs.size(), bytes)) || (rc = dmalloc(&b->d_sets, (size_t)G, bytes)) ||
+        (rc = dmalloc(&b->d_start, (size_t)std::max<int64_t>(total, 1), bytes)) ||
+        (rc = dmalloc(&b->d_queue, 1, bytes)) || (rc = dmalloc(&b->d_stats, 1, bytes))) {
+        free_batch(b);
+        return rc;
+    }
+    for (int32_t i = 0; i < G; i++) rs[i].start = b->d_start + rs[i].first;
+    cudaError_t e = cudaMemcpy(b->d_grids, descs.data(), sizeof(GridDev) * descs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_sets, rs.data(), sizeof(RaySetDev) * G, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return fail(VGRID_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e));
+    }
+    *out = b;
+    return VGRID_OK;
+}
+
+static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
+    RaySetDev none{};
+    VG_CUDA(vg::launch_prepare(nullptr, none, b->d_queue, b->d_stats, s));
+    VG_CUDA(vg::launch_locate(b->d_grids, b->d_sets, b->G, b->total, 1, nullptr, b->sms, s));
+    vg::TraceArgs a{};
+    a.grids = b->d_grids;
+    a.sets = b->d_sets;
+    a.nsets = b->G;
+    a.total = b->total;
+    a.queue = b->d_queue;
+    a.stats = b->d_stats;
+    return launch_trace(kernels(b->launch.lanes_per_ray).fn[0][vg::MODE_TAU], b->launch, b->sms, b->total, a, s);
+}
+
+int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_stream_t stream) {
+    if (!b) return fail(VGRID_ERR_ARG, "null batch");
+    DeviceGuard dg(b->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (use_graph) {
+        if (!s) return fail(VGRID_ERR_ARG, "graph replay needs a non-default stream");
+        if (!b->exec) {
+            VG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int rc = batch_issue(b, s);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (rc) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(VGRID_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            b->graph = graph;
+            VG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        }
+        VG_CUDA(cudaGraphLaunch(b->exec, s));
+    } else {
+        int rc = batch_issue(b, s);
+        if (rc) return rc;
+    }
+    if (stats) return read_stats(b->d_stats, stats, s);
+    return VGRID_OK;
+}
+
+int vgrid_batch_destroy(vgrid_batch_t *b) {
+    if (!b) return VGRID_OK;
+    DeviceGuard dg(b->device);
+    free_batch(b);
+    return VGRID_OK;
+}
+
+}  // extern "C"

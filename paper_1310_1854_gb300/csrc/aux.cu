@@ -1,0 +1,169 @@
+// Auxiliary kernels of libvgrid: start-cell location (C(r), Sect. 2.3),
+// per-call set-up, density reordering and the prefix sum that turns
+// per-ray segment counts into offsets.
+#include "kernels.h"
+#include "trace.cuh"
+
+namespace vg {
+
+// Write the ray-set descriptor and clear the work counter and statistics
+// (one thread; the descriptor travels as a kernel argument, so the call is
+// stream-ordered and needs no host staging buffer).
+__global__ void prepare_kernel(RaySetDev *d_set, RaySetDev set, unsigned long long *queue, StatsDev *stats) {
+    if (d_set) *d_set = set;
+    *queue = 0ull;
+    unsigned long long *s = reinterpret_cast<unsigned long long *>(stats);
+    for (int i = 0; i < (int)(sizeof(StatsDev) / sizeof(unsigned long long)); i++) s[i] = 0ull;
+}
+
+__global__ void put_grid_kernel(GridDev *d, GridDev g) { *d = g; }
+
+cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s) {
+    put_grid_kernel<<<1, 1, 0, s>>>(d, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long long *queue, StatsDev *stats,
+                           cudaStream_t s) {
+    prepare_kernel<<<1, 1, 0, s>>>(d_set, set, queue, stats);
+    return cudaGetLastError();
+}
+
+// C(r0) for every ray of every set: internal id into sets[].start, and the
+// caller's id into out_caller (if given).
+__global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const RaySetDev *sets, int nsets,
+                                                     int64_t total, int fp32, int32_t *out_caller, StatsDev *stats) {
+    unsigned rechecks = 0;
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int set = find_set(sets, nsets, w);
+        const RaySetDev &rs = sets[set];
+        const int64_t li = w - rs.first;
+        const GridDev *gp = grids + rs.grid;
+        const double *o = rs.origin + 3 * li;
+        int re = 0;
+        const int m = locate_point(gp, __ldg(o), __ldg(o + 1), __ldg(o + 2), fp32 != 0, &re);
+        rechecks += re;
+        rs.start[li] = m;
+        if (out_caller) out_caller[w] = m >= 0 ? __ldg(&gp->perm[m]) : -1;
+    }
+    if (stats) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, rechecks);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&stats->rechecks, (unsigned long long)v);
+    }
+}
+
+cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int fp32,
+                          int32_t *out_caller, int sms, cudaStream_t s) {
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
+    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, fp32, out_caller, nullptr);
+    return cudaGetLastError();
+}
+
+__global__ void permute_density_kernel(const float *__restrict__ rho_caller, const int32_t *__restrict__ perm,
+                                       int64_t M, float *__restrict__ rho_internal) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        rho_internal[i] = __ldg(&rho_caller[__ldg(&perm[i])]);
+}
+
+cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, int64_t M, float *rho_internal,
+                                   cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    int64_t blocks = (M + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, M, rho_internal);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// exclusive prefix sum over int64 (three passes: tiles, tile totals, fix-up)
+// ---------------------------------------------------------------------------
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t *warp_sums, int64_t &block_total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    block_total = warp_sums[(blockDim.x >> 5) - 1];
+    const int64_t before = wid > 0 ? warp_sums[wid - 1] : 0;
+    const int64_t r = before + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_tiles_kernel(int64_t *data, int64_t n, int64_t *tile_sums) {
+    __shared__ int64_t ws[32];
+    const int64_t base = blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = base + i < n ? data[base + i] : 0;
+        sum += v[i];
+    }
+    int64_t total;
+    int64_t run = block_exclusive_scan(sum, ws, total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (base + i < n) data[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(int64_t *tile_sums, int64_t ntiles, int64_t *out_total) {
+    __shared__ int64_t ws[32];
+    int64_t carry = 0;
+    for (int64_t b = 0; b < ntiles; b += kScanThreads) {
+        const int64_t i = b + threadIdx.x;
+        const int64_t v = i < ntiles ? tile_sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exclusive_scan(v, ws, total);
+        if (i < ntiles) tile_sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *out_total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_fix_kernel(int64_t *data, int64_t n, const int64_t *tile_sums) {
+    const int64_t add = tile_sums[blockIdx.x];
+    const int64_t base = blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++)
+        if (base + i < n) data[base + i] += add;
+}
+
+int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t s) {
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 0) {
+        return cudaMemsetAsync(data, 0, sizeof(int64_t), s);
+    }
+    scan_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, tmp);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(tmp, tiles, data + n);
+    scan_fix_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, tmp);
+    return cudaGetLastError();
+}
+
+}  // namespace vg

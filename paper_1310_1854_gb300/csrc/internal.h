@@ -1,0 +1,84 @@
+// Internal declarations shared by the host builder, the C-ABI layer and the
+// CUDA kernels of libvgrid. Not part of the public interface (include/vgrid.h).
+#pragma once
+
+#include <vector_types.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace vg {
+
+// Host results of the cell construction, in the library's internal cell order.
+struct CellsOut {
+    std::vector<int64_t> off;   // CSR offsets, M + 1
+    std::vector<int32_t> idx;   // neighbour ids (internal) and walls -1..-6
+    std::vector<double> vol;    // cell volumes
+    std::vector<double> bbox;   // 6 per cell
+};
+
+struct BlocksOut {
+    int32_t dim[3];
+    std::vector<int64_t> off;   // K + 1
+    std::vector<int32_t> idx;   // internal cell ids
+};
+
+int build_cells(const double *sites, int64_t M, const double *box, int threads, CellsOut &out, std::string &err);
+void morton_order(const double *sites, int64_t M, const double *box, std::vector<int32_t> &perm);
+void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M, double blocks_per_site,
+                  BlocksOut &out);
+
+}  // namespace vg
+
+// ---------------------------------------------------------------------------
+// Device-side view of one grid. Plain data, passed by value to kernels or
+// stored in an array for batched launches.
+//
+// site[i]  float4 (x, y, z, bits of nbr offset) for internal cell i. The
+//          neighbour list of cell i starts at nbr[off]: nbr[off] = count c,
+//          nbr[off + 1 .. off + c] = neighbour ids (internal) or walls -1..-6,
+//          then padding (-8) up to a multiple of 4 ints, so every list starts
+//          on a 16-byte boundary and can be read as int4.
+// rho[i]   density of internal cell i.
+// perm[i]  caller's id of internal cell i.
+// blk_*    block lists of Sect. 2.3 (internal ids).
+// ---------------------------------------------------------------------------
+struct GridDev {
+    const float4 *site;
+    const int32_t *nbr;
+    const float *rho;
+    const int32_t *perm;
+    const int32_t *blk_off;
+    const int32_t *blk_idx;
+    double lo[3], hi[3];      // domain box
+    double bscale[3];         // blocks per unit length along each axis
+    int32_t bdim[3];
+    int32_t M;
+    float kappa;
+    float pad0;
+    double eps64;             // epsilon nudge, float64 path
+    double eps32;             // epsilon nudge, float32 path
+    double scale;             // max |coordinate| of the box + diagonal
+    int64_t max_steps;
+};
+
+// A batch work descriptor: rays of one grid.
+struct RaySetDev {
+    const double *origin;
+    const double *dir;
+    void *tau;                // float (float32 form) or double (float64 form), nullable
+    int32_t *status;          // nullable
+    int32_t *start;           // located start cells (internal) - work buffer
+    int64_t n;
+    int64_t first;            // global index of the first ray of this set
+    int32_t grid;             // index into the GridDev array
+    int32_t pad;
+};
+
+// Counters accumulated on the device; mirrors vgrid_stats.
+struct StatsDev {
+    unsigned long long rays, crossings, decisions, rechecks, fallbacks, zero_steps, step_limit, outside, bad_dir;
+};
+
+#define VG_PAD_ID (-8)

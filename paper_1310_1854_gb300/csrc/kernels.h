@@ -1,0 +1,51 @@
+// Kernel tables and host-callable launch helpers of libvgrid (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace vg {
+
+enum { MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_GRAD = 3 };
+
+struct TraceArgs {
+    const GridDev *grids;     // one descriptor per grid
+    const RaySetDev *sets;    // one per (grid, rays) set
+    int32_t nsets;
+    int64_t total;            // rays over all sets
+    unsigned long long *queue;
+    StatsDev *stats;
+    int64_t *seg_off;         // count mode: counts per ray; fill mode: offsets
+    int32_t *seg_cell;
+    void *seg_len;            // float or double
+    int64_t seg_cap;          // entries of seg_cell / seg_len; writes beyond are dropped
+    const float *dL_dtau;
+    float *dL_drho;
+};
+
+
+// fn[fp64][mode]: trace kernels of one lanes-per-ray value (nullptr if absent)
+struct KernelSet {
+    const void *fn[2][4];
+};
+
+void kernel_table_lpr1(KernelSet &k);
+void kernel_table_lpr2(KernelSet &k);
+void kernel_table_lpr4(KernelSet &k);
+void kernel_table_lpr8(KernelSet &k);
+
+// auxiliary kernels (aux.cu)
+cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s);
+cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long long *queue, StatsDev *stats,
+                           cudaStream_t s);
+cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int fp32,
+                          int32_t *out_caller, int sms, cudaStream_t s);
+cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, int64_t M, float *rho_internal,
+                                   cudaStream_t s);
+// exclusive scan of counts[0..n-1] (int64) into off[0..n]; tmp holds
+// scan_tmp_elems(n) int64 values
+int64_t scan_tmp_elems(int64_t n);
+cudaError_t launch_exclusive_scan(int64_t *counts_to_off, int64_t n, int64_t *tmp, cudaStream_t s);
+
+}  // namespace vg

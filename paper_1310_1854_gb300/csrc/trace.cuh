@@ -1,0 +1,678 @@
+// Device code of the straight-path traversal (Sect. 2.2 of Camps, Baes &
+// Saftly 2013) and of C(r) (Sect. 2.3), shared by the kernel instantiations.
+//
+// Work mapping: a persistent grid of warps; each warp is split into groups of
+// LPR lanes, one ray per group. A group takes a new ray from a global counter
+// as soon as its ray ends, so rays of very different length do not leave
+// lanes idle. Inside a crossing the group's lanes stride over the current
+// cell's neighbour list (read as int4 chunks) and reduce the exit with
+// shuffles.
+//
+// Two arithmetic forms of the exit search (Sect. 2.2, steps 1-3, Eq. 1-5):
+//  * float64: Eq. 4 and Eq. 5 evaluated as written, in the same operation
+//    order as a plain C implementation with contraction disabled, the
+//    current point updated as r <- r + s k.
+//  * float32 with recheck: each plane test runs in float32 in the frame of
+//    the current site, together with a rigorous bound on its rounding error.
+//    The exit is accepted when the upper bound of the winner lies below the
+//    lower bound of every other candidate; otherwise that one crossing is
+//    recomputed with the float64 form. The ray parameter t is kept as an
+//    unevaluated float pair, so no float64 work is needed per crossing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace vg {
+
+enum { RAY_OK = 0, RAY_OUTSIDE = 1, RAY_STEP_LIMIT = 2, RAY_BAD_DIR = 3 };
+
+constexpr int kZeroRunMax = 4;                      // consecutive zero-length steps before a nudge
+constexpr int kNone = 0x7fffffff;                   // "no candidate"
+constexpr float kU = 5.9604644775390625e-8f;        // 2^-24, unit roundoff of float32
+constexpr float kU2 = 3.552713678800501e-15f;       // 2^-48
+constexpr float kCDen = 6.0f * kU;                  // |den~ - den| <= kCDen |n~|_1
+constexpr float kCA = 4.0f * kU;                    // |num~ - num| <= |n|_1 (kCA |n|_1 + kCB |r|_1 + 2 e_r)
+constexpr float kCB = 8.0f * kU;
+constexpr float kDivLo = 0.99999952316284180f;      // 1 - 2^-21: covers 2 ulp of __fdividef
+constexpr float kDivHi = 1.00000047683715820f;      // 1 + 2^-21
+
+
+// Grid arrays the inner loop touches, kept in registers.
+struct Hot {
+    const float4 *__restrict__ site;
+    const int32_t *__restrict__ nbr;
+    const int32_t *__restrict__ perm;
+};
+
+// ---------------------------------------------------------------------------
+// float pairs (value = hi + lo)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (hi, lo) += x
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    e = __fadd_rn(e, lo);
+    fast_two_sum(s, e, hi, lo);
+}
+
+__device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+__device__ __forceinline__ void ff_add_double(float &hi, float &lo, double x) {
+    float xh, xl, s, e;
+    split_double(x, xh, xl);
+    two_sum(hi, xh, s, e);
+    e = __fadd_rn(__fadd_rn(e, lo), xl);
+    fast_two_sum(s, e, hi, lo);
+}
+
+// r = (R0 + t K) - p along one axis, to within 2u|r| + 16 u^2 (|R0| + t + |p|):
+// R0_hi - p and t_hi K_hi are formed exactly, the small terms added last.
+__device__ __forceinline__ float local_coord(float R0h, float R0l, float Kh, float Kl, float th, float tl, float p) {
+    float ah, al;
+    two_sum(R0h, -p, ah, al);
+    const float bh = __fmul_rn(th, Kh);
+    const float bl = __fmaf_rn(th, Kh, -bh);
+    float small = __fmaf_rn(th, Kl, R0l);
+    small = __fmaf_rn(tl, Kh, small);
+    small = __fadd_rn(small, __fadd_rn(al, bl));
+    return __fadd_rn(__fadd_rn(ah, bh), small);
+}
+
+// ---------------------------------------------------------------------------
+// float64 exit search (Eq. 4, Eq. 5), lexicographic (s, id) minimum; walls
+// keep their negative ids, cells compare by the caller's index on exact ties
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool better64(const Hot &h, double s, int j, double bs, int bj) {
+    if (bj == kNone) return true;
+    if (s < bs) return true;
+    if (s > bs) return false;
+    const int kj = j < 0 ? j : __ldg(&h.perm[j]);
+    const int kb = bj < 0 ? bj : __ldg(&h.perm[bj]);
+    return kj < kb;
+}
+
+// One candidate: bisector of sites m and j (Eq. 1-4) or wall j < 0 (Eq. 5).
+// Returns false if it is not a candidate (n.k <= 0, or padding).
+__device__ __forceinline__ bool plane64(const Hot &h, const GridDev *gp, int j, double pmx, double pmy, double pmz,
+                                        const double *r, const double *k, double &s) {
+    if (j >= 0) {
+        const float4 q = __ldg(&h.site[j]);
+        const double px = (double)q.x, py = (double)q.y, pz = (double)q.z;
+        const double nx = __dsub_rn(px, pmx), ny = __dsub_rn(py, pmy), nz = __dsub_rn(pz, pmz);
+        const double den = __dadd_rn(__dadd_rn(__dmul_rn(nx, k[0]), __dmul_rn(ny, k[1])), __dmul_rn(nz, k[2]));
+        if (!(den > 0.0)) return false;
+        const double wx = __dsub_rn(__dmul_rn(__dadd_rn(px, pmx), 0.5), r[0]);
+        const double wy = __dsub_rn(__dmul_rn(__dadd_rn(py, pmy), 0.5), r[1]);
+        const double wz = __dsub_rn(__dmul_rn(__dadd_rn(pz, pmz), 0.5), r[2]);
+        double num = __dadd_rn(__dadd_rn(__dmul_rn(nx, wx), __dmul_rn(ny, wy)), __dmul_rn(nz, wz));
+        if (num < 0.0) num = 0.0;
+        s = __ddiv_rn(num, den);
+        return true;
+    }
+    if (j < -6) return false;
+    const int w = -j - 1, axis = w >> 1, hi = w & 1;
+    const double kc = k[axis];
+    if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
+    const double bound = hi ? gp->hi[axis] : gp->lo[axis];
+    const double v = __ddiv_rn(__dsub_rn(bound, r[axis]), kc);
+    s = v < 0.0 ? 0.0 : v;
+    return true;
+}
+
+template <int LPR>
+__device__ __forceinline__ void exit64(const Hot &h, const GridDev *gp, int off, double pmx, double pmy, double pmz,
+                                       const double *r, const double *k, unsigned gmask, int gl, double &bs,
+                                       int &bj) {
+    const int cnt = __ldg(&h.nbr[off]);
+    bs = 0.0;
+    bj = kNone;
+    for (int p = 1 + gl; p <= cnt; p += LPR) {
+        const int j = __ldg(&h.nbr[off + p]);
+        double s;
+        if (plane64(h, gp, j, pmx, pmy, pmz, r, k, s) && better64(h, s, j, bs, bj)) {
+            bs = s;
+            bj = j;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < LPR; o <<= 1) {
+        const double os = __shfl_xor_sync(gmask, bs, o);
+        const int oj = __shfl_xor_sync(gmask, bj, o);
+        if (oj != kNone && better64(h, os, oj, bs, bj)) {
+            bs = os;
+            bj = oj;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// C(r): nearest site among the candidates of r's block (Sect. 2.3)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ bool inside(const GridDev *gp, double x, double y, double z) {
+    return x >= gp->lo[0] && x <= gp->hi[0] && y >= gp->lo[1] && y <= gp->hi[1] && z >= gp->lo[2] &&
+           z <= gp->hi[2];
+}
+
+__device__ __forceinline__ int block_of(const GridDev *gp, double x, double y, double z) {
+    int i = (int)__dmul_rn(__dsub_rn(x, gp->lo[0]), gp->bscale[0]);
+    int j = (int)__dmul_rn(__dsub_rn(y, gp->lo[1]), gp->bscale[1]);
+    int k = (int)__dmul_rn(__dsub_rn(z, gp->lo[2]), gp->bscale[2]);
+    i = max(0, min(i, gp->bdim[0] - 1));
+    j = max(0, min(j, gp->bdim[1] - 1));
+    k = max(0, min(k, gp->bdim[2] - 1));
+    return (i * gp->bdim[1] + j) * gp->bdim[2] + k;
+}
+
+// float64 scan of a block list, distances as ((dx dx + dy dy) + dz dz)
+static __device__ __noinline__ int locate64(const GridDev *gp, double x, double y, double z, int beg, int end) {
+    const float4 *site = gp->site;
+    const int32_t *perm = gp->perm;
+    int best = -1;
+    double bd = 0.0;
+    for (int i = beg; i < end; i++) {
+        const int c = __ldg(&gp->blk_idx[i]);
+        const float4 q = __ldg(&site[c]);
+        const double dx = __dsub_rn(x, (double)q.x), dy = __dsub_rn(y, (double)q.y), dz = __dsub_rn(z, (double)q.z);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        if (best < 0 || d2 < bd || (d2 == bd && __ldg(&perm[c]) < __ldg(&perm[best]))) {
+            bd = d2;
+            best = c;
+        }
+    }
+    return best;
+}
+
+// Nearest site (internal id), -1 outside the closed box. With fp32 the
+// squared distances are float32 and the winner is accepted when
+// D2 - E(D2) > D1 + E(D1), E(D) = u (10 D + 4 X sqrt D), X = max |x_c|,
+// which bounds the rounding error of a float32 squared distance; otherwise
+// the list is rescanned in float64. *rechecked is set when that happened.
+static __device__ __noinline__ int locate_point(const GridDev *gp, double x, double y, double z, bool fp32,
+                                         int *rechecked) {
+    if (!inside(gp, x, y, z)) return -1;
+    const int b = block_of(gp, x, y, z);
+    const int beg = __ldg(&gp->blk_off[b]), end = __ldg(&gp->blk_off[b + 1]);
+    if (fp32) {
+        const float4 *site = gp->site;
+        const int32_t *blk = gp->blk_idx;
+        const float xf = __double2float_rn(x), yf = __double2float_rn(y), zf = __double2float_rn(z);
+        const float X = fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
+        float D1 = __int_as_float(0x7f800000), D2 = D1;
+        int i1 = -1;
+        for (int i = beg; i < end; i++) {
+            const int c = __ldg(&blk[i]);
+            const float4 q = __ldg(&site[c]);
+            const float dx = __fsub_rn(xf, q.x), dy = __fsub_rn(yf, q.y), dz = __fsub_rn(zf, q.z);
+            const float D = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            if (D < D1) {
+                D2 = D1;
+                D1 = D;
+                i1 = c;
+            } else if (D < D2) {
+                D2 = D;
+            }
+        }
+        if (end - beg <= 1) return i1;
+        const float s1 = sqrtf(D1), s2 = sqrtf(D2);
+        const float E1 = 1.0001f * kU * __fmaf_rn(10.0f, D1, 4.0f * X * s1);
+        const float E2 = 1.0001f * kU * __fmaf_rn(10.0f, D2, 4.0f * X * s2);
+        if (s2 > 8.0f * kU * X && __fsub_rd(D2, E2) > __fadd_ru(D1, E1)) return i1;
+        if (rechecked) *rechecked = 1;
+    }
+    return locate64(gp, x, y, z, beg, end);
+}
+
+// ---------------------------------------------------------------------------
+// float32 exit search with error bounds (one group)
+// ---------------------------------------------------------------------------
+
+struct Cand32 {
+    float L1, L2;        // smallest and second smallest lower bound
+    int j1;              // id with the smallest lower bound (internal), kNone if none
+    float num, den, dnum, dden;
+    float4 q;            // site record of j1
+};
+
+// Bisector of the current site (origin of the local frame) and site q.
+// Bounds (in units of u = 2^-24, for n~ = fl(q - p), r~ within 2u|r| + e_r):
+//   |den~ - n.k|  <= 6 |n~|_1                       (two roundings of n, three of the dot)
+//   |num~ - n.w|  <= |n~|_1 (4 |n~|_1 + 8 |r~|_1) + 2 e_r |n~|_1, w = n/2 - r
+// Planes with den~ <= -|den error| face away for certain (R2); the others
+// get the lower bound max(num~ - dnum, 0) / (den~ + dden) on s (Eq. 4).
+__device__ __forceinline__ void consider32(int j, float4 q, float pmx, float pmy, float pmz, float rx, float ry,
+                                           float rz, float rr, float Kx, float Ky, float Kz, Cand32 &c) {
+    const float nx = __fsub_rn(q.x, pmx), ny = __fsub_rn(q.y, pmy), nz = __fsub_rn(q.z, pmz);
+    const float den = __fmaf_rn(nz, Kz, __fmaf_rn(ny, Ky, __fmul_rn(nx, Kx)));
+    const float n1 = __fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz));
+    const float dden = __fmul_rn(kCDen, n1);
+    if (den > -dden) {
+        const float wx = __fmaf_rn(0.5f, nx, -rx), wy = __fmaf_rn(0.5f, ny, -ry), wz = __fmaf_rn(0.5f, nz, -rz);
+        const float num = __fmaf_rn(nz, wz, __fmaf_rn(ny, wy, __fmul_rn(nx, wx)));
+        const float dnum = __fmul_rn(n1, __fmaf_rn(kCA, n1, rr));
+        const float num_lo = fmaxf(__fsub_rd(num, dnum), 0.0f);
+        const float den_hi = __fadd_ru(den, dden);
+        const float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
+        if (lower < c.L1) {
+            c.L2 = c.L1;
+            c.L1 = lower;
+            c.j1 = j;
+            c.num = num;
+            c.den = den;
+            c.dnum = dnum;
+            c.dden = dden;
+            c.q = q;
+        } else if (lower < c.L2) {
+            c.L2 = lower;
+        }
+    }
+}
+
+template <int LPR>
+__device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float pmy, float pmz, float rx, float ry,
+                                       float rz, float rr, float Kx, float Ky, float Kz, unsigned gmask, int gl,
+                                       int gbase, Cand32 &c) {
+    const int4 *lst = reinterpret_cast<const int4 *>(h.nbr + off);
+    int4 v = __ldg(lst + gl);  // every list owns >= 1 chunk; the array is padded past its end
+    const int cnt = LPR == 1 ? v.x : __shfl_sync(gmask, v.x, gbase);
+    const int nch = (cnt + 4) >> 2;
+    c.L1 = __int_as_float(0x7f800000);
+    c.L2 = c.L1;
+    c.j1 = kNone;
+    for (int ch = gl; ch < nch; ch += LPR) {
+        if (ch != gl) v = __ldg(lst + ch);
+        const int p = ch * 4;
+        const int j0 = (p >= 1 && p <= cnt) ? v.x : -8;
+        const int j1 = (p + 1 <= cnt) ? v.y : -8;
+        const int j2 = (p + 2 <= cnt) ? v.z : -8;
+        const int j3 = (p + 3 <= cnt) ? v.w : -8;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 q0 = j0 >= 0 ? __ldg(&h.site[j0]) : z4;
+        const float4 q1 = j1 >= 0 ? __ldg(&h.site[j1]) : z4;
+        const float4 q2 = j2 >= 0 ? __ldg(&h.site[j2]) : z4;
+        const float4 q3 = j3 >= 0 ? __ldg(&h.site[j3]) : z4;
+        if (j0 >= 0) consider32(j0, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        if (j1 >= 0) consider32(j1, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        if (j2 >= 0) consider32(j2, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        if (j3 >= 0) consider32(j3, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+    }
+    if (LPR > 1) {
+        int win = gl;
+#pragma unroll
+        for (int o = 1; o < LPR; o <<= 1) {
+            const float oL1 = __shfl_xor_sync(gmask, c.L1, o);
+            const float oL2 = __shfl_xor_sync(gmask, c.L2, o);
+            const int ow = __shfl_xor_sync(gmask, win, o);
+            const float nL2 = fminf(fmaxf(c.L1, oL1), fminf(c.L2, oL2));
+            if (oL1 < c.L1 || (oL1 == c.L1 && ow < win)) {
+                c.L1 = oL1;
+                win = ow;
+            }
+            c.L2 = nL2;
+        }
+        const int src = gbase + win;
+        c.j1 = __shfl_sync(gmask, c.j1, src);
+        c.num = __shfl_sync(gmask, c.num, src);
+        c.den = __shfl_sync(gmask, c.den, src);
+        c.dnum = __shfl_sync(gmask, c.dnum, src);
+        c.dden = __shfl_sync(gmask, c.dden, src);
+        c.q.x = __shfl_sync(gmask, c.q.x, src);
+        c.q.y = __shfl_sync(gmask, c.q.y, src);
+        c.q.z = __shfl_sync(gmask, c.q.z, src);
+        c.q.w = __shfl_sync(gmask, c.q.w, src);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int find_set(const RaySetDev *sets, int nsets, int64_t w) {
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&sets[mid].first) <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int LPR, bool FP64, int MODE>
+__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
+    static_assert(LPR == 1 || LPR == 2 || LPR == 4 || LPR == 8, "lanes per ray");
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (LPR - 1);
+    const int gbase = lane & ~(LPR - 1);
+    const unsigned gmask = ((1u << LPR) - 1u) << gbase;
+
+    // per-thread statistics (group leaders count)
+    unsigned st_rays = 0, st_cross = 0, st_dec = 0, st_re = 0, st_fb = 0, st_zero = 0, st_lim = 0, st_out = 0,
+             st_bad = 0;
+
+    int64_t ray = -1;       // global work index; -1 wants a ray, -2 finished
+    int set = 0;
+    int64_t li = 0;         // index within the set
+    const GridDev *gp = a.grids;
+    Hot h{nullptr, nullptr, nullptr};
+    const float *rho = nullptr;
+    float kappa = 1.f;
+    int64_t max_steps = 0;
+    // float64 form: current point and direction
+    double r64[3] = {0, 0, 0}, k64[3] = {0, 0, 0};
+    // float32 form: origin and direction as float pairs, ray parameter t, wall exit
+    float R0h[3], R0l[3], Kh[3], Kl[3];
+    float th = 0.f, tl = 0.f, tmh = 0.f, tml = 0.f, er = 0.f, ewall = 0.f;
+    int wall = -1;
+    int m = -1, off = 0;
+    float pmx = 0.f, pmy = 0.f, pmz = 0.f;
+    float rho_m = 0.f;
+    double tau64 = 0.0;
+    float tau32 = 0.f, tauc = 0.f;
+    float dLr = 0.f;
+    int nseg = 0, zrun = 0, steps = 0, status = 0;
+    int64_t seg_base = 0;
+
+    for (;;) {
+        // ---------------- fetch new rays (one atomic per warp) ----------------
+        const bool need = ray == -1;
+        const unsigned needmask = __ballot_sync(0xffffffffu, need && gl == 0);
+        if (needmask) {
+            const int leader = __ffs(needmask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(a.queue, (unsigned long long)__popc(needmask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const int rank = __popc(needmask & ((1u << gbase) - 1u));
+                const int64_t w = (int64_t)base + rank;
+                ray = w < a.total ? w : -2;
+            }
+        }
+        if (!__any_sync(0xffffffffu, ray != -2)) break;
+
+        if (need && ray >= 0) {
+            // ---------------- start a ray ----------------
+            set = find_set(a.sets, a.nsets, ray);
+            const RaySetDev *rs = &a.sets[set];
+            li = ray - rs->first;
+            gp = a.grids + rs->grid;
+            h.site = gp->site;
+            h.nbr = gp->nbr;
+            h.perm = gp->perm;
+            rho = gp->rho;
+            kappa = gp->kappa;
+            max_steps = gp->max_steps;
+            const double *o = rs->origin + 3 * li;
+            const double *d = rs->dir + 3 * li;
+            for (int c = 0; c < 3; c++) {
+                r64[c] = __ldg(o + c);
+                k64[c] = __ldg(d + c);
+            }
+            nseg = 0;
+            zrun = 0;
+            steps = 0;
+            status = RAY_OK;
+            tau64 = 0.0;
+            tau32 = 0.f;
+            tauc = 0.f;
+            th = tl = 0.f;
+            if (MODE == MODE_FILL) seg_base = a.seg_off[ray];
+            if (MODE == MODE_GRAD) dLr = __ldg(&a.dL_dtau[ray]);
+            const double kk = __dadd_rn(__dadd_rn(__dmul_rn(k64[0], k64[0]), __dmul_rn(k64[1], k64[1])),
+                                        __dmul_rn(k64[2], k64[2]));
+            m = rs->start[li];
+            if (!(fabs(kk - 1.0) <= 2.000001e-6)) {
+                status = RAY_BAD_DIR;
+            } else if (m < 0) {
+                status = RAY_OUTSIDE;
+            } else {
+                const float4 q = __ldg(&h.site[m]);
+                pmx = q.x;
+                pmy = q.y;
+                pmz = q.z;
+                off = __float_as_int(q.w);
+                rho_m = __ldg(&rho[m]);
+                if (!FP64) {
+                    // distance to the wall ahead (Eq. 5 for the walls the ray faces)
+                    double tmax = 1e300;
+                    int wid = -1;
+                    for (int c = 0; c < 3; c++) {
+                        if (k64[c] > 0.0) {
+                            const double t = __ddiv_rn(__dsub_rn(gp->hi[c], r64[c]), k64[c]);
+                            if (t < tmax) { tmax = t; wid = -(2 * c + 2); }
+                        } else if (k64[c] < 0.0) {
+                            const double t = __ddiv_rn(__dsub_rn(gp->lo[c], r64[c]), k64[c]);
+                            if (t < tmax) { tmax = t; wid = -(2 * c + 1); }
+                        }
+                    }
+                    if (tmax < 0.0) tmax = 0.0;
+                    wall = wid;
+                    split_double(tmax, tmh, tml);
+                    for (int c = 0; c < 3; c++) {
+                        split_double(r64[c], R0h[c], R0l[c]);
+                        split_double(k64[c], Kh[c], Kl[c]);
+                    }
+                    er = 16.0f * kU2 * ((float)gp->scale + tmh);
+                    ewall = 16.0f * kU2 * tmh;
+                }
+            }
+            if (status != RAY_OK) {
+                if (gl == 0) {
+                    st_rays++;
+                    if (status == RAY_OUTSIDE) st_out++;
+                    if (status == RAY_BAD_DIR) st_bad++;
+                    if (MODE == MODE_TAU || MODE == MODE_FILL) {
+                        if (rs->tau) {
+                            if (FP64) ((double *)rs->tau)[li] = 0.0;
+                            else ((float *)rs->tau)[li] = 0.f;
+                        }
+                        if (rs->status) rs->status[li] = status;
+                    }
+                    if (MODE == MODE_COUNT) a.seg_off[ray] = 0;
+                }
+                ray = -1;
+                continue;
+            }
+        }
+        if (ray < 0) continue;
+
+        // ---------------- one exit decision ----------------
+        bool ended = false;
+        double s64 = 0.0;      // float64 length (float64 form or recheck)
+        bool from64 = FP64;
+        float len = 0.f;
+        int nxt = kNone;
+        bool have_q = false;
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (FP64) {
+            exit64<LPR>(h, gp, off, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64, nxt);
+        } else {
+            const float rx = local_coord(R0h[0], R0l[0], Kh[0], Kl[0], th, tl, pmx);
+            const float ry = local_coord(R0h[1], R0l[1], Kh[1], Kl[1], th, tl, pmy);
+            const float rz = local_coord(R0h[2], R0l[2], Kh[2], Kl[2], th, tl, pmz);
+            const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
+            const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
+            Cand32 c;
+            exit32<LPR>(h, off, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
+            // the wall ahead is one more candidate: s_w = t_max - t
+            float sw, swl;
+            two_sum(tmh, -th, sw, swl);
+            sw = __fadd_rn(sw, __fadd_rn(swl, __fsub_rn(tml, tl)));
+            const float Ew = __fmaf_rn(3.0f * kU, fabsf(sw), ewall);
+            const float lw = __fsub_rd(sw, Ew);
+            bool wall_wins = false;
+            if (lw < c.L1) {
+                c.L2 = c.L1;
+                c.L1 = lw;
+                wall_wins = true;
+            } else if (lw < c.L2) {
+                c.L2 = lw;
+            }
+            float upper;
+            if (wall_wins) {
+                upper = __fadd_ru(sw, Ew);
+            } else {
+                const float den_lo = __fsub_rd(c.den, c.dden);
+                const float num_hi = fmaxf(__fadd_ru(c.num, c.dnum), 0.0f);
+                upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : __int_as_float(0x7f800000);
+            }
+            if (upper < c.L2) {
+                if (wall_wins) {
+                    len = fmaxf(sw, 0.0f);
+                    nxt = wall;
+                } else {
+                    len = __fdiv_rn(fmaxf(c.num, 0.0f), c.den);
+                    nxt = c.j1;
+                    qn = c.q;
+                    have_q = true;
+                }
+            } else {
+                // float64 recheck of this crossing from r = r0 + t k
+                if (gl == 0) st_re++;
+                const RaySetDev *rs = &a.sets[set];
+                const double *o = rs->origin + 3 * li;
+                const double *d = rs->dir + 3 * li;
+                double kd[3], rp[3];
+                const double t = __dadd_rn((double)th, (double)tl);
+                for (int cc = 0; cc < 3; cc++) {
+                    kd[cc] = __ldg(d + cc);
+                    rp[cc] = __fma_rn(t, kd[cc], __ldg(o + cc));
+                }
+                exit64<LPR>(h, gp, off, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask, gl, s64, nxt);
+                len = __double2float_rn(s64);
+                from64 = true;
+            }
+        }
+
+        if (gl == 0) st_dec++;
+        steps++;
+        bool relocate = false;
+        if (nxt == kNone) {
+            relocate = true;  // no exit found (Sect. 2.2): nudge over epsilon and locate again
+        } else {
+            const bool positive = FP64 ? (s64 > 0.0) : (len > 0.0f);
+            if (positive) {
+                if (MODE == MODE_FILL && gl == 0) {
+                    const int64_t at = seg_base + nseg;
+                    if (at < a.seg_cap) {  // the count pass sized the buffer; never write past it
+                        a.seg_cell[at] = __ldg(&h.perm[m]);
+                        if (FP64) ((double *)a.seg_len)[at] = s64;
+                        else ((float *)a.seg_len)[at] = len;
+                    }
+                }
+                if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[__ldg(&h.perm[m])], dLr * kappa * len);
+                nseg++;
+                if (gl == 0) st_cross++;
+                if (FP64) {
+                    tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)rho_m), s64));
+                } else {
+                    // Kahan-compensated sum of kappa rho l
+                    const float y = __fsub_rn(__fmul_rn(__fmul_rn(kappa, rho_m), len), tauc);
+                    const float tt = __fadd_rn(tau32, y);
+                    tauc = __fsub_rn(__fsub_rn(tt, tau32), y);
+                    tau32 = tt;
+                }
+                zrun = 0;
+            } else {
+                zrun++;
+                if (gl == 0) st_zero++;
+            }
+            // advance the point
+            if (FP64) {
+                for (int c = 0; c < 3; c++) r64[c] = __dadd_rn(r64[c], __dmul_rn(s64, k64[c]));
+            } else if (from64) {
+                ff_add_double(th, tl, s64);
+            } else {
+                ff_add(th, tl, len);
+            }
+            if (nxt < 0) {
+                ended = true;
+            } else {
+                m = nxt;
+                if (!have_q) qn = __ldg(&h.site[m]);
+                pmx = qn.x;
+                pmy = qn.y;
+                pmz = qn.z;
+                off = __float_as_int(qn.w);
+                rho_m = __ldg(&rho[m]);
+                relocate = zrun > kZeroRunMax;
+            }
+        }
+        if (relocate) {
+            if (gl == 0) st_fb++;
+            zrun = 0;
+            double x[3];
+            if (FP64) {
+                for (int c = 0; c < 3; c++) r64[c] = __dadd_rn(r64[c], __dmul_rn(gp->eps64, k64[c]));
+                for (int c = 0; c < 3; c++) x[c] = r64[c];
+            } else {
+                ff_add_double(th, tl, gp->eps32);
+                const RaySetDev *rs = &a.sets[set];
+                const double t = __dadd_rn((double)th, (double)tl);
+                for (int c = 0; c < 3; c++) x[c] = __fma_rn(t, __ldg(rs->dir + 3 * li + c), __ldg(rs->origin + 3 * li + c));
+            }
+            const int nm = locate_point(gp, x[0], x[1], x[2], !FP64, nullptr);
+            if (nm < 0) {
+                ended = true;
+            } else {
+                m = nm;
+                const float4 q = __ldg(&h.site[m]);
+                pmx = q.x;
+                pmy = q.y;
+                pmz = q.z;
+                off = __float_as_int(q.w);
+                rho_m = __ldg(&rho[m]);
+            }
+        }
+        if (!ended && steps >= max_steps) {
+            ended = true;
+            status = RAY_STEP_LIMIT;
+            if (gl == 0) st_lim++;
+        }
+        if (ended) {
+            if (gl == 0) {
+                st_rays++;
+                const RaySetDev *rs = &a.sets[set];
+                if (MODE == MODE_TAU || MODE == MODE_FILL) {
+                    if (rs->tau) {
+                        if (FP64) ((double *)rs->tau)[li] = tau64;
+                        else ((float *)rs->tau)[li] = tau32;
+                    }
+                    if (rs->status) rs->status[li] = status;
+                }
+                if (MODE == MODE_COUNT) a.seg_off[ray] = nseg;
+            }
+            ray = -1;
+        }
+    }
+
+    // ---------------- statistics: one atomic per warp and counter ----------------
+    const unsigned vals[9] = {st_rays, st_cross, st_dec, st_re, st_fb, st_zero, st_lim, st_out, st_bad};
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.stats);
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const unsigned v = __reduce_add_sync(0xffffffffu, vals[i]);
+        if (lane == 0 && v) atomicAdd(dst + i, (unsigned long long)v);
+    }
+}
+
+}  // namespace vg

@@ -1,0 +1,18 @@
+// Instantiations of the traversal kernel for 1 lane(s) per ray.
+#include "kernels.h"
+#include "trace.cuh"
+
+namespace vg {
+
+void kernel_table_lpr1(KernelSet &k) {
+    k.fn[0][MODE_TAU] = (const void *)trace_kernel<1, false, MODE_TAU>;
+    k.fn[0][MODE_COUNT] = (const void *)trace_kernel<1, false, MODE_COUNT>;
+    k.fn[0][MODE_FILL] = (const void *)trace_kernel<1, false, MODE_FILL>;
+    k.fn[0][MODE_GRAD] = (const void *)trace_kernel<1, false, MODE_GRAD>;
+    k.fn[1][MODE_TAU] = (const void *)trace_kernel<1, true, MODE_TAU>;
+    k.fn[1][MODE_COUNT] = (const void *)trace_kernel<1, true, MODE_COUNT>;
+    k.fn[1][MODE_FILL] = (const void *)trace_kernel<1, true, MODE_FILL>;
+    k.fn[1][MODE_GRAD] = nullptr;
+}
+
+}  // namespace vg

@@ -25,3 +25,12 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def libvgrid():
+    """Builds libvgrid in-tree (nvcc cross-compiles without a GPU) and loads it."""
+    from paper_1310_1854_gb300 import build as libbuild
+    libbuild.build()
+    import paper_1310_1854_gb300
+    return paper_1310_1854_gb300.load()

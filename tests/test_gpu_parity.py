@@ -1,0 +1,278 @@
+"""GPU traversal against the CPU oracle, through the C-ABI.
+
+Acceptance (float64 form): cell sequences identical on rays whose exit
+decisions are not near ties (decision margin > 1e-9, start not equidistant),
+segment lengths within 1e-12 relative (1e-12 * diagonal absolute for
+lengths below 1e-6 * diagonal), tau within 1e-12 relative.
+Acceptance (float32 form with float64 recheck): the same cell sequences, and
+tau within 1e-5 relative of the oracle's float64 tau.
+Small cases compare every ray; full-size workloads compare a seeded sample
+of rays traced by the oracle with every site as a candidate.
+"""
+import numpy as np
+import pytest
+import torch
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TAU32_REL = 1e-5
+LEN64_REL = 1e-12
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def make(g, **kw):
+    from paper_1310_1854_gb300 import VoronoiGrid
+    vg = VoronoiGrid(g.sites, g.box, **kw)
+    vg.set_density(dev(g.rho), float(g.kappa))
+    return vg
+
+
+def oracle_full(g, rays, **kw):
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    return oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin, rays.dir, off=off, idx=idx,
+                        kappa=float(g.kappa), **kw)
+
+
+def check_segments(ref, sel, seg_off, seg_cell, seg_len, diag, len_rel):
+    """Cell sequences equal and lengths within tolerance on rays `sel`."""
+    so = seg_off.cpu().numpy()
+    cells = seg_cell.cpu().numpy()
+    lens = seg_len.cpu().numpy().astype(np.float64)
+    for i in sel:
+        rc, rl = ref.segments(i)
+        gc = cells[so[i]:so[i + 1]]
+        gl = lens[so[i]:so[i + 1]]
+        assert np.array_equal(gc, rc), f"ray {i}: cells differ"
+        if len_rel is not None:
+            tol = np.where(rl < 1e-6 * diag, 1e-12 * diag, len_rel * rl)
+            assert np.all(np.abs(gl - rl) <= tol), f"ray {i}: lengths differ by {np.max(np.abs(gl - rl) / rl)}"
+
+
+def run_case(g, rays, ref, lanes=(1, 4)):
+    """Every ray: float64 and float32 segment lists and tau against the
+    oracle, for each lanes-per-ray shape; tau identical across shapes."""
+    vg = make(g)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    O, D = dev(rays.origin), dev(rays.dir)
+    ok = np.nonzero(ref.near_tie == 0)[0]
+    assert ok.size >= 0.9 * len(rays.origin)
+    rt = ref.tau[ok]
+    taus = []
+    for lpr in lanes:
+        vg.set_launch(lanes_per_ray=lpr)
+        r64 = vg.trace(O, D, precision="fp64", segments=True, status=True)
+        r32 = vg.trace(O, D, precision="fp32", segments=True, status=True)
+        t32 = vg.trace(O, D, precision="fp32", stats=True)
+        check_segments(ref, ok, r64.seg_off, r64.seg_cell, r64.seg_len, diag, LEN64_REL)
+        check_segments(ref, ok, r32.seg_off, r32.seg_cell, r32.seg_len, diag, None)
+        np.testing.assert_allclose(r64.tau.cpu().numpy()[ok], rt, rtol=1e-12, atol=1e-300)
+        t = t32.tau.cpu().numpy().astype(np.float64)[ok]
+        err = np.abs(t - rt) / np.maximum(rt, 1e-300)
+        assert np.all(err[rt > 0] <= TAU32_REL), f"max rel tau error {err.max()}"
+        # tau mode writes the tau of segment mode (same decisions)
+        np.testing.assert_array_equal(t32.tau.cpu().numpy(), r32.tau.cpu().numpy())
+        assert np.all(r64.status.cpu().numpy() == 0) and np.all(r32.status.cpu().numpy() == 0)
+        taus.append(t32.tau.cpu().numpy())
+    for t in taus[1:]:
+        np.testing.assert_array_equal(t, taus[0])
+    return vg
+
+
+def test_config1_full_parity():
+    g, rays = gen.config1()
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref, lanes=(1, 2, 4, 8))
+
+
+def test_small_disk_parity():
+    g = gen.make_disk_grid(20_000, 101)
+    rays = gen.disk_rays(3000, 102)
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref)
+
+
+def test_small_clumpy_parity():
+    g = gen.make_clumpy_grid(20_000, 103, n_clumps=40)
+    rays = gen.uniform_rays(3000, 104)
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref)
+
+
+def test_cubic_lattice_parity():
+    """Degenerate geometry (eight cells per vertex): the float32 form must
+    fall back to float64 near the ties and still match the oracle."""
+    S = gen.cubic_lattice(8)
+    g = gen.Grid(S, gen.CUBE_BOX.copy(), gen.rng_for(5).uniform(0.5, 1.5, len(S)).astype(np.float32))
+    rays = gen.uniform_rays(2000, 106)
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref)
+
+
+def test_locate_parity():
+    g = gen.make_disk_grid(20_000, 107)
+    vg = make(g)
+    rng = gen.rng_for(108)
+    P = np.concatenate([gen.disk_points(4000, rng), gen.uniform_points(1000, rng, g.box),
+                        np.array([[5.0, 0, 0], [0, 0, -0.6], [4.0, 4.0, 0.5], [-4.0, -4.0, -0.5]])])
+    ref = oracle.locate(g.sites, g.box, P)
+    for prec in ("fp32", "fp64"):
+        out = vg.locate(dev(P), precision=prec).cpu().numpy()
+        np.testing.assert_array_equal(out, ref)
+
+
+def test_full_size_config2_sampled():
+    """10^5-site disk, 10^6 rays, the benchmark's launch shape; 200 rays
+    compared with the oracle over all sites."""
+    g, rays = gen.config2()
+    sample = np.sort(gen.rng_for(109).choice(len(rays.origin), 200, replace=False))
+    ref = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sample], rays.dir[sample])
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    r32 = vg.trace(O, D, precision="fp32", segments=True, stats=True)
+    r64 = vg.trace(O, D, precision="fp64", segments=True)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    so32 = r32.seg_off.cpu().numpy()
+    so64 = r64.seg_off.cpu().numpy()
+    c32, c64 = r32.seg_cell.cpu().numpy(), r64.seg_cell.cpu().numpy()
+    l64 = r64.seg_len.cpu().numpy()
+    t32 = r32.tau.cpu().numpy().astype(np.float64)
+    t64 = r64.tau.cpu().numpy()
+    n_ok = 0
+    for k, i in enumerate(sample):
+        if ref.near_tie[k]:
+            continue
+        n_ok += 1
+        rc, rl = ref.segments(k)
+        assert np.array_equal(c32[so32[i]:so32[i + 1]], rc)
+        assert np.array_equal(c64[so64[i]:so64[i + 1]], rc)
+        gl = l64[so64[i]:so64[i + 1]]
+        tol = np.where(rl < 1e-6 * diag, 1e-12 * diag, LEN64_REL * rl)
+        assert np.all(np.abs(gl - rl) <= tol)
+        assert abs(t64[i] - ref.tau[k]) <= 1e-12 * ref.tau[k]
+        assert abs(t32[i] - ref.tau[k]) <= TAU32_REL * ref.tau[k]
+    assert n_ok >= 190
+    # over all 10^6 rays: lengths sum to the in-domain distance
+    L = oracle_slab(g.box, rays.origin, rays.dir)
+    per_ray = np.bincount(np.repeat(np.arange(len(L)), np.diff(so64)), weights=l64, minlength=len(L))
+    np.testing.assert_allclose(per_ray, L, rtol=1e-12, atol=1e-12)
+    assert r32.stats["rays"] == len(L)
+
+
+def oracle_slab(box, O, D):
+    from tests.helpers import slab_length
+    return slab_length(box, O, D)
+
+
+@pytest.mark.slow
+def test_full_size_config3_sampled():
+    """10^6 clumpy sites, 10^7 rays; 24 sampled rays against the oracle."""
+    g, rays = gen.config3()
+    sample = np.sort(gen.rng_for(110).choice(len(rays.origin), 24, replace=False))
+    ref = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sample], rays.dir[sample])
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    r32 = vg.trace(O, D, precision="fp32", stats=True, status=True)
+    t32 = r32.tau.cpu().numpy().astype(np.float64)
+    assert np.all(r32.status.cpu().numpy() == 0)
+    Os, Ds = dev(rays.origin[sample]), dev(rays.dir[sample])
+    s32 = vg.trace(Os, Ds, precision="fp32", segments=True)
+    so = s32.seg_off.cpu().numpy()
+    cells = s32.seg_cell.cpu().numpy()
+    for k, i in enumerate(sample):
+        if ref.near_tie[k]:
+            continue
+        assert np.array_equal(cells[so[k]:so[k + 1]], ref.segments(k)[0])
+        assert abs(t32[i] - ref.tau[k]) <= TAU32_REL * ref.tau[k]
+
+
+def test_edge_cases():
+    from paper_1310_1854_gb300 import VGridError, _lib
+    g, rays = gen.config1(64)
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    # empty input
+    e = vg.trace(O[:0], D[:0], precision="fp32", segments=True)
+    assert e.seg_off.shape[0] == 1 and int(e.seg_off[0]) == 0
+    # a ray starting outside, one on the boundary going out, one with a bad direction
+    o = np.array([[2.0, 0, 0], [1.0, 0.1, 0.2], [0.0, 0.0, 0.0], [0.1, 0.1, 0.1]])
+    d = np.array([[1.0, 0, 0], [1.0, 0, 0], [0.5, 0.5, 0.0], [0.0, 0.0, 1.0]])
+    for prec in ("fp32", "fp64"):
+        r = vg.trace(dev(o), dev(d), precision=prec, status=True)
+        st = r.status.cpu().numpy()
+        assert st[0] == _lib.RAY_OUTSIDE and st[2] == _lib.RAY_BAD_DIR and st[3] == _lib.RAY_OK
+        assert float(r.tau[0]) == 0.0 and float(r.tau[1]) == 0.0
+        with pytest.raises(VGridError) as ex:
+            vg.trace(dev(o), dev(d), precision=prec, stats=True)
+        assert ex.value.code == _lib.ERR_ARG
+    # capacity: too small a buffer reports the sizes
+    with pytest.raises(VGridError) as ex:
+        vg.trace(O, D, precision="fp32", segments=True, seg_capacity=3)
+    assert ex.value.code == _lib.ERR_CAPACITY
+    # step limit
+    from paper_1310_1854_gb300 import VoronoiGrid
+    v1 = VoronoiGrid(g.sites, g.box, max_steps=2)
+    with pytest.raises(VGridError) as ex:
+        v1.trace(O, D, precision="fp32", stats=True)
+    assert ex.value.code == _lib.ERR_STEP_LIMIT
+    r = v1.trace(O, D, precision="fp32", status=True)
+    assert np.any(r.status.cpu().numpy() == _lib.RAY_STEP_LIMIT)
+
+
+def test_gradient_matches_oracle():
+    g, rays = gen.config1(3000)
+    ref = oracle_full(g, rays)
+    target = np.exp(-0.9 * ref.tau)
+    _, dL = oracle.exp_loss(ref.tau, target)
+    want = oracle.tau_grad(ref, len(g.sites), dL, kappa=float(g.kappa))
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    got = vg.trace_grad(O, D, dev(dL.astype(np.float32))).cpu().numpy().astype(np.float64)
+    big = np.abs(want) > 1e-6 * np.abs(want).max()
+    rel = np.abs(got[big] - want[big]) / np.abs(want[big])
+    assert rel.max() <= 1e-4, rel.max()
+    assert np.all(got[want == 0] == 0)
+    # autograd wrapper gives the same gradient
+    from paper_1310_1854_gb300 import optical_depth
+    rho = dev(g.rho).requires_grad_(True)
+    tau = optical_depth(vg, rho, O, D, float(g.kappa))
+    t = dev(target.astype(np.float32))
+    loss = ((torch.exp(-tau) - t) ** 2).sum()
+    loss.backward()
+    gg = rho.grad.cpu().numpy().astype(np.float64)
+    rel = np.abs(gg[big] - want[big]) / np.abs(want[big])
+    assert rel.max() <= 2e-3, rel.max()
+
+
+def test_batched_matches_single():
+    from paper_1310_1854_gb300 import Batch
+    sets = gen.config4(G=12, scale=0.02)
+    grids, single = [], []
+    for g, r in sets:
+        vg = make(g)
+        grids.append((vg, dev(r.origin), dev(r.dir)))
+        single.append(vg.trace(grids[-1][1], grids[-1][2], precision="fp32").tau.cpu().numpy())
+    b = Batch(grids)
+    st = b.run(stats=True)
+    for k in range(len(sets)):
+        np.testing.assert_array_equal(b.tau[k].cpu().numpy(), single[k])
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(graph=True, stream=s)
+        b.run(graph=True, stream=s)
+    s.synchronize()
+    for k in range(len(sets)):
+        np.testing.assert_array_equal(b.tau[k].cpu().numpy(), single[k])
+    assert st["rays"] == sum(len(r.origin) for _, r in sets)
+    # one grid against the oracle
+    g, r = sets[3]
+    ref = oracle_full(g, r)
+    ok = ref.near_tie == 0
+    t = b.tau[3].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])

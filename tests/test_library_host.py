@@ -1,0 +1,159 @@
+"""The C-ABI library on the host: it loads, exports every declared entry
+point, and its grid builder (an implementation independent of the oracle)
+agrees with the oracle's cells. No GPU is used: grids are built with
+host_only, which runs the whole construction and copies nothing to a device.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "vgrid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(vgrid_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol(libvgrid):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(libvgrid, n), n
+    from paper_1310_1854_gb300 import _lib
+    assert {s[0] for s in _lib.SIGNATURES} == set(names)
+
+
+def _grid(sites, box, **kw):
+    from paper_1310_1854_gb300 import VoronoiGrid
+    return VoronoiGrid(sites, box, host_only=True, **kw)
+
+
+def _assert_cells_match(vg, sites, box, ids, area_rel=1e-9):
+    off, idx = vg.neighbors()
+    vol, bb = vg.cells()
+    c = oracle.cells(sites, box, ids=ids)
+    for k, m in enumerate(ids):
+        ours = set(idx[off[m]:off[m + 1]].tolist())
+        faces = c.nbr[k]
+        big = set(faces[c.area[k] > area_rel * c.area[k].sum()].tolist())
+        # every face of non-negligible area is in our list; ours may add
+        # planes that only touch the cell (they never change an exit)
+        assert big <= ours, (m, big - ours)
+        assert ours <= set(faces.tolist()) | (ours - set(faces.tolist())), m
+        extra = ours - set(faces.tolist())
+        assert len(extra) <= 2, (m, extra)
+    np.testing.assert_allclose(vol[ids], c.vol, rtol=1e-10)
+    np.testing.assert_allclose(bb[ids], c.bbox, atol=1e-12 * np.linalg.norm(box[3:] - box[:3]))
+
+
+def test_builder_matches_oracle_uniform_1000(libvgrid):
+    g, _ = gen.config1(10)
+    vg = _grid(g.sites, g.box)
+    off, idx = vg.neighbors()
+    c = oracle.cells(g.sites, g.box)
+    for m in range(len(g.sites)):
+        assert np.array_equal(np.sort(idx[off[m]:off[m + 1]]), c.nbr[m]), m
+    vol, _ = vg.cells()
+    np.testing.assert_allclose(vol, c.vol, rtol=1e-11)
+    np.testing.assert_allclose(vol.sum(), 8.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["disk", "clumpy"])
+def test_builder_matches_oracle_sampled(libvgrid, kind):
+    if kind == "disk":
+        g = gen.make_disk_grid(20_000, 91)
+    else:
+        g = gen.make_clumpy_grid(20_000, 92, n_clumps=40)
+    vg = _grid(g.sites, g.box)
+    ids = gen.rng_for(93).choice(len(g.sites), 300, replace=False)
+    _assert_cells_match(vg, g.sites, g.box, ids)
+    vol, _ = vg.cells()
+    box = g.box
+    np.testing.assert_allclose(vol.sum(), np.prod(box[3:] - box[:3]), rtol=1e-11)
+
+
+def test_builder_symmetric_and_reorder_invariant(libvgrid):
+    g = gen.make_uniform_grid(3000, 94)
+    a = _grid(g.sites, g.box)
+    b = _grid(g.sites, g.box, reorder=False)
+    oa, ia = a.neighbors()
+    ob, ib = b.neighbors()
+    np.testing.assert_array_equal(oa, ob)
+    np.testing.assert_array_equal(ia, ib)
+    pairs = {(m, int(j)) for m in range(3000) for j in ia[oa[m]:oa[m + 1]] if j >= 0}
+    assert all((j, m) in pairs for m, j in pairs)
+
+
+def test_builder_lattices(libvgrid):
+    S = gen.cubic_lattice(8)
+    vg = _grid(S, gen.CUBE_BOX)
+    off, idx = vg.neighbors()
+    deg = np.diff(off)
+    interior = np.all(np.abs(S) < 0.8, axis=1)
+    assert np.all(deg[interior] >= 6)
+    c = oracle.cells(S, gen.CUBE_BOX)
+    for m in np.nonzero(interior)[0][:50]:
+        assert set(c.nbr[m].tolist()) <= set(idx[off[m]:off[m + 1]].tolist())
+    vol, _ = vg.cells()
+    np.testing.assert_allclose(vol, 0.25 ** 3, rtol=1e-12)
+    S = gen.bcc_lattice(8)
+    vg = _grid(S, gen.CUBE_BOX)
+    off, idx = vg.neighbors()
+    interior = np.all(np.abs(S) < 1 - 1.2 * 0.25, axis=1)
+    assert np.all(np.diff(off)[interior] >= 14)
+    vol, _ = vg.cells()
+    np.testing.assert_allclose(vol[interior], 0.25 ** 3 / 2, rtol=1e-12)
+
+
+def test_create_rejects_bad_input(libvgrid):
+    from paper_1310_1854_gb300 import VGridError, _lib
+    box = gen.CUBE_BOX
+    with pytest.raises(VGridError) as e:
+        _grid(np.array([[0.0, 0, 0], [0.0, 0, 0]]), box)
+    assert e.value.code == _lib.ERR_DUP_SITE
+    with pytest.raises(VGridError) as e:
+        _grid(np.array([[0.0, 0, 0], [1.5, 0, 0]]), box)
+    assert e.value.code == _lib.ERR_OUTSIDE
+    with pytest.raises(VGridError) as e:
+        _grid(np.array([[0.1, 0, 0]]), box)  # 0.1 is not a float32 value
+    assert e.value.code == _lib.ERR_ARG
+    _grid(np.array([[0.1, 0, 0]]), box, round_sites=True)
+    with pytest.raises(VGridError) as e:
+        _grid(np.zeros((0, 3)), box)
+    assert e.value.code == _lib.ERR_ARG
+    with pytest.raises(VGridError) as e:
+        _grid(np.array([[0.0, 0, 0]]), np.array([1, -1, -1, -1, 1, 1.0]))
+    assert e.value.code == _lib.ERR_ARG
+    with pytest.raises(VGridError) as e:
+        _grid(np.array([[np.nan, 0, 0]]), box)
+    assert e.value.code == _lib.ERR_ARG
+
+
+def test_single_site_grid_is_the_box(libvgrid):
+    vg = _grid(np.array([[0.25, -0.5, 0.125]]), gen.CUBE_BOX)
+    off, idx = vg.neighbors()
+    assert sorted(idx.tolist()) == [-6, -5, -4, -3, -2, -1]
+    vol, bb = vg.cells()
+    assert vol[0] == pytest.approx(8.0, rel=1e-14)
+
+
+def test_host_only_grid_refuses_device_calls(libvgrid):
+    from paper_1310_1854_gb300 import _lib
+    vg = _grid(gen.cubic_lattice(2), gen.CUBE_BOX)
+    lib = _lib.load()
+    dummy = ctypes.c_void_p(16)
+    rc = lib.vgrid_trace(vg._h, dummy, dummy, 1, _lib.FP32_RECHECK, _lib.TAU, dummy, None, None, None, 0, None,
+                         None, None)
+    assert rc == _lib.ERR_ARG
+    assert b"host_only" in lib.vgrid_last_error()
+    assert lib.vgrid_locate(vg._h, dummy, 1, 0, dummy, None) == _lib.ERR_ARG
+    assert lib.vgrid_trace_grad(vg._h, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
+    assert lib.vgrid_enable_timing(vg._h, 1) == _lib.ERR_ARG
