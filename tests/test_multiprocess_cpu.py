@@ -1,0 +1,82 @@
+"""The N > 1 path on CPU: two gloo ranks shard the rays, trace their shard
+with the oracle (standing in for one GPU each), and combine counts, the
+max-over-ranks time and the density gradient the way bench.py and
+paper_1310_1854_gb300.shard do on GPUs. No GPU is touched."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import gen
+import oracle
+from paper_1310_1854_gb300.shard import allreduce_sum_, max_over_ranks, shard_range, sum_over_ranks
+
+
+def test_shard_range_partitions():
+    for n in (0, 1, 7, 100, 1001):
+        for w in (1, 2, 3, 8):
+            parts = [shard_range(n, r, w) for r in range(w)]
+            assert parts[0][0] == 0 and parts[-1][1] == n
+            assert all(parts[i][1] == parts[i + 1][0] for i in range(w - 1))
+            sizes = [b - a for a, b in parts]
+            assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(ValueError):
+        shard_range(10, 2, 2)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g, rays = gen.config1(400)
+        c = oracle.cells(g.sites, g.box, threads=1)
+        off, idx = oracle.csr(c, len(g.sites))
+        a, b = shard_range(len(rays.origin), rank, world)
+        tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[a:b], rays.dir[a:b], off=off,
+                          idx=idx, threads=1)
+        segs = sum_over_ranks(float(tr.nseg.sum()))
+        tmax = max_over_ranks(float(rank + 1))
+        _, dL = oracle.exp_loss(tr.tau, np.exp(-0.5 * tr.tau))
+        grad = torch.from_numpy(oracle.tau_grad(tr, len(g.sites), dL))
+        allreduce_sum_(grad)
+        out[rank] = (segs, tmax, grad.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_match_single_process():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    g, rays = gen.config1(400)
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin, rays.dir, off=off, idx=idx)
+    _, dL = oracle.exp_loss(tr.tau, np.exp(-0.5 * tr.tau))
+    full = oracle.tau_grad(tr, len(g.sites), dL)
+    for r in range(world):
+        segs, tmax, grad = out[r]
+        assert segs == tr.nseg.sum()
+        assert tmax == world
+        np.testing.assert_allclose(grad, full, rtol=1e-12, atol=1e-15)
