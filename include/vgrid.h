@@ -260,6 +260,32 @@ int vgrid_batch_destroy(vgrid_batch_t *b);
 int vgrid_enable_timing(vgrid_t *g, int enable);
 int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *launches);
 
+/*
+ * Tau per ray with no device allocation, for callers that cannot call
+ * cudaMalloc: code whose device memory is handed out by another allocator
+ * under a fixed budget, or latency-bound loops that must not take the
+ * implicit device synchronisation cudaMalloc/cudaFree can cause. The paper
+ * has no counterpart; this is a variant of vgrid_trace in VGRID_TAU mode.
+ *
+ * Same arguments and results as vgrid_trace with output VGRID_TAU (tau is
+ * float64[N] for VGRID_FP64, float32[N] for VGRID_FP32_RECHECK; ray_status
+ * nullable), but its work buffers (start cells, work counter, counters) live
+ * in one fixed device array of VGRID_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. N above VGRID_NOALLOC_MAX_RAYS is rejected with VGRID_ERR_ARG before
+ * anything is enqueued. The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the grid's device current);
+ * make that first call before any stream capture. All calls share the one
+ * array: the call clears what must start at zero, but calls that overlap on
+ * the GPU (other streams, other threads, other grids on the same device)
+ * race on it and must be serialised by the caller. No counters are returned
+ * and nothing is synchronised.
+ */
+#define VGRID_NOALLOC_MAX_RAYS (1 << 20)
+#define VGRID_NOALLOC_SCRATCH_BYTES (512 + 4 * VGRID_NOALLOC_MAX_RAYS)
+int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,
+                        int32_t *ray_status, vgrid_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

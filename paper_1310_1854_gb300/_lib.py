@@ -96,7 +96,10 @@ SIGNATURES = [
     ("vgrid_enable_timing", c_int32, [c_void_p, c_int32]),
     ("vgrid_read_timing", c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                     ctypes.POINTER(c_int64)]),
+    ("vgrid_trace_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p]),
 ]
+
+NOALLOC_MAX_RAYS = 1 << 20
 
 
 def load():

@@ -772,3 +772,20 @@ int vgrid_batch_destroy(vgrid_batch_t *b) {
 }
 
 }  // extern "C"
+
+namespace vg {
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int grid_view(const struct vgrid *g, GridView *out) {
+    if (!g || g->device < 0) return -1;
+    out->device = g->device;
+    out->sms = g->sms;
+    out->d_desc = g->d_desc;
+    out->lanes_per_ray = g->launch.lanes_per_ray;
+    out->block = g->launch.block;
+    out->blocks_per_sm = g->launch.blocks_per_sm;
+    return 0;
+}
+
+}  // namespace vg

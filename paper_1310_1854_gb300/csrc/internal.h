@@ -82,3 +82,16 @@ struct StatsDev {
 };
 
 #define VG_PAD_ID (-8)
+
+// What the allocation-free entry point (noalloc.cu) needs from a grid.
+struct vgrid;
+namespace vg {
+struct GridView {
+    int device;
+    int sms;
+    const GridDev *d_desc;
+    int lanes_per_ray, block, blocks_per_sm;
+};
+int grid_view(const struct vgrid *g, GridView *out);  // 0, or -1 for a host-only grid
+void set_error(const std::string &msg);              // message for vgrid_last_error()
+}  // namespace vg
