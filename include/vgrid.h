@@ -281,8 +281,8 @@ int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *
  * race on it and must be serialised by the caller. No counters are returned
  * and nothing is synchronised.
  */
-#define VGRID_NOALLOC_MAX_RAYS (1 << 20)
-#define VGRID_NOALLOC_SCRATCH_BYTES (512 + 4 * VGRID_NOALLOC_MAX_RAYS)
+#define VGRID_NOALLOC_MAX_RAYS (1 << 18)
+#define VGRID_NOALLOC_SCRATCH_BYTES (512 + 64 * VGRID_NOALLOC_MAX_RAYS)
 int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,
                         int32_t *ray_status, vgrid_stream_t stream);
 

@@ -129,7 +129,7 @@ class VoronoiGrid:
         return vol, bb
 
     # -------------------------------------------------------------- launch
-    def set_launch(self, lanes_per_ray=4, block=256, blocks_per_sm=0):
+    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0):
         l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm))
         check(load().vgrid_set_launch(self._h, ctypes.byref(l)))
 
@@ -213,7 +213,7 @@ class Batch:
     CUDA graph on the first run and replayed afterwards.
     """
 
-    def __init__(self, sets, lanes_per_ray=4, block=256, blocks_per_sm=0):
+    def __init__(self, sets, lanes_per_ray=1, block=128, blocks_per_sm=0):
         self._keep = []
         arr = (_lib.Rayset * len(sets))()
         self.tau = []

@@ -99,7 +99,7 @@ SIGNATURES = [
     ("vgrid_trace_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p]),
 ]
 
-NOALLOC_MAX_RAYS = 1 << 20
+NOALLOC_MAX_RAYS = 1 << 18
 
 
 def load():

@@ -79,7 +79,7 @@ struct vgrid {
     int sms = 1;
     int64_t M = 0;
     vgrid_opts opts{};
-    vgrid_launch launch{4, 256, 0};
+    vgrid_launch launch{1, 128, 0};
     GridDev hd{};
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
@@ -95,7 +95,7 @@ struct vgrid {
     unsigned long long *d_queue = nullptr;
     StatsDev *d_stats = nullptr;
     RaySetDev *d_set = nullptr;
-    int32_t *d_start = nullptr;
+    RayPrep *d_start = nullptr;
     int64_t start_cap = 0;
     int64_t *d_scan = nullptr;
     int64_t scan_cap = 0;
@@ -112,10 +112,10 @@ struct vgrid_batch {
     int sms = 1;
     int32_t G = 0;
     int64_t total = 0;
-    vgrid_launch launch{4, 256, 0};
+    vgrid_launch launch{1, 128, 0};
     GridDev *d_grids = nullptr;
     RaySetDev *d_sets = nullptr;
-    int32_t *d_start = nullptr;
+    RayPrep *d_start = nullptr;
     unsigned long long *d_queue = nullptr;
     StatsDev *d_stats = nullptr;
     int ngrids = 0;
@@ -404,7 +404,7 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
 int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (!l) {
-        g->launch = vgrid_launch{4, 256, 0};
+        g->launch = vgrid_launch{1, 128, 0};
         return VGRID_OK;
     }
     if (!valid_lpr(l->lanes_per_ray)) return fail(VGRID_ERR_ARG, "lanes_per_ray must be 1, 2, 4 or 8");
@@ -447,7 +447,7 @@ int ensure_start(vgrid_t *g, int64_t N) {
     if (N <= g->start_cap) return VGRID_OK;
     if (g->d_start) {
         cudaFree(g->d_start);
-        g->device_bytes -= g->start_cap * (int64_t)sizeof(int32_t);
+        g->device_bytes -= g->start_cap * (int64_t)sizeof(RayPrep);
         g->d_start = nullptr;
         g->start_cap = 0;
     }
@@ -527,7 +527,8 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
     if (rc) return rc;
     RaySetDev set{pts, pts, nullptr, nullptr, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, precision == VGRID_FP32_RECHECK, cell, g->sms, s));
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N,
+                              precision == VGRID_FP32_RECHECK ? vg::PREP_CELL32 : vg::PREP_CELL64, cell, g->sms, s));
     return VGRID_OK;
 }
 
@@ -556,7 +557,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, !fp64, nullptr, g->sms, s));
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, fp64 ? vg::PREP_FP64 : vg::PREP_FP32, nullptr, g->sms, s));
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.grids = g->d_desc;
@@ -565,6 +566,8 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     a.total = N;
     a.queue = g->d_queue;
     a.stats = g->d_stats;
+    a.g1 = g->hd;
+    a.s1 = set;
     if (output == VGRID_TAU) {
         mark(g, 1, 0, s);
         if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], g->launch, g->sms, N, a, s))) return rc;
@@ -608,7 +611,7 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
     RaySetDev set{origin, dir, nullptr, nullptr, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, 1, nullptr, g->sms, s));
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.grids = g->d_desc;
@@ -619,6 +622,8 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
     a.stats = g->d_stats;
     a.dL_dtau = dL_dtau;
     a.dL_drho = dL_drho;
+    a.g1 = g->hd;
+    a.s1 = set;
     mark(g, 1, 0, s);
     rc = launch_trace(kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_GRAD], g->launch, g->sms, N, a, s);
     mark(g, 1, 1, s);
@@ -725,7 +730,7 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
 static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
     RaySetDev none{};
     VG_CUDA(vg::launch_prepare(nullptr, none, b->d_queue, b->d_stats, s));
-    VG_CUDA(vg::launch_locate(b->d_grids, b->d_sets, b->G, b->total, 1, nullptr, b->sms, s));
+    VG_CUDA(vg::launch_locate(b->d_grids, b->d_sets, b->G, b->total, vg::PREP_FP32, nullptr, b->sms, s));
     vg::TraceArgs a{};
     a.grids = b->d_grids;
     a.sets = b->d_sets;
@@ -733,7 +738,7 @@ static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
     a.total = b->total;
     a.queue = b->d_queue;
     a.stats = b->d_stats;
-    return launch_trace(kernels(b->launch.lanes_per_ray).fn[0][vg::MODE_TAU], b->launch, b->sms, b->total, a, s);
+    return launch_trace(kernels(b->launch.lanes_per_ray).batch, b->launch, b->sms, b->total, a, s);
 }
 
 int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_stream_t stream) {
@@ -782,6 +787,7 @@ int grid_view(const struct vgrid *g, GridView *out) {
     out->device = g->device;
     out->sms = g->sms;
     out->d_desc = g->d_desc;
+    out->hd = g->hd;
     out->lanes_per_ray = g->launch.lanes_per_ray;
     out->block = g->launch.block;
     out->blocks_per_sm = g->launch.blocks_per_sm;

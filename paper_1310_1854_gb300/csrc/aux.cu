@@ -29,35 +29,68 @@ cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long
     return cudaGetLastError();
 }
 
-// C(r0) for every ray of every set: internal id into sets[].start, and the
-// caller's id into out_caller (if given).
+// Start records for every ray of every set. PREP_CELL32 / PREP_CELL64: C(r0)
+// only (the cell), with float32 (rechecked) or float64 distances;
+// PREP_FP32: float32 form (cell, direction check, wall exit of Eq. 5 and the
+// float pairs of origin and direction); PREP_FP64: float64 form (cell and
+// direction check). The caller's id of the cell goes to out_caller if given.
 __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const RaySetDev *sets, int nsets,
-                                                     int64_t total, int fp32, int32_t *out_caller, StatsDev *stats) {
-    unsigned rechecks = 0;
+                                                     int64_t total, int prep, int32_t *out_caller) {
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int set = find_set(sets, nsets, w);
         const RaySetDev &rs = sets[set];
         const int64_t li = w - rs.first;
         const GridDev *gp = grids + rs.grid;
         const double *o = rs.origin + 3 * li;
-        int re = 0;
-        const int m = locate_point(gp, __ldg(o), __ldg(o + 1), __ldg(o + 2), fp32 != 0, &re);
-        rechecks += re;
-        rs.start[li] = m;
+        const double r0[3] = {__ldg(o), __ldg(o + 1), __ldg(o + 2)};
+        RayPrep *out = rs.start + li;
+        int m = locate_point(gp, r0[0], r0[1], r0[2], prep == PREP_CELL32 || prep == PREP_FP32, nullptr);
         if (out_caller) out_caller[w] = m >= 0 ? __ldg(&gp->perm[m]) : -1;
-    }
-    if (stats) {
-        const unsigned v = __reduce_add_sync(0xffffffffu, rechecks);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&stats->rechecks, (unsigned long long)v);
+        if (prep == PREP_CELL32 || prep == PREP_CELL64) {
+            out->cell = m;
+            continue;
+        }
+        const double *d = rs.dir + 3 * li;
+        const double k[3] = {__ldg(d), __ldg(d + 1), __ldg(d + 2)};
+        const double kk = __dadd_rn(__dadd_rn(__dmul_rn(k[0], k[0]), __dmul_rn(k[1], k[1])), __dmul_rn(k[2], k[2]));
+        if (!(fabs(kk - 1.0) <= 2.000001e-6)) m = -2;
+        if (prep == PREP_FP64) {
+            out->cell = m;
+            continue;
+        }
+        // distance to the wall ahead (Eq. 5 for the walls the ray faces)
+        double tmax = 1e300;
+        int wid = -1;
+        for (int c = 0; c < 3; c++) {
+            if (k[c] > 0.0) {
+                const double t = __ddiv_rn(__dsub_rn(gp->hi[c], r0[c]), k[c]);
+                if (t < tmax) { tmax = t; wid = -(2 * c + 2); }
+            } else if (k[c] < 0.0) {
+                const double t = __ddiv_rn(__dsub_rn(gp->lo[c], r0[c]), k[c]);
+                if (t < tmax) { tmax = t; wid = -(2 * c + 1); }
+            }
+        }
+        if (!(tmax >= 0.0) || tmax > 1e299) tmax = 0.0;
+        RayPrep p;
+        p.cell = m;
+        p.wall = wid;
+        split_double(tmax, p.tmax_hi, p.tmax_lo);
+        for (int c = 0; c < 3; c++) {
+            split_double(r0[c], p.r0_hi[c], p.r0_lo[c]);
+            split_double(k[c], p.k_hi[c], p.k_lo[c]);
+        }
+        const float4 *src = reinterpret_cast<const float4 *>(&p);
+        float4 *dst = reinterpret_cast<float4 *>(out);
+        for (int q = 0; q < 4; q++) dst[q] = src[q];
     }
 }
 
-cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int fp32,
+cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,
                           int32_t *out_caller, int sms, cudaStream_t s) {
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
-    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, fp32, out_caller, nullptr);
+    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, prep, out_caller);
     return cudaGetLastError();
 }
 

@@ -63,13 +63,24 @@ struct GridDev {
     int64_t max_steps;
 };
 
+// Per-ray record written by the start-cell kernel (full warps, where the
+// float64 set-up is cheap) and read once by the traversal kernel when the
+// ray starts (64 bytes).
+struct RayPrep {
+    int32_t cell;             // start cell (internal); -1 outside the box, -2 direction not unit
+    int32_t wall;             // wall the ray leaves through (Eq. 5), -1..-6
+    float tmax_hi, tmax_lo;   // distance to that wall, as a float pair
+    float r0_hi[3], r0_lo[3]; // origin as float pairs
+    float k_hi[3], k_lo[3];   // direction as float pairs
+};
+
 // A batch work descriptor: rays of one grid.
 struct RaySetDev {
     const double *origin;
     const double *dir;
     void *tau;                // float (float32 form) or double (float64 form), nullable
     int32_t *status;          // nullable
-    int32_t *start;           // located start cells (internal) - work buffer
+    RayPrep *start;           // per-ray start records - work buffer
     int64_t n;
     int64_t first;            // global index of the first ray of this set
     int32_t grid;             // index into the GridDev array
@@ -90,6 +101,7 @@ struct GridView {
     int device;
     int sms;
     const GridDev *d_desc;
+    GridDev hd;  // host copy of *d_desc
     int lanes_per_ray, block, blocks_per_sm;
 };
 int grid_view(const struct vgrid *g, GridView *out);  // 0, or -1 for a host-only grid

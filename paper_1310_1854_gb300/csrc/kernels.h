@@ -22,12 +22,18 @@ struct TraceArgs {
     int64_t seg_cap;          // entries of seg_cell / seg_len; writes beyond are dropped
     const float *dL_dtau;
     float *dL_drho;
+    // single-grid launches read the grid and the ray set from here (kernel
+    // parameter space) instead of from `grids` / `sets`
+    GridDev g1;
+    RaySetDev s1;
 };
 
 
-// fn[fp64][mode]: trace kernels of one lanes-per-ray value (nullptr if absent)
+// fn[fp64][mode]: single-grid trace kernels of one lanes-per-ray value
+// (nullptr if absent); batch: the float32 tau kernel over many grids
 struct KernelSet {
     const void *fn[2][4];
+    const void *batch;
 };
 
 void kernel_table_lpr1(KernelSet &k);
@@ -39,7 +45,9 @@ void kernel_table_lpr8(KernelSet &k);
 cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s);
 cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long long *queue, StatsDev *stats,
                            cudaStream_t s);
-cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int fp32,
+// what the start-cell kernel writes per ray (see locate_kernel)
+enum { PREP_CELL32 = 0, PREP_FP32 = 1, PREP_FP64 = 2, PREP_CELL64 = 3 };
+cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,
                           int32_t *out_caller, int sms, cudaStream_t s);
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, int64_t M, float *rho_internal,
                                    cudaStream_t s);

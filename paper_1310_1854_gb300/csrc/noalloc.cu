@@ -22,10 +22,11 @@ namespace {
 constexpr size_t kQueueOff = 0;     // unsigned long long work counter
 constexpr size_t kStatsOff = 64;    // StatsDev
 constexpr size_t kSetOff = 256;     // RaySetDev
-constexpr size_t kStartOff = 512;   // int32 start cell per ray
+constexpr size_t kStartOff = 512;   // RayPrep start record per ray
 static_assert(sizeof(StatsDev) <= kSetOff - kStatsOff, "stats slot");
 static_assert(sizeof(RaySetDev) <= kStartOff - kSetOff, "ray-set slot");
-static_assert(kStartOff + 4 * (size_t)VGRID_NOALLOC_MAX_RAYS == (size_t)VGRID_NOALLOC_SCRATCH_BYTES, "size");
+static_assert(sizeof(RayPrep) == 64, "start record");
+static_assert(kStartOff + sizeof(RayPrep) * (size_t)VGRID_NOALLOC_MAX_RAYS == (size_t)VGRID_NOALLOC_SCRATCH_BYTES, "size");
 
 static __device__ __align__(256) unsigned char vg_noalloc_scratch[VGRID_NOALLOC_SCRATCH_BYTES];
 
@@ -80,13 +81,14 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
         auto *queue = reinterpret_cast<unsigned long long *>(base + kQueueOff);
         auto *stats = reinterpret_cast<StatsDev *>(base + kStatsOff);
         auto *dset = reinterpret_cast<RaySetDev *>(base + kSetOff);
-        auto *start = reinterpret_cast<int32_t *>(base + kStartOff);
+        auto *start = reinterpret_cast<RayPrep *>(base + kStartOff);
         cudaStream_t s = (cudaStream_t)stream;
         const int fp64 = precision == VGRID_FP64;
         RaySetDev set{origin, dir, tau, ray_status, start, N, 0, 0, 0};
         // clears the counter and statistics left by the previous call
         if ((e = vg::launch_prepare(dset, set, queue, stats, s)) != cudaSuccess ||
-            (e = vg::launch_locate(v.d_desc, dset, 1, N, !fp64, nullptr, v.sms, s)) != cudaSuccess) {
+            (e = vg::launch_locate(v.d_desc, dset, 1, N, fp64 ? vg::PREP_FP64 : vg::PREP_FP32, nullptr, v.sms,
+                                   s)) != cudaSuccess) {
             rc = fail(VGRID_ERR_CUDA, cudaGetErrorString(e));
             break;
         }
@@ -112,6 +114,8 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
         a.total = N;
         a.queue = queue;
         a.stats = stats;
+        a.g1 = v.hd;
+        a.s1 = set;
         void *args[] = {&a};
         e = cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.block), args, 0, s);
         if (e != cudaSuccess) rc = fail(VGRID_ERR_CUDA, std::string("cudaLaunchKernel: ") + cudaGetErrorString(e));

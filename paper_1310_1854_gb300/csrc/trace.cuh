@@ -250,42 +250,47 @@ static __device__ __noinline__ int locate_point(const GridDev *gp, double x, dou
 struct Cand32 {
     float L1, L2;        // smallest and second smallest lower bound
     int j1;              // id with the smallest lower bound (internal), kNone if none
-    float num, den, dnum, dden;
-    float4 q;            // site record of j1
 };
 
-// Bisector of the current site (origin of the local frame) and site q.
-// Bounds (in units of u = 2^-24, for n~ = fl(q - p), r~ within 2u|r| + e_r):
-//   |den~ - n.k|  <= 6 |n~|_1                       (two roundings of n, three of the dot)
-//   |num~ - n.w|  <= |n~|_1 (4 |n~|_1 + 8 |r~|_1) + 2 e_r |n~|_1, w = n/2 - r
-// Planes with den~ <= -|den error| face away for certain (R2); the others
-// get the lower bound max(num~ - dnum, 0) / (den~ + dden) on s (Eq. 4).
+// Terms of the bisector of the current site (origin of the local frame) and
+// site q, with their rounding-error bounds (u = 2^-24, n~ = fl(q - p),
+// r~ within 2u|r| + e_r):
+//   |den~ - n.k|  <= dden = 6u |n~|_1               (two roundings of n, three of the dot)
+//   |num~ - n.w|  <= dnum = |n~|_1 (4u |n~|_1 + 8u |r~|_1 + 2 e_r),   w = n/2 - r
+struct Plane32 {
+    float num, den, dnum, dden;
+};
+
+__device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float pmz, float rx, float ry, float rz,
+                                           float rr, float Kx, float Ky, float Kz) {
+    Plane32 p;
+    const float nx = __fsub_rn(q.x, pmx), ny = __fsub_rn(q.y, pmy), nz = __fsub_rn(q.z, pmz);
+    p.den = __fmaf_rn(nz, Kz, __fmaf_rn(ny, Ky, __fmul_rn(nx, Kx)));
+    const float n1 = __fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz));
+    p.dden = __fmul_rn(kCDen, n1);
+    const float wx = __fmaf_rn(0.5f, nx, -rx), wy = __fmaf_rn(0.5f, ny, -ry), wz = __fmaf_rn(0.5f, nz, -rz);
+    p.num = __fmaf_rn(nz, wz, __fmaf_rn(ny, wy, __fmul_rn(nx, wx)));
+    p.dnum = __fmul_rn(n1, __fmaf_rn(kCA, n1, rr));
+    return p;
+}
+
+// Planes with den~ <= -dden face away for certain (R2); the others get the
+// lower bound max(num~ - dnum, 0) / (den~ + dden) on s (Eq. 4), rounded down.
+// Branch-free: in a warp some lane nearly always has a plane facing ahead,
+// so skipping the numerator for planes facing away (the sign shortcut of
+// Sect. 2.2) would only add divergence; a masked result costs nothing more.
+// Padding slots (j < 0) are masked the same way.
 __device__ __forceinline__ void consider32(int j, float4 q, float pmx, float pmy, float pmz, float rx, float ry,
                                            float rz, float rr, float Kx, float Ky, float Kz, Cand32 &c) {
-    const float nx = __fsub_rn(q.x, pmx), ny = __fsub_rn(q.y, pmy), nz = __fsub_rn(q.z, pmz);
-    const float den = __fmaf_rn(nz, Kz, __fmaf_rn(ny, Ky, __fmul_rn(nx, Kx)));
-    const float n1 = __fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz));
-    const float dden = __fmul_rn(kCDen, n1);
-    if (den > -dden) {
-        const float wx = __fmaf_rn(0.5f, nx, -rx), wy = __fmaf_rn(0.5f, ny, -ry), wz = __fmaf_rn(0.5f, nz, -rz);
-        const float num = __fmaf_rn(nz, wz, __fmaf_rn(ny, wy, __fmul_rn(nx, wx)));
-        const float dnum = __fmul_rn(n1, __fmaf_rn(kCA, n1, rr));
-        const float num_lo = fmaxf(__fsub_rd(num, dnum), 0.0f);
-        const float den_hi = __fadd_ru(den, dden);
-        const float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
-        if (lower < c.L1) {
-            c.L2 = c.L1;
-            c.L1 = lower;
-            c.j1 = j;
-            c.num = num;
-            c.den = den;
-            c.dnum = dnum;
-            c.dden = dden;
-            c.q = q;
-        } else if (lower < c.L2) {
-            c.L2 = lower;
-        }
-    }
+    const Plane32 p = plane32(q, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz);
+    const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
+    const float den_hi = __fadd_ru(p.den, p.dden);
+    float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
+    lower = (j >= 0 && p.den > -p.dden) ? lower : __int_as_float(0x7f800000);
+    const bool b = lower < c.L1;
+    c.L2 = b ? c.L1 : fminf(c.L2, lower);
+    c.j1 = b ? j : c.j1;
+    c.L1 = fminf(c.L1, lower);
 }
 
 template <int LPR>
@@ -293,14 +298,16 @@ __device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float p
                                        float rz, float rr, float Kx, float Ky, float Kz, unsigned gmask, int gl,
                                        int gbase, Cand32 &c) {
     const int4 *lst = reinterpret_cast<const int4 *>(h.nbr + off);
-    int4 v = __ldg(lst + gl);  // every list owns >= 1 chunk; the array is padded past its end
+    // every list owns >= 1 chunk and the array is padded past its end, so the
+    // first chunk of every lane and one chunk ahead can be read speculatively
+    int4 v = __ldg(lst + gl);
     const int cnt = LPR == 1 ? v.x : __shfl_sync(gmask, v.x, gbase);
     const int nch = (cnt + 4) >> 2;
+    int4 vn = __ldg(lst + gl + LPR);
     c.L1 = __int_as_float(0x7f800000);
     c.L2 = c.L1;
     c.j1 = kNone;
     for (int ch = gl; ch < nch; ch += LPR) {
-        if (ch != gl) v = __ldg(lst + ch);
         const int p = ch * 4;
         const int j0 = (p >= 1 && p <= cnt) ? v.x : -8;
         const int j1 = (p + 1 <= cnt) ? v.y : -8;
@@ -311,10 +318,14 @@ __device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float p
         const float4 q1 = j1 >= 0 ? __ldg(&h.site[j1]) : z4;
         const float4 q2 = j2 >= 0 ? __ldg(&h.site[j2]) : z4;
         const float4 q3 = j3 >= 0 ? __ldg(&h.site[j3]) : z4;
-        if (j0 >= 0) consider32(j0, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        if (j1 >= 0) consider32(j1, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        if (j2 >= 0) consider32(j2, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        if (j3 >= 0) consider32(j3, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        // ids two chunks ahead travel while this chunk is tested
+        const int4 vnn = ch + 2 * LPR < nch ? __ldg(lst + ch + 2 * LPR) : vn;
+        consider32(j0, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(j1, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(j2, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(j3, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        v = vn;
+        vn = vnn;
     }
     if (LPR > 1) {
         int win = gl;
@@ -330,16 +341,7 @@ __device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float p
             }
             c.L2 = nL2;
         }
-        const int src = gbase + win;
-        c.j1 = __shfl_sync(gmask, c.j1, src);
-        c.num = __shfl_sync(gmask, c.num, src);
-        c.den = __shfl_sync(gmask, c.den, src);
-        c.dnum = __shfl_sync(gmask, c.dnum, src);
-        c.dden = __shfl_sync(gmask, c.dden, src);
-        c.q.x = __shfl_sync(gmask, c.q.x, src);
-        c.q.y = __shfl_sync(gmask, c.q.y, src);
-        c.q.z = __shfl_sync(gmask, c.q.z, src);
-        c.q.w = __shfl_sync(gmask, c.q.w, src);
+        c.j1 = __shfl_sync(gmask, c.j1, gbase + win);
     }
 }
 
@@ -357,7 +359,9 @@ __device__ __forceinline__ int find_set(const RaySetDev *sets, int nsets, int64_
     return lo;
 }
 
-template <int LPR, bool FP64, int MODE>
+// BATCH = false: one grid, read from the parameter space (a.g1, a.s1);
+// BATCH = true: many grids and ray sets, looked up per ray.
+template <int LPR, bool FP64, int MODE, bool BATCH>
 __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     static_assert(LPR == 1 || LPR == 2 || LPR == 4 || LPR == 8, "lanes per ray");
     const int lane = threadIdx.x & 31;
@@ -365,18 +369,22 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     const int gbase = lane & ~(LPR - 1);
     const unsigned gmask = ((1u << LPR) - 1u) << gbase;
 
-    // per-thread statistics (group leaders count)
-    unsigned st_rays = 0, st_cross = 0, st_dec = 0, st_re = 0, st_fb = 0, st_zero = 0, st_lim = 0, st_out = 0,
-             st_bad = 0;
+    // statistics: block counters in shared memory, updated by group leaders
+    // once per ray and on rare events, added to the global counters at exit
+    __shared__ unsigned long long s_stats[9];
+    if (threadIdx.x < 9) s_stats[threadIdx.x] = 0ull;
+    __syncthreads();
+    enum { S_RAYS, S_CROSS, S_DEC, S_RE, S_FB, S_ZERO, S_LIM, S_OUT, S_BAD };
+#define VG_STAT(i, v) atomicAdd(&s_stats[i], (unsigned long long)(v))
 
     int64_t ray = -1;       // global work index; -1 wants a ray, -2 finished
     int set = 0;
     int64_t li = 0;         // index within the set
-    const GridDev *gp = a.grids;
-    Hot h{nullptr, nullptr, nullptr};
-    const float *rho = nullptr;
-    float kappa = 1.f;
-    int64_t max_steps = 0;
+    const GridDev *gp = a.grids;  // device copy of the descriptor (cold paths)
+    Hot h{a.g1.site, a.g1.nbr, a.g1.perm};
+    const float *rho = a.g1.rho;
+    float kappa = a.g1.kappa;
+    int max_steps = (int)min(a.g1.max_steps, (int64_t)0x7fffffff);
     // float64 form: current point and direction
     double r64[3] = {0, 0, 0}, k64[3] = {0, 0, 0};
     // float32 form: origin and direction as float pairs, ray parameter t, wall exit
@@ -411,75 +419,69 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
 
         if (need && ray >= 0) {
             // ---------------- start a ray ----------------
-            set = find_set(a.sets, a.nsets, ray);
-            const RaySetDev *rs = &a.sets[set];
-            li = ray - rs->first;
-            gp = a.grids + rs->grid;
-            h.site = gp->site;
-            h.nbr = gp->nbr;
-            h.perm = gp->perm;
-            rho = gp->rho;
-            kappa = gp->kappa;
-            max_steps = gp->max_steps;
-            const double *o = rs->origin + 3 * li;
-            const double *d = rs->dir + 3 * li;
-            for (int c = 0; c < 3; c++) {
-                r64[c] = __ldg(o + c);
-                k64[c] = __ldg(d + c);
+            const RaySetDev *rs = &a.s1;
+            li = ray;
+            if (BATCH) {
+                set = find_set(a.sets, a.nsets, ray);
+                rs = &a.sets[set];
+                li = ray - rs->first;
+                gp = a.grids + rs->grid;
+                h.site = gp->site;
+                h.nbr = gp->nbr;
+                h.perm = gp->perm;
+                rho = gp->rho;
+                kappa = gp->kappa;
+                max_steps = (int)min(gp->max_steps, (int64_t)0x7fffffff);
             }
             nseg = 0;
             zrun = 0;
             steps = 0;
-            status = RAY_OK;
             tau64 = 0.0;
             tau32 = 0.f;
             tauc = 0.f;
             th = tl = 0.f;
             if (MODE == MODE_FILL) seg_base = a.seg_off[ray];
             if (MODE == MODE_GRAD) dLr = __ldg(&a.dL_dtau[ray]);
-            const double kk = __dadd_rn(__dadd_rn(__dmul_rn(k64[0], k64[0]), __dmul_rn(k64[1], k64[1])),
-                                        __dmul_rn(k64[2], k64[2]));
-            m = rs->start[li];
-            if (!(fabs(kk - 1.0) <= 2.000001e-6)) {
-                status = RAY_BAD_DIR;
-            } else if (m < 0) {
-                status = RAY_OUTSIDE;
+            // the start record was prepared by the start-cell kernel
+            const RayPrep *pr = rs->start + li;
+            if (FP64) {
+                m = pr->cell;
+                if (m >= 0) {
+                    const double *o = rs->origin + 3 * li;
+                    const double *d = rs->dir + 3 * li;
+                    for (int c = 0; c < 3; c++) {
+                        r64[c] = __ldg(o + c);
+                        k64[c] = __ldg(d + c);
+                    }
+                }
             } else {
+                const float4 *p4 = reinterpret_cast<const float4 *>(pr);
+                const float4 a0 = __ldg(p4), a1 = __ldg(p4 + 1), a2 = __ldg(p4 + 2), a3 = __ldg(p4 + 3);
+                m = __float_as_int(a0.x);
+                wall = __float_as_int(a0.y);
+                tmh = a0.z;
+                tml = a0.w;
+                R0h[0] = a1.x; R0h[1] = a1.y; R0h[2] = a1.z;
+                R0l[0] = a1.w; R0l[1] = a2.x; R0l[2] = a2.y;
+                Kh[0] = a2.z;  Kh[1] = a2.w;  Kh[2] = a3.x;
+                Kl[0] = a3.y;  Kl[1] = a3.z;  Kl[2] = a3.w;
+                const float scale = BATCH ? (float)gp->scale : (float)a.g1.scale;
+                er = 16.0f * kU2 * (scale + tmh);
+                ewall = 16.0f * kU2 * tmh;
+            }
+            status = m == -2 ? RAY_BAD_DIR : (m < 0 ? RAY_OUTSIDE : RAY_OK);
+            if (status == RAY_OK) {
                 const float4 q = __ldg(&h.site[m]);
                 pmx = q.x;
                 pmy = q.y;
                 pmz = q.z;
                 off = __float_as_int(q.w);
                 rho_m = __ldg(&rho[m]);
-                if (!FP64) {
-                    // distance to the wall ahead (Eq. 5 for the walls the ray faces)
-                    double tmax = 1e300;
-                    int wid = -1;
-                    for (int c = 0; c < 3; c++) {
-                        if (k64[c] > 0.0) {
-                            const double t = __ddiv_rn(__dsub_rn(gp->hi[c], r64[c]), k64[c]);
-                            if (t < tmax) { tmax = t; wid = -(2 * c + 2); }
-                        } else if (k64[c] < 0.0) {
-                            const double t = __ddiv_rn(__dsub_rn(gp->lo[c], r64[c]), k64[c]);
-                            if (t < tmax) { tmax = t; wid = -(2 * c + 1); }
-                        }
-                    }
-                    if (tmax < 0.0) tmax = 0.0;
-                    wall = wid;
-                    split_double(tmax, tmh, tml);
-                    for (int c = 0; c < 3; c++) {
-                        split_double(r64[c], R0h[c], R0l[c]);
-                        split_double(k64[c], Kh[c], Kl[c]);
-                    }
-                    er = 16.0f * kU2 * ((float)gp->scale + tmh);
-                    ewall = 16.0f * kU2 * tmh;
-                }
             }
             if (status != RAY_OK) {
                 if (gl == 0) {
-                    st_rays++;
-                    if (status == RAY_OUTSIDE) st_out++;
-                    if (status == RAY_BAD_DIR) st_bad++;
+                    VG_STAT(S_RAYS, 1);
+                    VG_STAT(status == RAY_OUTSIDE ? S_OUT : S_BAD, 1);
                     if (MODE == MODE_TAU || MODE == MODE_FILL) {
                         if (rs->tau) {
                             if (FP64) ((double *)rs->tau)[li] = 0.0;
@@ -528,11 +530,16 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 c.L2 = lw;
             }
             float upper;
+            Plane32 w1{0.f, 1.f, 0.f, 0.f};
             if (wall_wins) {
                 upper = __fadd_ru(sw, Ew);
             } else {
-                const float den_lo = __fsub_rd(c.den, c.dden);
-                const float num_hi = fmaxf(__fadd_ru(c.num, c.dnum), 0.0f);
+                // the winner's terms again (same operations, same values)
+                qn = __ldg(&h.site[c.j1]);
+                have_q = true;
+                w1 = plane32(qn, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2]);
+                const float den_lo = __fsub_rd(w1.den, w1.dden);
+                const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
                 upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : __int_as_float(0x7f800000);
             }
             if (upper < c.L2) {
@@ -540,15 +547,15 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     len = fmaxf(sw, 0.0f);
                     nxt = wall;
                 } else {
-                    len = __fdiv_rn(fmaxf(c.num, 0.0f), c.den);
+                    // den > dden > 0 here; 2-ulp division (the length only feeds tau and t)
+                    len = __fdividef(fmaxf(w1.num, 0.0f), w1.den);
                     nxt = c.j1;
-                    qn = c.q;
-                    have_q = true;
                 }
             } else {
+                have_q = false;
                 // float64 recheck of this crossing from r = r0 + t k
-                if (gl == 0) st_re++;
-                const RaySetDev *rs = &a.sets[set];
+                if (gl == 0) VG_STAT(S_RE, 1);
+                const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
                 const double *o = rs->origin + 3 * li;
                 const double *d = rs->dir + 3 * li;
                 double kd[3], rp[3];
@@ -563,7 +570,6 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             }
         }
 
-        if (gl == 0) st_dec++;
         steps++;
         bool relocate = false;
         if (nxt == kNone) {
@@ -581,7 +587,6 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 }
                 if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[__ldg(&h.perm[m])], dLr * kappa * len);
                 nseg++;
-                if (gl == 0) st_cross++;
                 if (FP64) {
                     tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)rho_m), s64));
                 } else {
@@ -594,7 +599,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 zrun = 0;
             } else {
                 zrun++;
-                if (gl == 0) st_zero++;
+                if (gl == 0) VG_STAT(S_ZERO, 1);
             }
             // advance the point
             if (FP64) {
@@ -618,7 +623,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             }
         }
         if (relocate) {
-            if (gl == 0) st_fb++;
+            if (gl == 0) VG_STAT(S_FB, 1);
             zrun = 0;
             double x[3];
             if (FP64) {
@@ -626,7 +631,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 for (int c = 0; c < 3; c++) x[c] = r64[c];
             } else {
                 ff_add_double(th, tl, gp->eps32);
-                const RaySetDev *rs = &a.sets[set];
+                const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
                 const double t = __dadd_rn((double)th, (double)tl);
                 for (int c = 0; c < 3; c++) x[c] = __fma_rn(t, __ldg(rs->dir + 3 * li + c), __ldg(rs->origin + 3 * li + c));
             }
@@ -646,12 +651,14 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         if (!ended && steps >= max_steps) {
             ended = true;
             status = RAY_STEP_LIMIT;
-            if (gl == 0) st_lim++;
+            if (gl == 0) VG_STAT(S_LIM, 1);
         }
         if (ended) {
             if (gl == 0) {
-                st_rays++;
-                const RaySetDev *rs = &a.sets[set];
+                VG_STAT(S_RAYS, 1);
+                VG_STAT(S_CROSS, nseg);
+                VG_STAT(S_DEC, steps);
+                const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
                 if (MODE == MODE_TAU || MODE == MODE_FILL) {
                     if (rs->tau) {
                         if (FP64) ((double *)rs->tau)[li] = tau64;
@@ -665,14 +672,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         }
     }
 
-    // ---------------- statistics: one atomic per warp and counter ----------------
-    const unsigned vals[9] = {st_rays, st_cross, st_dec, st_re, st_fb, st_zero, st_lim, st_out, st_bad};
-    unsigned long long *dst = reinterpret_cast<unsigned long long *>(a.stats);
-#pragma unroll
-    for (int i = 0; i < 9; i++) {
-        const unsigned v = __reduce_add_sync(0xffffffffu, vals[i]);
-        if (lane == 0 && v) atomicAdd(dst + i, (unsigned long long)v);
-    }
+    // ---------------- statistics: one global atomic per block and counter ----------------
+#undef VG_STAT
+    __syncthreads();
+    if (threadIdx.x < 9 && s_stats[threadIdx.x])
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + threadIdx.x, s_stats[threadIdx.x]);
 }
 
 }  // namespace vg

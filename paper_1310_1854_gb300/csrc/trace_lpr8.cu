@@ -5,14 +5,15 @@
 namespace vg {
 
 void kernel_table_lpr8(KernelSet &k) {
-    k.fn[0][MODE_TAU] = (const void *)trace_kernel<8, false, MODE_TAU>;
-    k.fn[0][MODE_COUNT] = (const void *)trace_kernel<8, false, MODE_COUNT>;
-    k.fn[0][MODE_FILL] = (const void *)trace_kernel<8, false, MODE_FILL>;
-    k.fn[0][MODE_GRAD] = (const void *)trace_kernel<8, false, MODE_GRAD>;
-    k.fn[1][MODE_TAU] = (const void *)trace_kernel<8, true, MODE_TAU>;
-    k.fn[1][MODE_COUNT] = (const void *)trace_kernel<8, true, MODE_COUNT>;
-    k.fn[1][MODE_FILL] = (const void *)trace_kernel<8, true, MODE_FILL>;
+    k.fn[0][MODE_TAU] = (const void *)trace_kernel<8, false, MODE_TAU, false>;
+    k.fn[0][MODE_COUNT] = (const void *)trace_kernel<8, false, MODE_COUNT, false>;
+    k.fn[0][MODE_FILL] = (const void *)trace_kernel<8, false, MODE_FILL, false>;
+    k.fn[0][MODE_GRAD] = (const void *)trace_kernel<8, false, MODE_GRAD, false>;
+    k.fn[1][MODE_TAU] = (const void *)trace_kernel<8, true, MODE_TAU, false>;
+    k.fn[1][MODE_COUNT] = (const void *)trace_kernel<8, true, MODE_COUNT, false>;
+    k.fn[1][MODE_FILL] = (const void *)trace_kernel<8, true, MODE_FILL, false>;
     k.fn[1][MODE_GRAD] = nullptr;
+    k.batch = (const void *)trace_kernel<8, false, MODE_TAU, true>;
 }
 
 }  // namespace vg

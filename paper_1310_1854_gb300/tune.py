@@ -1,0 +1,114 @@
+"""Launch-shape autotuner for the traversal kernels.
+
+The shape that traces fastest depends on the GPU, the arithmetic form and
+the workload (sites per grid, rays, mean path length): lanes per ray
+(1, 2, 4, 8), threads per block, and persistent blocks per SM. The tuner
+times each candidate shape with CUDA events on a seeded sample of the
+caller's rays, keeps the fastest, and caches it per (GPU, form, size class)
+in a JSON file so later runs skip the search.
+
+Timing uses the library's own event record around the traversal launch
+(vgrid_enable_timing / vgrid_read_timing), so only kernel time counts.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+from typing import Callable, Iterable
+
+DEFAULT_SPACE = tuple((l, b, 0) for l in (1, 2, 4) for b in (128, 256))
+_lock = threading.Lock()
+
+
+def cache_path() -> str:
+    p = os.environ.get("VGRID_TUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "vgrid", "tune.json")
+
+
+def shape_key(gpu: str, precision: str, sites: int, rays: int) -> str:
+    """Size class: powers of two of the site and ray counts."""
+    ls = int(round(math.log2(max(sites, 1))))
+    lr = int(round(math.log2(max(rays, 1))))
+    return f"{gpu}|{precision}|M2^{ls}|N2^{lr}"
+
+
+def load_cache(path: str | None = None) -> dict:
+    path = path or cache_path()
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def store(key: str, entry: dict, path: str | None = None) -> None:
+    path = path or cache_path()
+    with _lock:
+        d = load_cache(path)
+        d[key] = entry
+        os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+        tmp = f"{path}.{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(d, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def search(space: Iterable[tuple[int, int, int]], time_fn: Callable[[tuple[int, int, int]], float],
+           repeats: int = 3) -> tuple[tuple[int, int, int], dict]:
+    """Best shape of `space` by the smallest median of `repeats` timings."""
+    results = {}
+    for shape in space:
+        ts = sorted(time_fn(shape) for _ in range(repeats))
+        results[shape] = ts[len(ts) // 2]
+    best = min(results, key=results.get)
+    return best, {f"{l},{b},{s}": t for (l, b, s), t in results.items()}
+
+
+def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200_000, space=DEFAULT_SPACE,
+             use_cache: bool = True, path: str | None = None) -> dict:
+    """Pick and apply the fastest launch shape for tracing these rays
+    through `grid`; returns {"lanes_per_ray", "block", "blocks_per_sm",
+    "ms", "cached", "key"}."""
+    import torch
+
+    name = torch.cuda.get_device_name(grid.device).replace("|", "/")
+    key = shape_key(name, precision, grid.M, origin.shape[0])
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit:
+            grid.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"])
+            return dict(hit, cached=True, key=key)
+    n = min(sample, origin.shape[0])
+    g = torch.Generator(device="cpu").manual_seed(1310_1854)
+    sel = torch.randperm(origin.shape[0], generator=g)[:n].sort().values.to(origin.device)
+    o = origin.index_select(0, sel).contiguous()
+    d = direction.index_select(0, sel).contiguous()
+    tau = torch.empty(n, dtype=torch.float64 if precision == "fp64" else torch.float32, device=origin.device)
+    prev = grid.get_launch()
+
+    def time_fn(shape):
+        grid.set_launch(*shape)
+        grid.trace(o, d, precision=precision, out_tau=tau)  # warm
+        grid.enable_timing(True)
+        grid.read_timing()
+        grid.trace(o, d, precision=precision, out_tau=tau)
+        _, ms, launches = grid.read_timing()
+        grid.enable_timing(False)
+        return ms / max(launches, 1)
+
+    try:
+        best, table = search(space, time_fn)
+    except Exception:
+        grid.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"])
+        raise
+    grid.set_launch(*best)
+    entry = {"lanes_per_ray": best[0], "block": best[1], "blocks_per_sm": best[2], "ms": table[f"{best[0]},{best[1]},{best[2]}"],
+             "sample_rays": n, "table": table}
+    if use_cache:
+        store(key, entry, path)
+    return dict(entry, cached=False, key=key)

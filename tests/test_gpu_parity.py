@@ -276,3 +276,76 @@ def test_batched_matches_single():
     ok = ref.near_tie == 0
     t = b.tau[3].cpu().numpy().astype(np.float64)
     assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
+
+
+@pytest.mark.slow
+def test_full_size_config5_gradient_sampled():
+    """10^6-site disk with the 512^2 detector and 10^6 interior rays: tau of
+    every ray is traced; the adjoint of a seeded subset of 64 rays is
+    compared cell by cell with the oracle's gradient of the same rays (all
+    sites as candidates), and the gradient of all rays is checked for
+    linearity in dL/dtau."""
+    g, det, inner, rho_t = gen.config5()
+    rays = gen.concat_rays(det, inner)
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    r = vg.trace(O, D, precision="fp32", stats=True, status=True)
+    assert np.all(r.status.cpu().numpy() == 0)
+    tau = r.tau
+    # loss against the perturbed-density target
+    vg.set_density(dev(rho_t), 1.0)
+    target = torch.exp(-vg.trace(O, D, precision="fp32").tau)
+    vg.set_density(dev(g.rho), 1.0)
+    dL = (-2.0 * (torch.exp(-tau) - target) * torch.exp(-tau)).float()
+    full = vg.trace_grad(O, D, dL)
+    half = vg.trace_grad(O, D, 0.5 * dL)
+    np.testing.assert_allclose(half.cpu().numpy(), 0.5 * full.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    sample = np.sort(gen.rng_for(111).choice(len(rays.origin), 64, replace=False))
+    ref = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sample], rays.dir[sample])
+    keep = ref.near_tie == 0
+    sel = sample[keep]
+    dls = dL.cpu().numpy().astype(np.float64)[sel]
+    sub = oracle.Trace(*(getattr(ref, f)[keep] for f in ("nseg", "seg_cell", "seg_len", "tau", "length",
+                                                         "min_margin", "near_tie", "nfallback", "status")))
+    want = oracle.tau_grad(sub, len(g.sites), dls)
+    got = vg.trace_grad(dev(rays.origin[sel]), dev(rays.dir[sel]), dev(dls.astype(np.float32)))
+    got = got.cpu().numpy().astype(np.float64)
+    big = np.abs(want) > 1e-6 * np.abs(want).max()
+    assert big.sum() > 1000
+    rel = np.abs(got[big] - want[big]) / np.abs(want[big])
+    assert rel.max() <= 1e-4, rel.max()
+    assert np.all(got[want == 0] == 0)
+    # tau of the sampled rays against the oracle
+    t = tau.cpu().numpy().astype(np.float64)[sel]
+    assert np.all(np.abs(t - ref.tau[keep]) <= TAU32_REL * ref.tau[keep])
+
+
+@pytest.mark.slow
+def test_full_size_config4_batched_sampled():
+    """64 grids of uneven size (2.75e6 sites, ~1.4e7 rays in total) in one
+    persistent launch and its CUDA-graph replay; 4 rays from each of 8 grids
+    against the oracle, and every grid's tau against its own single-grid
+    launch."""
+    from paper_1310_1854_gb300 import Batch
+    sets = gen.config4()
+    grids = []
+    for gg, rr in sets:
+        vg = make(gg)
+        grids.append((vg, dev(rr.origin), dev(rr.dir)))
+    b = Batch(grids)
+    st = b.run(stats=True)
+    assert st["rays"] == sum(len(rr.origin) for _, rr in sets) and st["step_limit"] == 0
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.run(graph=True, stream=s)
+    s.synchronize()
+    for k in range(0, 64, 8):
+        vg, O, D = grids[k]
+        single = vg.trace(O, D, precision="fp32").tau.cpu().numpy()
+        np.testing.assert_array_equal(b.tau[k].cpu().numpy(), single)
+        gg, rr = sets[k]
+        sample = np.sort(gen.rng_for(200 + k).choice(len(rr.origin), 4, replace=False))
+        ref = oracle.trace(gg.sites, gg.box, gg.rho.astype(np.float64), rr.origin[sample], rr.dir[sample])
+        t = single.astype(np.float64)[sample]
+        ok = ref.near_tie == 0
+        assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
