@@ -207,10 +207,14 @@ def main():
     ap.add_argument("--block", type=int, default=int(os.environ.get("VGRID_BLOCK", "0")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=1_000_000)
+    ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6"],
+                    help="disk1e5 is the benchmark line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
+    if args.workload != "disk1e5":
+        return run_extra(args)
 
     import torch
     import torch.distributed as tdist
@@ -369,6 +373,126 @@ def main():
     print(json.dumps(line), flush=True)
     if ws > 1:
         tdist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# other workloads (one GPU): 10^6 clumpy sites, 64 uneven grids in one
+# launch, and the adjoint on the 10^6-site disk
+# ---------------------------------------------------------------------------
+
+def _events_ms(fn, steps, flush):
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record()
+        fn()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def run_extra(args):
+    import torch
+
+    import gen
+    from paper_1310_1854_gb300 import Batch, VoronoiGrid
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peaks()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+    sampler = ClockSampler(gpu_index(0))
+    if args.workload in ("clumpy1e6", "grad1e6"):
+        t0 = time.time()
+        if args.workload == "clumpy1e6":
+            g, rays = gen.config3()
+            rho = g.rho
+            desc = "clumpy 1e6 sites (2,000 clumps), 1e7 uniform rays, tau per ray"
+        else:
+            g, det, inner, rho_t = gen.config5()
+            rays = gen.concat_rays(det, inner)
+            rho = g.rho
+            desc = "exp-disk 1e6 sites, 512^2 detector + 1e6 interior rays, tau and adjoint d loss / d rho"
+        vg = VoronoiGrid(g.sites, g.box)
+        vg.set_density(torch.from_numpy(rho).to(dev))
+        build_s = time.time() - t0
+        info = vg.info()
+        O = torch.from_numpy(rays.origin).to(dev)
+        D = torch.from_numpy(rays.dir).to(dev)
+        N = O.shape[0]
+        tau = torch.empty(N, dtype=torch.float32, device=dev)
+        st = vg.trace(O, D, precision="fp32", stats=True).stats
+        deg = info["nnz"] / info["M"]
+        bpc = 28.0 + 20.0 * deg
+        if args.workload == "clumpy1e6":
+            fn = lambda: vg.trace(O, D, precision="fp32", out_tau=tau)
+        else:
+            vg.set_density(torch.from_numpy(rho_t).to(dev))
+            target = torch.exp(-vg.trace(O, D, precision="fp32").tau)
+            vg.set_density(torch.from_numpy(rho).to(dev))
+            grad = torch.zeros(g.sites.shape[0], dtype=torch.float32, device=dev)
+
+            def fn():
+                t = vg.trace(O, D, precision="fp32", out_tau=tau).tau
+                e = torch.exp(-t)
+                dL = -2.0 * (e - target) * e
+                grad.zero_()
+                vg.trace_grad(O, D, dL, out=grad)
+        for _ in range(args.warmup):
+            fn()
+        vg.enable_timing(True)
+        vg.read_timing()
+        sampler.start()
+        ms = _events_ms(fn, args.steps, flush)
+        clocks = sampler.stop()
+        loc_ms, tr_ms, launches = vg.read_timing()
+        vg.enable_timing(False)
+        passes = 1 if args.workload == "clumpy1e6" else 2
+        segs = st["crossings"] * passes
+        kern = tr_ms / max(launches, 1)
+        line.update({"value": segs * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "config": {"workload": desc, "sites": info["M"], "rays": N, "mean_degree": round(deg, 3),
+                                "traversals_per_step": passes, "host_build_s": round(build_s, 2),
+                                "device_bytes": info["device_bytes"], "l2": "flushed between timed steps"},
+                     "stats_per_traversal": st, "rays_per_s": N * passes * args.steps / (ms / 1e3),
+                     "gpu_launches": 3 * passes * args.steps,
+                     "roofline": {"bound": "hbm", "achieved": st["crossings"] * bpc / (kern / 1e3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": st["crossings"] * bpc / (kern / 1e3) / 1e9 / peak,
+                                  "traffic": None, "kernel_ms_per_launch": kern,
+                                  "algorithmic_bytes_per_crossing": bpc, "peak_source": peak_kind},
+                     "e2e": None, "clocks": clocks})
+    else:
+        t0 = time.time()
+        sets = gen.config4()
+        grids = []
+        total_sites = 0
+        for g, r in sets:
+            vg = VoronoiGrid(g.sites, g.box)
+            vg.set_density(torch.from_numpy(g.rho).to(dev))
+            grids.append((vg, torch.from_numpy(r.origin).to(dev), torch.from_numpy(r.dir).to(dev)))
+            total_sites += g.sites.shape[0]
+        build_s = time.time() - t0
+        b = Batch(grids)
+        st = b.run(stats=True)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            for _ in range(args.warmup):
+                b.run(graph=True, stream=s)
+            s.synchronize()
+            sampler.start()
+            ms = _events_ms(lambda: b.run(graph=True, stream=s), args.steps, flush)
+            clocks = sampler.stop()
+        line.update({"value": st["crossings"] * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "config": {"workload": "64 grids, sites log-uniform 2e3..2e5, rays log-uniform 1e4..1e6, "
+                                            "one persistent launch replayed from a CUDA graph",
+                                "grids": len(sets), "sites": total_sites, "rays": st["rays"],
+                                "host_build_s": round(build_s, 2), "l2": "flushed between timed steps"},
+                     "stats_per_step": st, "rays_per_s": st["rays"] * args.steps / (ms / 1e3),
+                     "gpu_launches": 3 * args.steps, "roofline": None, "e2e": None, "clocks": clocks})
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -83,8 +83,7 @@ struct vgrid {
     GridDev hd{};
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
-    int32_t *d_nbr = nullptr;
-    float *d_rho = nullptr;
+    float4 *d_cells = nullptr;
     int32_t *d_perm = nullptr;
     int32_t *d_blk_off = nullptr;
     int32_t *d_blk_idx = nullptr;
@@ -152,7 +151,7 @@ static void free_events(vgrid_t *g) {
 static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
-    void *ptrs[] = {g->d_desc, g->d_site, g->d_nbr, g->d_rho, g->d_perm, g->d_blk_off, g->d_blk_idx,
+    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_perm, g->d_blk_off, g->d_blk_idx,
                     g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -228,27 +227,43 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
     }
 
-    // neighbour lists: [count, ids..., padding to a multiple of 4], 16-byte aligned
-    std::vector<int32_t> lists;
+    // cell blocks: header (caller id, count, rho = 1, internal id), then one
+    // record per neighbour (site of the neighbour, its block offset) or wall
+    std::vector<int64_t> boffs(M + 1, 0);
+    for (int64_t i = 0; i < M; i++) boffs[i + 1] = boffs[i] + 1 + (g->cells.off[i + 1] - g->cells.off[i]);
+    if (boffs[M] + 8 >= ((int64_t)1 << 31)) {
+        delete g;
+        return fail(VGRID_ERR_NOMEM, "cell blocks exceed 2^31 records");
+    }
+    const int64_t nrec = boffs[M] + 8;  // room past the end for the last block's reads
+    std::vector<float> blocks(4 * nrec, 0.0f);
     std::vector<float> site4(4 * M);
-    lists.reserve(g->cells.idx.size() + 4 * M + 64);
+    auto put_int = [](float *dst, int32_t v) { std::memcpy(dst, &v, 4); };
     for (int64_t i = 0; i < M; i++) {
-        const int64_t off = (int64_t)lists.size();
-        if (off >= ((int64_t)1 << 31) - 64) {
-            delete g;
-            return fail(VGRID_ERR_NOMEM, "neighbour lists exceed 2^31 entries");
-        }
         const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
-        lists.push_back((int32_t)(e - b));
-        for (int64_t q = b; q < e; q++) lists.push_back(g->cells.idx[q]);
-        while (lists.size() % 4) lists.push_back(VG_PAD_ID);
-        int32_t offi = (int32_t)off;
+        float *h = &blocks[4 * boffs[i]];
+        put_int(h + 0, g->perm[i]);
+        put_int(h + 1, (int32_t)(e - b));
+        h[2] = 1.0f;
+        put_int(h + 3, (int32_t)i);
+        for (int64_t q = b; q < e; q++) {
+            float *r = &blocks[4 * (boffs[i] + 1 + (q - b))];
+            const int32_t j = g->cells.idx[q];
+            if (j >= 0) {
+                r[0] = (float)Si[3 * (int64_t)j + 0];
+                r[1] = (float)Si[3 * (int64_t)j + 1];
+                r[2] = (float)Si[3 * (int64_t)j + 2];
+                put_int(r + 3, (int32_t)boffs[j]);
+            } else {
+                put_int(r + 3, j);
+            }
+        }
         site4[4 * i + 0] = (float)Si[3 * i + 0];
         site4[4 * i + 1] = (float)Si[3 * i + 1];
         site4[4 * i + 2] = (float)Si[3 * i + 2];
-        std::memcpy(&site4[4 * i + 3], &offi, 4);
+        put_int(&site4[4 * i + 3], (int32_t)boffs[i]);
     }
-    for (int i = 0; i < 64; i++) lists.push_back(VG_PAD_ID);  // room for speculative chunk reads
+    for (int64_t r = boffs[M]; r < nrec; r++) put_int(&blocks[4 * r + 3], -8);
     std::vector<int32_t> boff(g->blocks.off.size());
     for (size_t i = 0; i < boff.size(); i++) boff[i] = (int32_t)g->blocks.off[i];
 
@@ -276,8 +291,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         return rc;                                                  \
     }
     VG_ALLOC(g->d_site, M);
-    VG_ALLOC(g->d_nbr, lists.size());
-    VG_ALLOC(g->d_rho, M);
+    VG_ALLOC(g->d_cells, nrec);
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
     VG_ALLOC(g->d_blk_idx, g->blocks.idx.size());
@@ -286,11 +300,9 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     VG_ALLOC(g->d_stats, 1);
     VG_ALLOC(g->d_set, 1);
 #undef VG_ALLOC
-    std::vector<float> ones(M, 1.0f);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(g->d_site, site4.data(), sizeof(float) * 4 * M, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_nbr, lists.data(), sizeof(int32_t) * lists.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_rho, ones.data(), sizeof(float) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, blocks.data(), sizeof(float) * 4 * nrec, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !g->blocks.idx.empty())
@@ -298,8 +310,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
 
     GridDev &hd = g->hd;
     hd.site = g->d_site;
-    hd.nbr = g->d_nbr;
-    hd.rho = g->d_rho;
+    hd.cells = g->d_cells;
     hd.perm = g->d_perm;
     hd.blk_off = g->d_blk_off;
     hd.blk_idx = g->d_blk_idx;
@@ -395,7 +406,7 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
     if (!std::isfinite(kappa)) return fail(VGRID_ERR_ARG, "kappa is not finite");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
-    VG_CUDA(vg::launch_permute_density(rho, g->d_perm, g->M, g->d_rho, s));
+    VG_CUDA(vg::launch_permute_density(rho, g->d_perm, g->d_site, g->M, g->d_cells, s));
     g->hd.kappa = kappa;
     VG_CUDA(vg::launch_put_grid(g->d_desc, g->hd, s));
     return VGRID_OK;

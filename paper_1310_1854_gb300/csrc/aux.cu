@@ -94,18 +94,21 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
     return cudaGetLastError();
 }
 
+// rho (caller order) into the headers of the cell blocks
 __global__ void permute_density_kernel(const float *__restrict__ rho_caller, const int32_t *__restrict__ perm,
-                                       int64_t M, float *__restrict__ rho_internal) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
-        rho_internal[i] = __ldg(&rho_caller[__ldg(&perm[i])]);
+                                       const float4 *__restrict__ site, int64_t M, float4 *cells) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int b = __float_as_int(__ldg(&site[i]).w);
+        cells[b].z = __ldg(&rho_caller[__ldg(&perm[i])]);
+    }
 }
 
-cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, int64_t M, float *rho_internal,
-                                   cudaStream_t s) {
+cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,
+                                   float4 *cells, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     int64_t blocks = (M + 255) / 256;
     if (blocks > 65535) blocks = 65535;
-    permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, M, rho_internal);
+    permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, site, M, cells);
     return cudaGetLastError();
 }
 

@@ -33,21 +33,21 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 
 // ---------------------------------------------------------------------------
 // Device-side view of one grid. Plain data, passed by value to kernels or
-// stored in an array for batched launches.
+// stored in an array for batched launches. Cells are in the library's
+// internal (Morton) order.
 //
-// site[i]  float4 (x, y, z, bits of nbr offset) for internal cell i. The
-//          neighbour list of cell i starts at nbr[off]: nbr[off] = count c,
-//          nbr[off + 1 .. off + c] = neighbour ids (internal) or walls -1..-6,
-//          then padding (-8) up to a multiple of 4 ints, so every list starts
-//          on a 16-byte boundary and can be read as int4.
-// rho[i]   density of internal cell i.
+// cells    cell blocks, float4: cell i starts at block offset B_i with a
+//          header (bits of the caller's id, bits of the neighbour count c,
+//          rho, bits of i) followed by c records (x, y, z of the neighbour's
+//          site, bits of the neighbour's block offset B_j, or of a wall id
+//          -1..-6). Each cell has at least four records.
+// site[i]  float4 (x, y, z, bits of B_i): positions for C(r) and ray starts.
 // perm[i]  caller's id of internal cell i.
 // blk_*    block lists of Sect. 2.3 (internal ids).
 // ---------------------------------------------------------------------------
 struct GridDev {
     const float4 *site;
-    const int32_t *nbr;
-    const float *rho;
+    const float4 *cells;
     const int32_t *perm;
     const int32_t *blk_off;
     const int32_t *blk_idx;
@@ -92,7 +92,6 @@ struct StatsDev {
     unsigned long long rays, crossings, decisions, rechecks, fallbacks, zero_steps, step_limit, outside, bad_dir;
 };
 
-#define VG_PAD_ID (-8)
 
 // What the allocation-free entry point (noalloc.cu) needs from a grid.
 struct vgrid;

@@ -5,8 +5,13 @@
 // LPR lanes, one ray per group. A group takes a new ray from a global counter
 // as soon as its ray ends, so rays of very different length do not leave
 // lanes idle. Inside a crossing the group's lanes stride over the current
-// cell's neighbour list (read as int4 chunks) and reduce the exit with
-// shuffles.
+// cell's block and reduce the exit with shuffles.
+//
+// Cell blocks: cell i owns a contiguous run of float4 starting at B_i: a
+// header (caller's id, neighbour count, rho, internal id) and one record per
+// neighbour (x, y, z of the neighbour's site, and the neighbour's block
+// offset B_j, or a wall id -1..-6). A crossing therefore reads one contiguous
+// block; the winner's record already holds the next cell's site and block.
 //
 // Two arithmetic forms of the exit search (Sect. 2.2, steps 1-3, Eq. 1-5):
 //  * float64: Eq. 4 and Eq. 5 evaluated as written, in the same operation
@@ -40,13 +45,6 @@ constexpr float kCB = 8.0f * kU;
 constexpr float kDivLo = 0.99999952316284180f;      // 1 - 2^-21: covers 2 ulp of __fdividef
 constexpr float kDivHi = 1.00000047683715820f;      // 1 + 2^-21
 
-
-// Grid arrays the inner loop touches, kept in registers.
-struct Hot {
-    const float4 *__restrict__ site;
-    const int32_t *__restrict__ nbr;
-    const int32_t *__restrict__ perm;
-};
 
 // ---------------------------------------------------------------------------
 // float pairs (value = hi + lo)
@@ -98,25 +96,41 @@ __device__ __forceinline__ float local_coord(float R0h, float R0l, float Kh, flo
 }
 
 // ---------------------------------------------------------------------------
+// cell blocks
+// ---------------------------------------------------------------------------
+
+struct Hot {
+    const float4 *__restrict__ cells;  // cell blocks
+    const float4 *__restrict__ site;   // (x, y, z, bits of block offset) per internal cell
+};
+
+__device__ __forceinline__ int rec_w(float4 q) { return __float_as_int(q.w); }
+__device__ __forceinline__ int hdr_caller(float4 h) { return __float_as_int(h.x); }
+__device__ __forceinline__ int hdr_count(float4 h) { return __float_as_int(h.y); }
+
+// ---------------------------------------------------------------------------
 // float64 exit search (Eq. 4, Eq. 5), lexicographic (s, id) minimum; walls
 // keep their negative ids, cells compare by the caller's index on exact ties
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool better64(const Hot &h, double s, int j, double bs, int bj) {
-    if (bj == kNone) return true;
-    if (s < bs) return true;
-    if (s > bs) return false;
-    const int kj = j < 0 ? j : __ldg(&h.perm[j]);
-    const int kb = bj < 0 ? bj : __ldg(&h.perm[bj]);
-    return kj < kb;
+// tie-break key of a record: the wall id, or the caller's id of the cell
+__device__ __forceinline__ int key64(const Hot &h, int w) {
+    return w < 0 ? w : hdr_caller(__ldg(&h.cells[w]));
 }
 
-// One candidate: bisector of sites m and j (Eq. 1-4) or wall j < 0 (Eq. 5).
-// Returns false if it is not a candidate (n.k <= 0, or padding).
-__device__ __forceinline__ bool plane64(const Hot &h, const GridDev *gp, int j, double pmx, double pmy, double pmz,
+__device__ __forceinline__ bool better64(const Hot &h, double s, int w, double bs, int bw, bool have) {
+    if (!have) return true;
+    if (s < bs) return true;
+    if (s > bs) return false;
+    return key64(h, w) < key64(h, bw);
+}
+
+// One record: bisector of the current site and the record's site (Eq. 1-4),
+// or a wall (Eq. 5). Returns false if it is not a candidate (n.k <= 0).
+__device__ __forceinline__ bool plane64(const GridDev *gp, float4 q, double pmx, double pmy, double pmz,
                                         const double *r, const double *k, double &s) {
-    if (j >= 0) {
-        const float4 q = __ldg(&h.site[j]);
+    const int w = rec_w(q);
+    if (w >= 0) {
         const double px = (double)q.x, py = (double)q.y, pz = (double)q.z;
         const double nx = __dsub_rn(px, pmx), ny = __dsub_rn(py, pmy), nz = __dsub_rn(pz, pmz);
         const double den = __dadd_rn(__dadd_rn(__dmul_rn(nx, k[0]), __dmul_rn(ny, k[1])), __dmul_rn(nz, k[2]));
@@ -129,8 +143,8 @@ __device__ __forceinline__ bool plane64(const Hot &h, const GridDev *gp, int j, 
         s = __ddiv_rn(num, den);
         return true;
     }
-    if (j < -6) return false;
-    const int w = -j - 1, axis = w >> 1, hi = w & 1;
+    if (w < -6) return false;
+    const int wi = -w - 1, axis = wi >> 1, hi = wi & 1;
     const double kc = k[axis];
     if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
     const double bound = hi ? gp->hi[axis] : gp->lo[axis];
@@ -139,30 +153,36 @@ __device__ __forceinline__ bool plane64(const Hot &h, const GridDev *gp, int j, 
     return true;
 }
 
+// Exit of the cell whose records are blk[1..cnt] for the group: the
+// lexicographically smallest (s, id); returns the winner's record position
+// (1-based) or 0 if there is no candidate.
 template <int LPR>
-__device__ __forceinline__ void exit64(const Hot &h, const GridDev *gp, int off, double pmx, double pmy, double pmz,
-                                       const double *r, const double *k, unsigned gmask, int gl, double &bs,
-                                       int &bj) {
-    const int cnt = __ldg(&h.nbr[off]);
+__device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const float4 *blk, int cnt, double pmx,
+                                      double pmy, double pmz, const double *r, const double *k, unsigned gmask,
+                                      int gl, double &bs) {
     bs = 0.0;
-    bj = kNone;
+    int bp = 0, bw = 0;
     for (int p = 1 + gl; p <= cnt; p += LPR) {
-        const int j = __ldg(&h.nbr[off + p]);
+        const float4 q = __ldg(blk + p);
         double s;
-        if (plane64(h, gp, j, pmx, pmy, pmz, r, k, s) && better64(h, s, j, bs, bj)) {
+        if (plane64(gp, q, pmx, pmy, pmz, r, k, s) && better64(h, s, rec_w(q), bs, bw, bp != 0)) {
             bs = s;
-            bj = j;
+            bp = p;
+            bw = rec_w(q);
         }
     }
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) {
         const double os = __shfl_xor_sync(gmask, bs, o);
-        const int oj = __shfl_xor_sync(gmask, bj, o);
-        if (oj != kNone && better64(h, os, oj, bs, bj)) {
+        const int op = __shfl_xor_sync(gmask, bp, o);
+        const int ow = __shfl_xor_sync(gmask, bw, o);
+        if (op != 0 && better64(h, os, ow, bs, bw, bp != 0)) {
             bs = os;
-            bj = oj;
+            bp = op;
+            bw = ow;
         }
     }
+    return bp;
 }
 
 // ---------------------------------------------------------------------------
@@ -249,7 +269,7 @@ static __device__ __noinline__ int locate_point(const GridDev *gp, double x, dou
 
 struct Cand32 {
     float L1, L2;        // smallest and second smallest lower bound
-    int j1;              // id with the smallest lower bound (internal), kNone if none
+    int p1;              // record position (1-based) of the smallest, 0 if none
 };
 
 // Terms of the bisector of the current site (origin of the local frame) and
@@ -279,53 +299,42 @@ __device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float
 // Branch-free: in a warp some lane nearly always has a plane facing ahead,
 // so skipping the numerator for planes facing away (the sign shortcut of
 // Sect. 2.2) would only add divergence; a masked result costs nothing more.
-// Padding slots (j < 0) are masked the same way.
-__device__ __forceinline__ void consider32(int j, float4 q, float pmx, float pmy, float pmz, float rx, float ry,
-                                           float rz, float rr, float Kx, float Ky, float Kz, Cand32 &c) {
+// Walls (handled by the wall candidate t_max - t) and positions past the
+// count are masked the same way.
+__device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float pmx, float pmy, float pmz, float rx,
+                                           float ry, float rz, float rr, float Kx, float Ky, float Kz, Cand32 &c) {
     const Plane32 p = plane32(q, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz);
     const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
     float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
-    lower = (j >= 0 && p.den > -p.dden) ? lower : __int_as_float(0x7f800000);
+    lower = (valid && rec_w(q) >= 0 && p.den > -p.dden) ? lower : __int_as_float(0x7f800000);
     const bool b = lower < c.L1;
     c.L2 = b ? c.L1 : fminf(c.L2, lower);
-    c.j1 = b ? j : c.j1;
+    c.p1 = b ? pos : c.p1;
     c.L1 = fminf(c.L1, lower);
 }
 
+// Records blk[1..cnt]; lane gl of the group takes records gl+1, gl+1+LPR, ...
+// four at a time. Every cell has at least four faces, so the first four
+// records exist.
 template <int LPR>
-__device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float pmy, float pmz, float rx, float ry,
-                                       float rz, float rr, float Kx, float Ky, float Kz, unsigned gmask, int gl,
-                                       int gbase, Cand32 &c) {
-    const int4 *lst = reinterpret_cast<const int4 *>(h.nbr + off);
-    // every list owns >= 1 chunk and the array is padded past its end, so the
-    // first chunk of every lane and one chunk ahead can be read speculatively
-    int4 v = __ldg(lst + gl);
-    const int cnt = LPR == 1 ? v.x : __shfl_sync(gmask, v.x, gbase);
-    const int nch = (cnt + 4) >> 2;
-    int4 vn = __ldg(lst + gl + LPR);
+__device__ __forceinline__ void exit32(const float4 *blk, int cnt, float pmx, float pmy, float pmz, float rx,
+                                       float ry, float rz, float rr, float Kx, float Ky, float Kz, unsigned gmask,
+                                       int gl, int gbase, Cand32 &c) {
     c.L1 = __int_as_float(0x7f800000);
     c.L2 = c.L1;
-    c.j1 = kNone;
-    for (int ch = gl; ch < nch; ch += LPR) {
-        const int p = ch * 4;
-        const int j0 = (p >= 1 && p <= cnt) ? v.x : -8;
-        const int j1 = (p + 1 <= cnt) ? v.y : -8;
-        const int j2 = (p + 2 <= cnt) ? v.z : -8;
-        const int j3 = (p + 3 <= cnt) ? v.w : -8;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 q0 = j0 >= 0 ? __ldg(&h.site[j0]) : z4;
-        const float4 q1 = j1 >= 0 ? __ldg(&h.site[j1]) : z4;
-        const float4 q2 = j2 >= 0 ? __ldg(&h.site[j2]) : z4;
-        const float4 q3 = j3 >= 0 ? __ldg(&h.site[j3]) : z4;
-        // ids two chunks ahead travel while this chunk is tested
-        const int4 vnn = ch + 2 * LPR < nch ? __ldg(lst + ch + 2 * LPR) : vn;
-        consider32(j0, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(j1, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(j2, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(j3, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        v = vn;
-        vn = vnn;
+    c.p1 = 0;
+    for (int p = 1 + gl; p <= cnt; p += 4 * LPR) {
+        const int p0 = p, p1 = p + LPR, p2 = p + 2 * LPR, p3 = p + 3 * LPR;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, __int_as_float(-8));
+        const float4 q0 = __ldg(blk + p0);
+        const float4 q1 = p1 <= cnt ? __ldg(blk + p1) : z4;
+        const float4 q2 = p2 <= cnt ? __ldg(blk + p2) : z4;
+        const float4 q3 = p3 <= cnt ? __ldg(blk + p3) : z4;
+        consider32(p0, true, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(p1, p1 <= cnt, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(p2, p2 <= cnt, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(p3, p3 <= cnt, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
     }
     if (LPR > 1) {
         int win = gl;
@@ -341,7 +350,7 @@ __device__ __forceinline__ void exit32(const Hot &h, int off, float pmx, float p
             }
             c.L2 = nL2;
         }
-        c.j1 = __shfl_sync(gmask, c.j1, gbase + win);
+        c.p1 = __shfl_sync(gmask, c.p1, gbase + win);
     }
 }
 
@@ -381,8 +390,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     int set = 0;
     int64_t li = 0;         // index within the set
     const GridDev *gp = a.grids;  // device copy of the descriptor (cold paths)
-    Hot h{a.g1.site, a.g1.nbr, a.g1.perm};
-    const float *rho = a.g1.rho;
+    Hot h{a.g1.cells, a.g1.site};
     float kappa = a.g1.kappa;
     int max_steps = (int)min(a.g1.max_steps, (int64_t)0x7fffffff);
     // float64 form: current point and direction
@@ -391,9 +399,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     float R0h[3], R0l[3], Kh[3], Kl[3];
     float th = 0.f, tl = 0.f, tmh = 0.f, tml = 0.f, er = 0.f, ewall = 0.f;
     int wall = -1;
-    int m = -1, off = 0;
+    int B = 0;              // block offset of the current cell
     float pmx = 0.f, pmy = 0.f, pmz = 0.f;
-    float rho_m = 0.f;
     double tau64 = 0.0;
     float tau32 = 0.f, tauc = 0.f;
     float dLr = 0.f;
@@ -426,10 +433,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 rs = &a.sets[set];
                 li = ray - rs->first;
                 gp = a.grids + rs->grid;
+                h.cells = gp->cells;
                 h.site = gp->site;
-                h.nbr = gp->nbr;
-                h.perm = gp->perm;
-                rho = gp->rho;
                 kappa = gp->kappa;
                 max_steps = (int)min(gp->max_steps, (int64_t)0x7fffffff);
             }
@@ -444,6 +449,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             if (MODE == MODE_GRAD) dLr = __ldg(&a.dL_dtau[ray]);
             // the start record was prepared by the start-cell kernel
             const RayPrep *pr = rs->start + li;
+            int m;
             if (FP64) {
                 m = pr->cell;
                 if (m >= 0) {
@@ -475,8 +481,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 pmx = q.x;
                 pmy = q.y;
                 pmz = q.z;
-                off = __float_as_int(q.w);
-                rho_m = __ldg(&rho[m]);
+                B = rec_w(q);
             }
             if (status != RAY_OK) {
                 if (gl == 0) {
@@ -498,15 +503,17 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         if (ray < 0) continue;
 
         // ---------------- one exit decision ----------------
+        const float4 *blk = h.cells + B;
+        const float4 hdr = __ldg(blk);
+        const int cnt = hdr_count(hdr);
         bool ended = false;
         double s64 = 0.0;      // float64 length (float64 form or recheck)
         bool from64 = FP64;
         float len = 0.f;
-        int nxt = kNone;
-        bool have_q = false;
-        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+        int win = 0;           // winning record position, 0 none
+        bool to_wall = false;
         if (FP64) {
-            exit64<LPR>(h, gp, off, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64, nxt);
+            win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
         } else {
             const float rx = local_coord(R0h[0], R0l[0], Kh[0], Kl[0], th, tl, pmx);
             const float ry = local_coord(R0h[1], R0l[1], Kh[1], Kl[1], th, tl, pmy);
@@ -514,7 +521,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
             const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
             Cand32 c;
-            exit32<LPR>(h, off, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
+            exit32<LPR>(blk, cnt, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
             // the wall ahead is one more candidate: s_w = t_max - t
             float sw, swl;
             two_sum(tmh, -th, sw, swl);
@@ -535,9 +542,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 upper = __fadd_ru(sw, Ew);
             } else {
                 // the winner's terms again (same operations, same values)
-                qn = __ldg(&h.site[c.j1]);
-                have_q = true;
-                w1 = plane32(qn, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2]);
+                w1 = plane32(__ldg(blk + c.p1), pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2]);
                 const float den_lo = __fsub_rd(w1.den, w1.dden);
                 const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
                 upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : __int_as_float(0x7f800000);
@@ -545,14 +550,14 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             if (upper < c.L2) {
                 if (wall_wins) {
                     len = fmaxf(sw, 0.0f);
-                    nxt = wall;
+                    to_wall = true;
+                    win = -1;
                 } else {
                     // den > dden > 0 here; 2-ulp division (the length only feeds tau and t)
                     len = __fdividef(fmaxf(w1.num, 0.0f), w1.den);
-                    nxt = c.j1;
+                    win = c.p1;
                 }
             } else {
-                have_q = false;
                 // float64 recheck of this crossing from r = r0 + t k
                 if (gl == 0) VG_STAT(S_RE, 1);
                 const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
@@ -564,15 +569,20 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     kd[cc] = __ldg(d + cc);
                     rp[cc] = __fma_rn(t, kd[cc], __ldg(o + cc));
                 }
-                exit64<LPR>(h, gp, off, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask, gl, s64, nxt);
+                win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask, gl, s64);
                 len = __double2float_rn(s64);
                 from64 = true;
             }
         }
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (win > 0) {
+            qn = __ldg(blk + win);
+            to_wall = rec_w(qn) < 0;
+        }
 
         steps++;
         bool relocate = false;
-        if (nxt == kNone) {
+        if (win == 0) {
             relocate = true;  // no exit found (Sect. 2.2): nudge over epsilon and locate again
         } else {
             const bool positive = FP64 ? (s64 > 0.0) : (len > 0.0f);
@@ -580,18 +590,18 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 if (MODE == MODE_FILL && gl == 0) {
                     const int64_t at = seg_base + nseg;
                     if (at < a.seg_cap) {  // the count pass sized the buffer; never write past it
-                        a.seg_cell[at] = __ldg(&h.perm[m]);
+                        a.seg_cell[at] = hdr_caller(hdr);
                         if (FP64) ((double *)a.seg_len)[at] = s64;
                         else ((float *)a.seg_len)[at] = len;
                     }
                 }
-                if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[__ldg(&h.perm[m])], dLr * kappa * len);
+                if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[hdr_caller(hdr)], dLr * kappa * len);
                 nseg++;
                 if (FP64) {
-                    tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)rho_m), s64));
+                    tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)hdr.z), s64));
                 } else {
                     // Kahan-compensated sum of kappa rho l
-                    const float y = __fsub_rn(__fmul_rn(__fmul_rn(kappa, rho_m), len), tauc);
+                    const float y = __fsub_rn(__fmul_rn(__fmul_rn(kappa, hdr.z), len), tauc);
                     const float tt = __fadd_rn(tau32, y);
                     tauc = __fsub_rn(__fsub_rn(tt, tau32), y);
                     tau32 = tt;
@@ -609,16 +619,13 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             } else {
                 ff_add(th, tl, len);
             }
-            if (nxt < 0) {
+            if (to_wall) {
                 ended = true;
             } else {
-                m = nxt;
-                if (!have_q) qn = __ldg(&h.site[m]);
                 pmx = qn.x;
                 pmy = qn.y;
                 pmz = qn.z;
-                off = __float_as_int(qn.w);
-                rho_m = __ldg(&rho[m]);
+                B = rec_w(qn);
                 relocate = zrun > kZeroRunMax;
             }
         }
@@ -639,13 +646,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             if (nm < 0) {
                 ended = true;
             } else {
-                m = nm;
-                const float4 q = __ldg(&h.site[m]);
+                const float4 q = __ldg(&h.site[nm]);
                 pmx = q.x;
                 pmy = q.y;
                 pmz = q.z;
-                off = __float_as_int(q.w);
-                rho_m = __ldg(&rho[m]);
+                B = rec_w(q);
             }
         }
         if (!ended && steps >= max_steps) {

@@ -20,6 +20,9 @@ pytestmark = pytest.mark.gpu
 
 TAU32_REL = 1e-5
 LEN64_REL = 1e-12
+# float32 adjoint: per cell within this fraction of the sum of |contributions|
+# (float32 products plus atomic summation in arbitrary order)
+GRAD32_REL = 1e-5
 
 
 def dev(a):
@@ -233,11 +236,12 @@ def test_gradient_matches_oracle():
     want = oracle.tau_grad(ref, len(g.sites), dL, kappa=float(g.kappa))
     vg = make(g)
     O, D = dev(rays.origin), dev(rays.dir)
+    wabs = oracle.tau_grad(ref, len(g.sites), np.abs(dL), kappa=float(g.kappa))
     got = vg.trace_grad(O, D, dev(dL.astype(np.float32))).cpu().numpy().astype(np.float64)
-    big = np.abs(want) > 1e-6 * np.abs(want).max()
-    rel = np.abs(got[big] - want[big]) / np.abs(want[big])
-    assert rel.max() <= 1e-4, rel.max()
-    assert np.all(got[want == 0] == 0)
+    ok = np.all(ref.near_tie == 0)
+    assert ok or ref.near_tie.sum() < 5
+    assert np.all(np.abs(got - want) <= GRAD32_REL * wabs + 1e-30)
+    assert np.all(got[wabs == 0] == 0)
     # autograd wrapper gives the same gradient
     from paper_1310_1854_gb300 import optical_depth
     rho = dev(g.rho).requires_grad_(True)
@@ -246,8 +250,9 @@ def test_gradient_matches_oracle():
     loss = ((torch.exp(-tau) - t) ** 2).sum()
     loss.backward()
     gg = rho.grad.cpu().numpy().astype(np.float64)
-    rel = np.abs(gg[big] - want[big]) / np.abs(want[big])
-    assert rel.max() <= 2e-3, rel.max()
+    # torch evaluates the loss in float32 from float32 tau; dL/dtau carries
+    # that rounding (about 1e-7 relative to exp(-tau))
+    assert np.all(np.abs(gg - want) <= 1e-3 * wabs + 1e-30)
 
 
 def test_batched_matches_single():
@@ -297,9 +302,12 @@ def test_full_size_config5_gradient_sampled():
     target = torch.exp(-vg.trace(O, D, precision="fp32").tau)
     vg.set_density(dev(g.rho), 1.0)
     dL = (-2.0 * (torch.exp(-tau) - target) * torch.exp(-tau)).float()
-    full = vg.trace_grad(O, D, dL)
-    half = vg.trace_grad(O, D, 0.5 * dL)
-    np.testing.assert_allclose(half.cpu().numpy(), 0.5 * full.cpu().numpy(), rtol=1e-5, atol=1e-12)
+    full = vg.trace_grad(O, D, dL).cpu().numpy().astype(np.float64)
+    half = vg.trace_grad(O, D, 0.5 * dL).cpu().numpy().astype(np.float64)
+    # float32 atomics add in no fixed order: the bound is relative to the sum
+    # of the absolute contributions of each cell
+    absum = vg.trace_grad(O, D, dL.abs()).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(half - 0.5 * full) <= GRAD32_REL * absum + 1e-30)
     sample = np.sort(gen.rng_for(111).choice(len(rays.origin), 64, replace=False))
     ref = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sample], rays.dir[sample])
     keep = ref.near_tie == 0
@@ -307,14 +315,33 @@ def test_full_size_config5_gradient_sampled():
     dls = dL.cpu().numpy().astype(np.float64)[sel]
     sub = oracle.Trace(*(getattr(ref, f)[keep] for f in ("nseg", "seg_cell", "seg_len", "tau", "length",
                                                          "min_margin", "near_tie", "nfallback", "status")))
-    want = oracle.tau_grad(sub, len(g.sites), dls)
-    got = vg.trace_grad(dev(rays.origin[sel]), dev(rays.dir[sel]), dev(dls.astype(np.float32)))
-    got = got.cpu().numpy().astype(np.float64)
-    big = np.abs(want) > 1e-6 * np.abs(want).max()
-    assert big.sum() > 1000
-    rel = np.abs(got[big] - want[big]) / np.abs(want[big])
-    assert rel.max() <= 1e-4, rel.max()
-    assert np.all(got[want == 0] == 0)
+    M = len(g.sites)
+    want = oracle.tau_grad(sub, M, dls)
+    wabs = oracle.tau_grad(sub, M, np.abs(dls))
+    Os, Ds = dev(rays.origin[sel]), dev(rays.dir[sel])
+    got = vg.trace_grad(Os, Ds, dev(dls.astype(np.float32))).cpu().numpy().astype(np.float64)
+    assert np.count_nonzero(want) > 1000
+    # float32 exit points are accurate to a few ulp of the local scale, so a
+    # segment's length carries an absolute error (bounded here by 2e-6 of the
+    # ray's in-domain length), which the per-cell bound must include
+    slack = np.zeros(M)
+    for k in range(len(sel)):
+        c, _ = sub.segments(k)
+        np.add.at(slack, c, np.abs(dls[k]) * 2e-6 * sub.length[k])
+    assert np.all(np.abs(got - want) <= GRAD32_REL * wabs + slack + 1e-30)
+    assert np.all(got[wabs == 0] == 0)
+    # the adjoint against the GPU's own float32 segments of the same rays
+    seg = vg.trace(Os, Ds, precision="fp32", segments=True)
+    so = seg.seg_off.cpu().numpy()
+    cells = seg.seg_cell.cpu().numpy()
+    lens = seg.seg_len.cpu().numpy().astype(np.float64)
+    per_ray = np.repeat(np.arange(len(sel)), np.diff(so))
+    mine = np.bincount(cells, weights=dls[per_ray] * lens, minlength=M)
+    mabs = np.bincount(cells, weights=np.abs(dls[per_ray]) * lens, minlength=M)
+    assert np.all(np.abs(got - mine) <= GRAD32_REL * mabs + 1e-30)
+    for k in range(len(sel)):
+        assert np.array_equal(cells[so[k]:so[k + 1]], sub.segments(k)[0])
+        assert np.all(np.abs(lens[so[k]:so[k + 1]] - sub.segments(k)[1]) <= 2e-6 * sub.length[k])
     # tau of the sampled rays against the oracle
     t = tau.cpu().numpy().astype(np.float64)[sel]
     assert np.all(np.abs(t - ref.tau[keep]) <= TAU32_REL * ref.tau[keep])
