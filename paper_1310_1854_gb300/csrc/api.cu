@@ -86,7 +86,7 @@ struct vgrid {
     float4 *d_cells = nullptr;
     int32_t *d_perm = nullptr;
     int32_t *d_blk_off = nullptr;
-    int32_t *d_blk_idx = nullptr;
+    float4 *d_blk_rec = nullptr;
     std::vector<int32_t> perm, inv;  // internal -> caller, caller -> internal
     vg::CellsOut cells;              // internal order
     vg::BlocksOut blocks;
@@ -132,7 +132,7 @@ void vgrid_default_opts(vgrid_opts *o) {
     o->threads = 0;
     o->round_sites = 0;
     o->reorder = 1;
-    o->blocks_per_site = 0.5;
+    o->blocks_per_site = 2.0;
     o->max_steps = 100000;
     o->host_only = 0;
 }
@@ -151,7 +151,7 @@ static void free_events(vgrid_t *g) {
 static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
-    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_perm, g->d_blk_off, g->d_blk_idx,
+    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_perm, g->d_blk_off, g->d_blk_rec,
                     g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -171,7 +171,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     vgrid_opts o;
     vgrid_default_opts(&o);
     if (opts) o = *opts;
-    if (!(o.blocks_per_site > 0)) o.blocks_per_site = 0.5;
+    if (!(o.blocks_per_site > 0)) o.blocks_per_site = 2.0;
     if (o.max_steps <= 0) o.max_steps = 100000;
     const auto t0 = std::chrono::steady_clock::now();
 
@@ -294,7 +294,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     VG_ALLOC(g->d_cells, nrec);
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
-    VG_ALLOC(g->d_blk_idx, g->blocks.idx.size());
+    VG_ALLOC(g->d_blk_rec, g->blocks.idx.size());
     VG_ALLOC(g->d_desc, 1);
     VG_ALLOC(g->d_queue, 1);
     VG_ALLOC(g->d_stats, 1);
@@ -305,15 +305,24 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, blocks.data(), sizeof(float) * 4 * nrec, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !g->blocks.idx.empty())
-        e = cudaMemcpy(g->d_blk_idx, g->blocks.idx.data(), sizeof(int32_t) * g->blocks.idx.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !g->blocks.idx.empty()) {
+        std::vector<float> brec(4 * g->blocks.idx.size());
+        for (size_t q = 0; q < g->blocks.idx.size(); q++) {
+            const int32_t c = g->blocks.idx[q];
+            brec[4 * q + 0] = (float)Si[3 * (int64_t)c + 0];
+            brec[4 * q + 1] = (float)Si[3 * (int64_t)c + 1];
+            brec[4 * q + 2] = (float)Si[3 * (int64_t)c + 2];
+            put_int(&brec[4 * q + 3], c);
+        }
+        e = cudaMemcpy(g->d_blk_rec, brec.data(), sizeof(float) * brec.size(), cudaMemcpyHostToDevice);
+    }
 
     GridDev &hd = g->hd;
     hd.site = g->d_site;
     hd.cells = g->d_cells;
     hd.perm = g->d_perm;
     hd.blk_off = g->d_blk_off;
-    hd.blk_idx = g->d_blk_idx;
+    hd.blk_rec = g->d_blk_rec;
     double dmax = 0;
     for (int c = 0; c < 3; c++) {
         hd.lo[c] = bbox[c];

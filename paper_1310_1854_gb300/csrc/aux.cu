@@ -58,27 +58,44 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
             out->cell = m;
             continue;
         }
-        // distance to the wall ahead (Eq. 5 for the walls the ray faces)
-        double tmax = 1e300;
-        int wid = -1;
-        for (int c = 0; c < 3; c++) {
-            if (k[c] > 0.0) {
-                const double t = __ddiv_rn(__dsub_rn(gp->hi[c], r0[c]), k[c]);
-                if (t < tmax) { tmax = t; wid = -(2 * c + 2); }
-            } else if (k[c] < 0.0) {
-                const double t = __ddiv_rn(__dsub_rn(gp->lo[c], r0[c]), k[c]);
-                if (t < tmax) { tmax = t; wid = -(2 * c + 1); }
-            }
-        }
-        if (!(tmax >= 0.0) || tmax > 1e299) tmax = 0.0;
         RayPrep p;
         p.cell = m;
-        p.wall = wid;
-        split_double(tmax, p.tmax_hi, p.tmax_lo);
         for (int c = 0; c < 3; c++) {
             split_double(r0[c], p.r0_hi[c], p.r0_lo[c]);
             split_double(k[c], p.k_hi[c], p.k_lo[c]);
         }
+        // distance to the wall ahead (Eq. 5 for the walls the ray faces), as
+        // a float pair: q1 = n/k rounded, the exact remainder n - q1 k by
+        // fma, then q2 = remainder / k (relative error a few 2^-48)
+        float th = 3.0e38f, tl = 0.0f;
+        int wid = -1;
+        for (int c = 0; c < 3; c++) {
+            if (k[c] == 0.0) continue;
+            const bool up = k[c] > 0.0;
+            float nh, nl;
+            split_double(__dsub_rn(up ? gp->hi[c] : gp->lo[c], r0[c]), nh, nl);
+            const float kh = p.k_hi[c], kl = p.k_lo[c];
+            const float q1 = __fdiv_rn(nh, kh);
+            float rem = __fmaf_rn(-q1, kh, nh);
+            rem = __fadd_rn(rem, __fmaf_rn(-q1, kl, nl));
+            const float q2 = __fdiv_rn(rem, kh);
+            float h, l;
+            two_sum(q1, q2, h, l);
+            if (h < th || (h == th && l < tl)) {
+                th = h;
+                tl = l;
+                wid = up ? -(2 * c + 2) : -(2 * c + 1);
+            }
+        }
+        if (!(th >= 0.0f) || th > 1.0e38f) {  // start on the boundary facing out (or k = 0)
+            th = 0.0f;
+            tl = 0.0f;
+        } else if (th == 0.0f && tl < 0.0f) {
+            tl = 0.0f;
+        }
+        p.wall = wid;
+        p.tmax_hi = th;
+        p.tmax_lo = tl;
         const float4 *src = reinterpret_cast<const float4 *>(&p);
         float4 *dst = reinterpret_cast<float4 *>(out);
         for (int q = 0; q < 4; q++) dst[q] = src[q];

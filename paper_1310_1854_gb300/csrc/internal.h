@@ -43,14 +43,16 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 //          -1..-6). Each cell has at least four records.
 // site[i]  float4 (x, y, z, bits of B_i): positions for C(r) and ray starts.
 // perm[i]  caller's id of internal cell i.
-// blk_*    block lists of Sect. 2.3 (internal ids).
+// blk_off, blk_rec  block lists of Sect. 2.3: for every block, records
+//          (x, y, z of a site, bits of its internal id) of the cells whose
+//          bounding box overlaps the block.
 // ---------------------------------------------------------------------------
 struct GridDev {
     const float4 *site;
     const float4 *cells;
     const int32_t *perm;
     const int32_t *blk_off;
-    const int32_t *blk_idx;
+    const float4 *blk_rec;
     double lo[3], hi[3];      // domain box
     double bscale[3];         // blocks per unit length along each axis
     int32_t bdim[3];

@@ -206,13 +206,13 @@ __device__ __forceinline__ int block_of(const GridDev *gp, double x, double y, d
 
 // float64 scan of a block list, distances as ((dx dx + dy dy) + dz dz)
 static __device__ __noinline__ int locate64(const GridDev *gp, double x, double y, double z, int beg, int end) {
-    const float4 *site = gp->site;
+    const float4 *rec = gp->blk_rec;
     const int32_t *perm = gp->perm;
     int best = -1;
     double bd = 0.0;
     for (int i = beg; i < end; i++) {
-        const int c = __ldg(&gp->blk_idx[i]);
-        const float4 q = __ldg(&site[c]);
+        const float4 q = __ldg(&rec[i]);
+        const int c = __float_as_int(q.w);
         const double dx = __dsub_rn(x, (double)q.x), dy = __dsub_rn(y, (double)q.y), dz = __dsub_rn(z, (double)q.z);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         if (best < 0 || d2 < bd || (d2 == bd && __ldg(&perm[c]) < __ldg(&perm[best]))) {
@@ -229,29 +229,24 @@ static __device__ __noinline__ int locate64(const GridDev *gp, double x, double 
 // which bounds the rounding error of a float32 squared distance; otherwise
 // the list is rescanned in float64. *rechecked is set when that happened.
 static __device__ __noinline__ int locate_point(const GridDev *gp, double x, double y, double z, bool fp32,
-                                         int *rechecked) {
+                                                int *rechecked) {
     if (!inside(gp, x, y, z)) return -1;
     const int b = block_of(gp, x, y, z);
     const int beg = __ldg(&gp->blk_off[b]), end = __ldg(&gp->blk_off[b + 1]);
     if (fp32) {
-        const float4 *site = gp->site;
-        const int32_t *blk = gp->blk_idx;
+        const float4 *rec = gp->blk_rec;
         const float xf = __double2float_rn(x), yf = __double2float_rn(y), zf = __double2float_rn(z);
         const float X = fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
         float D1 = __int_as_float(0x7f800000), D2 = D1;
         int i1 = -1;
         for (int i = beg; i < end; i++) {
-            const int c = __ldg(&blk[i]);
-            const float4 q = __ldg(&site[c]);
+            const float4 q = __ldg(&rec[i]);
             const float dx = __fsub_rn(xf, q.x), dy = __fsub_rn(yf, q.y), dz = __fsub_rn(zf, q.z);
             const float D = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            if (D < D1) {
-                D2 = D1;
-                D1 = D;
-                i1 = c;
-            } else if (D < D2) {
-                D2 = D;
-            }
+            const bool better = D < D1;
+            D2 = better ? D1 : fminf(D2, D);
+            i1 = better ? __float_as_int(q.w) : i1;
+            D1 = fminf(D1, D);
         }
         if (end - beg <= 1) return i1;
         const float s1 = sqrtf(D1), s2 = sqrtf(D2);
