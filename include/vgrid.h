@@ -62,8 +62,15 @@ enum {
 
 /* what vgrid_trace writes */
 enum {
-    VGRID_TAU = 0,     /* tau per ray */
-    VGRID_SEGMENTS = 1 /* tau per ray and the segment list of every ray */
+    VGRID_TAU = 0,      /* tau per ray */
+    VGRID_SEGMENTS = 1, /* tau per ray and the segment list of every ray */
+    VGRID_ENTER = 0x100 /* flag, OR it in: a ray starting outside the domain
+                           first moves to where it enters the box (the
+                           nearest boundary point along +k, slab test) and is
+                           traced from there; rays that miss the box stay
+                           VGRID_RAY_OUTSIDE (Sect. 2.2 notes the method is
+                           easily adjusted for rays that originate outside the
+                           domain) */
 };
 
 /* per-ray status codes written to ray_status */
@@ -112,9 +119,10 @@ typedef struct {
 
 /* launch shape of the traversal kernels */
 typedef struct {
-    int32_t lanes_per_ray; /* 1, 2, 4 or 8 lanes cooperate on one ray */
-    int32_t block;         /* threads per block (multiple of 32, 32..256) */
-    int32_t blocks_per_sm; /* persistent blocks per SM; 0 = as many as fit */
+    int32_t lanes_per_ray;      /* 1, 2, 4 or 8 lanes cooperate on one ray (default 1) */
+    int32_t block;              /* threads per block (multiple of 32, 32..256; default 128) */
+    int32_t blocks_per_sm;      /* persistent blocks per SM; 0 = as many as fit */
+    int32_t fp64_lanes_per_ray; /* lanes per ray of the float64 form; 0 = lanes_per_ray (default 4) */
 } vgrid_launch;
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -177,7 +185,9 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  *                 within 1e-6 (checked on the device: such a ray gets tau 0,
  *                 no segments and status VGRID_RAY_BAD_DIR).
  *   precision     VGRID_FP64 or VGRID_FP32_RECHECK.
- *   output        VGRID_TAU or VGRID_SEGMENTS.
+ *   output        VGRID_TAU or VGRID_SEGMENTS, optionally | VGRID_ENTER
+ *                 (segments, tau and lengths then start at the entry point;
+ *                 needs a work buffer of N*3 doubles, grown like the others).
  *   tau           device float64[N] (FP64) or float32[N] (FP32_RECHECK);
  *                 nullable in segment mode.
  *   seg_off       device int64[N+1] (segment mode): exclusive prefix sum of
@@ -212,6 +222,29 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
  */
 int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *dL_dtau,
                      float *dL_drho, vgrid_stream_t stream);
+
+/*
+ * Interaction sampling along the path: the Monte Carlo step that consumes
+ * the traversal in the paper's radiative-transfer code (Sect. 3.1, 3.4:
+ * photon packages are shot through the grid and their absorption is booked
+ * in the cells they cross). Ray r carries an optical depth tau_int[r]
+ * (typically -ln of a uniform deviate, drawn by the caller) and a weight
+ * w[r]; it is traced (float32 form, as vgrid_trace) until the running
+ * tau = sum kappa rho l reaches tau_int[r] inside some cell.
+ *   tau_int   device float32[N]
+ *   weight    device float32[N] or NULL (all 1)
+ *   cell      device int32[N]: the cell where the ray interacts (caller id),
+ *             -1 if it leaves the domain first (or starts outside / is cut)
+ *   s         device float32[N]: distance from the origin to the interaction
+ *             point, or the in-domain path length if it leaves first
+ *   absorbed  device float32[M] or NULL, accumulated into: for every cell
+ *             crossed before the interaction, w (exp(-tau_in) - exp(-tau_out))
+ *             where tau_in, tau_out are the running tau entering and leaving
+ *             the cell (capped at tau_int), i.e. the part of the package the
+ *             cell removes.
+ */
+int vgrid_interact(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *tau_int,
+                   const float *weight, int32_t *cell, float *s, float *absorbed, vgrid_stream_t stream);
 
 /* Launch shape used by this grid's traversal kernels (NULL resets to the
  * built-in default). */

@@ -129,14 +129,15 @@ class VoronoiGrid:
         return vol, bb
 
     # -------------------------------------------------------------- launch
-    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0):
-        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm))
+    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, fp64_lanes_per_ray=4):
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), int(fp64_lanes_per_ray))
         check(load().vgrid_set_launch(self._h, ctypes.byref(l)))
 
     def get_launch(self):
         l = _lib.Launch()
         check(load().vgrid_get_launch(self._h, ctypes.byref(l)))
-        return {"lanes_per_ray": l.lanes_per_ray, "block": l.block, "blocks_per_sm": l.blocks_per_sm}
+        return {"lanes_per_ray": l.lanes_per_ray, "block": l.block, "blocks_per_sm": l.blocks_per_sm,
+                "fp64_lanes_per_ray": l.fp64_lanes_per_ray}
 
     def enable_timing(self, enable=True):
         check(load().vgrid_enable_timing(self._h, int(bool(enable))))
@@ -163,36 +164,56 @@ class VoronoiGrid:
         return out
 
     def trace(self, origin, direction, precision="fp32", segments=False, status=False, stats=False,
-              seg_capacity=None, stream=None, out_tau=None) -> TraceResult:
+              seg_capacity=None, stream=None, out_tau=None, enter=False) -> TraceResult:
         lib = load()
         O = _rays(origin, "origin", self.device)
         D = _rays(direction, "direction", self.device)
         N = O.shape[0]
         prec = _PREC[precision]
+        flag = _lib.ENTER if enter else 0
         tdt = torch.float64 if prec == _lib.FP64 else torch.float32
         tau = out_tau if out_tau is not None else torch.empty(N, dtype=tdt, device=self.device)
         st = torch.empty(N, dtype=torch.int32, device=self.device) if status else None
         cs = _lib.Stats() if (stats or segments) else None
         sref = ctypes.byref(cs) if cs is not None else None
         if not segments:
-            check(lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.TAU, _ptr(tau), None, None, None, 0,
+            check(lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.TAU | flag, _ptr(tau), None, None, None, 0,
                                   _ptr(st), sref, _stream(stream)))
             return TraceResult(tau, status=st, stats=cs.as_dict() if cs is not None else None)
         seg_off = torch.empty(N + 1, dtype=torch.int64, device=self.device)
         cap = int(seg_capacity) if seg_capacity is not None else 0
         cells = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
         lens = torch.empty(max(cap, 1), dtype=tdt, device=self.device)
-        rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS, _ptr(tau), _ptr(seg_off),
+        rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS | flag, _ptr(tau), _ptr(seg_off),
                              _ptr(cells), _ptr(lens), cap, _ptr(st), sref, _stream(stream))
         if rc == _lib.ERR_CAPACITY and seg_capacity is None:
             total = int(seg_off[N].item())
             cells = torch.empty(max(total, 1), dtype=torch.int32, device=self.device)
             lens = torch.empty(max(total, 1), dtype=tdt, device=self.device)
-            rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS, _ptr(tau), _ptr(seg_off),
+            rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS | flag, _ptr(tau), _ptr(seg_off),
                                  _ptr(cells), _ptr(lens), total, _ptr(st), sref, _stream(stream))
         check(rc)
         total = int(seg_off[N].item())
         return TraceResult(tau, seg_off, cells[:total], lens[:total], st, cs.as_dict())
+
+    def interact(self, origin, direction, tau_int: torch.Tensor, weight: torch.Tensor | None = None,
+                 absorbed: bool | torch.Tensor = False, stream=None):
+        """Where each ray's running tau reaches tau_int: (cell int32, s float32,
+        absorbed float32[M] or None); cell -1 means the ray left the domain."""
+        O = _rays(origin, "origin", self.device)
+        D = _rays(direction, "direction", self.device)
+        N = O.shape[0]
+        ti = tau_int.detach().to(torch.float32).contiguous()
+        w = weight.detach().to(torch.float32).contiguous() if weight is not None else None
+        cell = torch.empty(N, dtype=torch.int32, device=self.device)
+        s = torch.empty(N, dtype=torch.float32, device=self.device)
+        if isinstance(absorbed, torch.Tensor):
+            ab = absorbed
+        else:
+            ab = torch.zeros(self.M, dtype=torch.float32, device=self.device) if absorbed else None
+        check(load().vgrid_interact(self._h, _ptr(O), _ptr(D), N, _ptr(ti), _ptr(w), _ptr(cell), _ptr(s), _ptr(ab),
+                                    _stream(stream)))
+        return cell, s, ab
 
     def trace_grad(self, origin, direction, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         """dL/drho (float32[M]) for dL/dtau per ray; accumulates into ``out``."""
@@ -229,7 +250,7 @@ class Batch:
             arr[i] = _lib.Rayset(grid._h.value, O.data_ptr() if O.numel() else None,
                                  D.data_ptr() if D.numel() else None, O.shape[0],
                                  t.data_ptr() if t.numel() else None, s.data_ptr() if s.numel() else None)
-        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm))
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), 0)
         h = ctypes.c_void_p()
         check(load().vgrid_batch_create(arr, len(sets), ctypes.byref(l), ctypes.byref(h)))
         self._h = h

@@ -33,6 +33,7 @@ FP64 = 0
 FP32_RECHECK = 1
 TAU = 0
 SEGMENTS = 1
+ENTER = 0x100
 
 RAY_OK, RAY_OUTSIDE, RAY_STEP_LIMIT, RAY_BAD_DIR = 0, 1, 2, 3
 
@@ -56,7 +57,8 @@ class Info(ctypes.Structure):
 
 
 class Launch(ctypes.Structure):
-    _fields_ = [("lanes_per_ray", c_int32), ("block", c_int32), ("blocks_per_sm", c_int32)]
+    _fields_ = [("lanes_per_ray", c_int32), ("block", c_int32), ("blocks_per_sm", c_int32),
+                ("fp64_lanes_per_ray", c_int32)]
 
 
 class Rayset(ctypes.Structure):
@@ -96,6 +98,8 @@ SIGNATURES = [
     ("vgrid_enable_timing", c_int32, [c_void_p, c_int32]),
     ("vgrid_read_timing", c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                     ctypes.POINTER(c_int64)]),
+    ("vgrid_interact", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 c_void_p, c_void_p]),
     ("vgrid_trace_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p]),
 ]
 

@@ -79,7 +79,7 @@ struct vgrid {
     int sms = 1;
     int64_t M = 0;
     vgrid_opts opts{};
-    vgrid_launch launch{1, 128, 0};
+    vgrid_launch launch{1, 128, 0, 4};
     GridDev hd{};
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
@@ -98,6 +98,8 @@ struct vgrid {
     int64_t start_cap = 0;
     int64_t *d_scan = nullptr;
     int64_t scan_cap = 0;
+    double *d_entry = nullptr;   // entry points of VGRID_ENTER calls
+    int64_t entry_cap = 0;
     double build_seconds = 0;
     int64_t device_bytes = 0;
     // optional event record: {locate start, locate end} or {trace start, trace end}
@@ -111,7 +113,7 @@ struct vgrid_batch {
     int sms = 1;
     int32_t G = 0;
     int64_t total = 0;
-    vgrid_launch launch{1, 128, 0};
+    vgrid_launch launch{1, 128, 0, 4};
     GridDev *d_grids = nullptr;
     RaySetDev *d_sets = nullptr;
     RayPrep *d_start = nullptr;
@@ -152,7 +154,7 @@ static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
     void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_perm, g->d_blk_off, g->d_blk_rec,
-                    g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan};
+                    g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan, g->d_entry};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -424,10 +426,12 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
 int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (!l) {
-        g->launch = vgrid_launch{1, 128, 0};
+        g->launch = vgrid_launch{1, 128, 0, 4};
         return VGRID_OK;
     }
     if (!valid_lpr(l->lanes_per_ray)) return fail(VGRID_ERR_ARG, "lanes_per_ray must be 1, 2, 4 or 8");
+    if (l->fp64_lanes_per_ray != 0 && !valid_lpr(l->fp64_lanes_per_ray))
+        return fail(VGRID_ERR_ARG, "fp64_lanes_per_ray must be 0, 1, 2, 4 or 8");
     if (l->block < 32 || l->block > 256 || l->block % 32) return fail(VGRID_ERR_ARG, "block must be 32..256, multiple of 32");
     if (l->blocks_per_sm < 0) return fail(VGRID_ERR_ARG, "blocks_per_sm must be >= 0");
     g->launch = *l;
@@ -474,6 +478,20 @@ int ensure_start(vgrid_t *g, int64_t N) {
     int rc = dmalloc(&g->d_start, (size_t)N, g->device_bytes);
     if (rc) return rc;
     g->start_cap = N;
+    return VGRID_OK;
+}
+
+int ensure_entry(vgrid_t *g, int64_t N) {
+    if (N <= g->entry_cap) return VGRID_OK;
+    if (g->d_entry) {
+        cudaFree(g->d_entry);
+        g->device_bytes -= g->entry_cap * 3 * (int64_t)sizeof(double);
+        g->d_entry = nullptr;
+        g->entry_cap = 0;
+    }
+    int rc = dmalloc(&g->d_entry, (size_t)(3 * N), g->device_bytes);
+    if (rc) return rc;
+    g->entry_cap = N;
     return VGRID_OK;
 }
 
@@ -558,6 +576,8 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
     if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    const bool enter = (output & VGRID_ENTER) != 0;
+    output &= ~VGRID_ENTER;
     if (output != VGRID_TAU && output != VGRID_SEGMENTS) return fail(VGRID_ERR_ARG, "bad output");
     if (N < 0 || (N > 0 && (!origin || !dir))) return fail(VGRID_ERR_ARG, "bad rays");
     if (output == VGRID_TAU && N > 0 && !tau) return fail(VGRID_ERR_ARG, "tau is NULL");
@@ -572,8 +592,15 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     }
     int rc = ensure_start(g, N);
     if (rc) return rc;
+    if (enter) {
+        if ((rc = ensure_entry(g, N))) return rc;
+        VG_CUDA(vg::launch_enter(origin, dir, N, g->d_desc, g->d_entry, g->sms, s));
+        origin = g->d_entry;
+    }
     const int fp64 = precision == VGRID_FP64;
-    const vg::KernelSet &ks = kernels(g->launch.lanes_per_ray);
+    vgrid_launch L = g->launch;
+    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+    const vg::KernelSet &ks = kernels(L.lanes_per_ray);
     RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
@@ -590,7 +617,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     a.s1 = set;
     if (output == VGRID_TAU) {
         mark(g, 1, 0, s);
-        if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], g->launch, g->sms, N, a, s))) return rc;
+        if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], L, g->sms, N, a, s))) return rc;
         mark(g, 1, 1, s);
         if (stats) return read_stats(g->d_stats, stats, s);
         return VGRID_OK;
@@ -599,7 +626,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     if ((rc = ensure_scan(g, N))) return rc;
     a.seg_off = seg_off;
     mark(g, 1, 0, s);
-    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_COUNT], g->launch, g->sms, N, a, s))) return rc;
+    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_COUNT], L, g->sms, N, a, s))) return rc;
     mark(g, 1, 1, s);
     VG_CUDA(vg::launch_exclusive_scan(seg_off, N, g->d_scan, s));
     int64_t total = 0;
@@ -613,7 +640,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     a.seg_len = seg_len;
     a.seg_cap = total;
     mark(g, 1, 0, s);
-    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_FILL], g->launch, g->sms, N, a, s))) return rc;
+    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_FILL], L, g->sms, N, a, s))) return rc;
     mark(g, 1, 1, s);
     return read_stats(g->d_stats, stats, s);
 }
@@ -679,6 +706,41 @@ int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *
     if (launches) *launches = (int64_t)g->n_trace;
     g->n_loc = g->n_trace = 0;
     return VGRID_OK;
+}
+
+int vgrid_interact(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *tau_int,
+                   const float *weight, int32_t *cell, float *s_out, float *absorbed, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (N < 0 || (N > 0 && (!origin || !dir || !tau_int || !cell || !s_out))) return fail(VGRID_ERR_ARG, "bad arguments");
+    if (N == 0) return VGRID_OK;
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_start(g, N);
+    if (rc) return rc;
+    RaySetDev set{origin, dir, nullptr, nullptr, g->d_start, N, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
+    mark(g, 0, 0, s);
+    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
+    mark(g, 0, 1, s);
+    vg::TraceArgs a{};
+    a.grids = g->d_desc;
+    a.sets = g->d_set;
+    a.nsets = 1;
+    a.total = N;
+    a.queue = g->d_queue;
+    a.stats = g->d_stats;
+    a.tau_int = tau_int;
+    a.weight = weight;
+    a.int_cell = cell;
+    a.int_s = s_out;
+    a.absorbed = absorbed;
+    a.g1 = g->hd;
+    a.s1 = set;
+    mark(g, 1, 0, s);
+    rc = launch_trace(kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_INTERACT], g->launch, g->sms, N, a, s);
+    mark(g, 1, 1, s);
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -809,6 +871,7 @@ int grid_view(const struct vgrid *g, GridView *out) {
     out->d_desc = g->d_desc;
     out->hd = g->hd;
     out->lanes_per_ray = g->launch.lanes_per_ray;
+    out->fp64_lanes_per_ray = g->launch.fp64_lanes_per_ray ? g->launch.fp64_lanes_per_ray : g->launch.lanes_per_ray;
     out->block = g->launch.block;
     out->blocks_per_sm = g->launch.blocks_per_sm;
     return 0;

@@ -129,6 +129,51 @@ cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm,
     return cudaGetLastError();
 }
 
+// Rays that start outside the box move to where they enter it: the slab
+// test gives the parameter interval [t_in, t_out] in which the line is
+// inside every slab; a ray with t_in <= t_out and t_out >= 0 starts at
+// r0 + max(t_in, 0) k, clamped into the closed box against rounding. Rays
+// inside are copied unchanged, rays that miss keep their outside origin.
+__global__ void enter_kernel(const double *__restrict__ origin, const double *__restrict__ dir, int64_t N,
+                             const GridDev *gp, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double r[3], k[3];
+        bool in = true;
+        for (int c = 0; c < 3; c++) {
+            r[c] = origin[3 * i + c];
+            k[c] = dir[3 * i + c];
+            in = in && r[c] >= gp->lo[c] && r[c] <= gp->hi[c];
+        }
+        if (!in) {
+            double t_in = -1e300, t_out = 1e300;
+            bool miss = false;
+            for (int c = 0; c < 3; c++) {
+                if (k[c] != 0.0) {
+                    const double t1 = (gp->lo[c] - r[c]) / k[c], t2 = (gp->hi[c] - r[c]) / k[c];
+                    t_in = fmax(t_in, fmin(t1, t2));
+                    t_out = fmin(t_out, fmax(t1, t2));
+                } else if (r[c] < gp->lo[c] || r[c] > gp->hi[c]) {
+                    miss = true;
+                }
+            }
+            if (!miss && t_in <= t_out && t_out >= 0.0) {
+                const double t = fmax(t_in, 0.0);
+                for (int c = 0; c < 3; c++) r[c] = fmin(fmax(__fma_rn(t, k[c], r[c]), gp->lo[c]), gp->hi[c]);
+            }
+        }
+        for (int c = 0; c < 3; c++) out[3 * i + c] = r[c];
+    }
+}
+
+cudaError_t launch_enter(const double *origin, const double *dir, int64_t N, const GridDev *gp, double *out, int sms,
+                         cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    int64_t blocks = (N + 255) / 256;
+    blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
+    enter_kernel<<<(unsigned)blocks, 256, 0, s>>>(origin, dir, N, gp, out);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // exclusive prefix sum over int64 (three passes: tiles, tile totals, fix-up)
 // ---------------------------------------------------------------------------

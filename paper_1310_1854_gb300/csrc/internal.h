@@ -103,7 +103,7 @@ struct GridView {
     int sms;
     const GridDev *d_desc;
     GridDev hd;  // host copy of *d_desc
-    int lanes_per_ray, block, blocks_per_sm;
+    int lanes_per_ray, block, blocks_per_sm, fp64_lanes_per_ray;
 };
 int grid_view(const struct vgrid *g, GridView *out);  // 0, or -1 for a host-only grid
 void set_error(const std::string &msg);              // message for vgrid_last_error()

@@ -7,7 +7,7 @@
 
 namespace vg {
 
-enum { MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_GRAD = 3 };
+enum { MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_GRAD = 3, MODE_INTERACT = 4, NUM_MODES = 5 };
 
 struct TraceArgs {
     const GridDev *grids;     // one descriptor per grid
@@ -22,6 +22,12 @@ struct TraceArgs {
     int64_t seg_cap;          // entries of seg_cell / seg_len; writes beyond are dropped
     const float *dL_dtau;
     float *dL_drho;
+    // interaction mode
+    const float *tau_int;     // optical depth at which each ray interacts
+    const float *weight;      // package weight per ray (nullable: 1)
+    int32_t *int_cell;        // caller id of the interaction cell, -1 if the ray escapes
+    float *int_s;             // distance from the origin to the interaction point (or the exit)
+    float *absorbed;          // per cell (caller ids), accumulated; nullable
     // single-grid launches read the grid and the ray set from here (kernel
     // parameter space) instead of from `grids` / `sets`
     GridDev g1;
@@ -32,7 +38,7 @@ struct TraceArgs {
 // fn[fp64][mode]: single-grid trace kernels of one lanes-per-ray value
 // (nullptr if absent); batch: the float32 tau kernel over many grids
 struct KernelSet {
-    const void *fn[2][4];
+    const void *fn[2][NUM_MODES];
     const void *batch;
 };
 
@@ -43,6 +49,8 @@ void kernel_table_lpr8(KernelSet &k);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s);
+cudaError_t launch_enter(const double *origin, const double *dir, int64_t N, const GridDev *gp, double *out, int sms,
+                         cudaStream_t s);
 cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long long *queue, StatsDev *stats,
                            cudaStream_t s);
 // what the start-cell kernel writes per ray (see locate_kernel)

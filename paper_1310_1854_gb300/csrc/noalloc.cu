@@ -92,6 +92,7 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
             rc = fail(VGRID_ERR_CUDA, cudaGetErrorString(e));
             break;
         }
+        if (fp64) v.lanes_per_ray = v.fp64_lanes_per_ray;
         vg::KernelSet ks{};
         switch (v.lanes_per_ray) {
             case 1: vg::kernel_table_lpr1(ks); break;

@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     double tau64 = 0.0;
     float tau32 = 0.f, tauc = 0.f;
     float dLr = 0.f;
+    float tint = 0.f, wgt = 1.f, att = 1.f;   // interaction mode: tau_int, weight, exp(-tau)
     int nseg = 0, zrun = 0, steps = 0, status = 0;
     int64_t seg_base = 0;
 
@@ -442,6 +443,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             th = tl = 0.f;
             if (MODE == MODE_FILL) seg_base = a.seg_off[ray];
             if (MODE == MODE_GRAD) dLr = __ldg(&a.dL_dtau[ray]);
+            if (MODE == MODE_INTERACT) {
+                tint = __ldg(&a.tau_int[ray]);
+                wgt = a.weight ? __ldg(&a.weight[ray]) : 1.f;
+                att = 1.f;
+            }
             // the start record was prepared by the start-cell kernel
             const RayPrep *pr = rs->start + li;
             int m;
@@ -490,6 +496,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                         if (rs->status) rs->status[li] = status;
                     }
                     if (MODE == MODE_COUNT) a.seg_off[ray] = 0;
+                    if (MODE == MODE_INTERACT) {
+                        a.int_cell[ray] = -1;
+                        a.int_s[ray] = 0.f;
+                    }
                 }
                 ray = -1;
                 continue;
@@ -569,6 +579,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 from64 = true;
             }
         }
+        bool interacted = false;  // interaction mode: the package interacts in this cell
         float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
         if (win > 0) {
             qn = __ldg(blk + win);
@@ -591,6 +602,27 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     }
                 }
                 if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[hdr_caller(hdr)], dLr * kappa * len);
+                if (MODE == MODE_INTERACT) {
+                    // the package is attenuated by exp(-dtau) in this cell; it
+                    // interacts here if the running tau reaches tau_int
+                    const float krho = __fmul_rn(kappa, hdr.z);
+                    const float dtau = __fmul_rn(krho, len);
+                    const float left = __fsub_rn(tint, tau32);
+                    if (left <= __fsub_rn(dtau, tauc)) {
+                        const float part = fmaxf(left, 0.0f);
+                        if (gl == 0) {
+                            if (a.absorbed) atomicAdd(&a.absorbed[hdr_caller(hdr)], wgt * att * -expm1f(-part));
+                            a.int_cell[ray] = hdr_caller(hdr);
+                            const float ds = krho > 0.0f ? fminf(__fdividef(part, krho), len) : 0.0f;
+                            a.int_s[ray] = __fadd_rn(__fadd_rn(th, tl), ds);
+                        }
+                        interacted = true;
+                    } else {
+                        if (gl == 0 && a.absorbed)
+                            atomicAdd(&a.absorbed[hdr_caller(hdr)], wgt * att * -expm1f(-dtau));
+                        att = __fmul_rn(att, __expf(-dtau));
+                    }
+                }
                 nseg++;
                 if (FP64) {
                     tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)hdr.z), s64));
@@ -606,6 +638,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 zrun++;
                 if (gl == 0) VG_STAT(S_ZERO, 1);
             }
+            if (MODE == MODE_INTERACT && interacted) to_wall = true;  // the path ends here
             // advance the point
             if (FP64) {
                 for (int c = 0; c < 3; c++) r64[c] = __dadd_rn(r64[c], __dmul_rn(s64, k64[c]));
@@ -667,6 +700,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     if (rs->status) rs->status[li] = status;
                 }
                 if (MODE == MODE_COUNT) a.seg_off[ray] = nseg;
+                if (MODE == MODE_INTERACT && !interacted) {
+                    a.int_cell[ray] = -1;  // escaped (or cut at the step limit)
+                    a.int_s[ray] = __fadd_rn(th, tl);
+                }
             }
             ray = -1;
         }

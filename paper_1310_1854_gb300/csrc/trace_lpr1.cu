@@ -13,6 +13,8 @@ void kernel_table_lpr1(KernelSet &k) {
     k.fn[1][MODE_COUNT] = (const void *)trace_kernel<1, true, MODE_COUNT, false>;
     k.fn[1][MODE_FILL] = (const void *)trace_kernel<1, true, MODE_FILL, false>;
     k.fn[1][MODE_GRAD] = nullptr;
+    k.fn[0][MODE_INTERACT] = (const void *)trace_kernel<1, false, MODE_INTERACT, false>;
+    k.fn[1][MODE_INTERACT] = nullptr;
     k.batch = (const void *)trace_kernel<1, false, MODE_TAU, true>;
 }
 

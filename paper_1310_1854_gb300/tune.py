@@ -81,7 +81,11 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
     if use_cache:
         hit = load_cache(path).get(key)
         if hit:
-            grid.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"])
+            cur = grid.get_launch()
+            if precision == "fp64":
+                grid.set_launch(cur["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], hit["lanes_per_ray"])
+            else:
+                grid.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], cur["fp64_lanes_per_ray"])
             return dict(hit, cached=True, key=key)
     n = min(sample, origin.shape[0])
     g = torch.Generator(device="cpu").manual_seed(1310_1854)
@@ -90,9 +94,13 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
     d = direction.index_select(0, sel).contiguous()
     tau = torch.empty(n, dtype=torch.float64 if precision == "fp64" else torch.float32, device=origin.device)
     prev = grid.get_launch()
+    fp64_lanes = prev["fp64_lanes_per_ray"]
 
     def time_fn(shape):
-        grid.set_launch(*shape)
+        if precision == "fp64":
+            grid.set_launch(prev["lanes_per_ray"], shape[1], shape[2], shape[0])
+        else:
+            grid.set_launch(shape[0], shape[1], shape[2], fp64_lanes)
         grid.trace(o, d, precision=precision, out_tau=tau)  # warm
         grid.enable_timing(True)
         grid.read_timing()
@@ -104,9 +112,9 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
     try:
         best, table = search(space, time_fn)
     except Exception:
-        grid.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"])
+        grid.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"], fp64_lanes)
         raise
-    grid.set_launch(*best)
+    time_fn(best)
     entry = {"lanes_per_ray": best[0], "block": best[1], "blocks_per_sm": best[2], "ms": table[f"{best[0]},{best[1]},{best[2]}"],
              "sample_rays": n, "table": table}
     if use_cache:

@@ -69,7 +69,7 @@ def run_case(g, rays, ref, lanes=(1, 4)):
     rt = ref.tau[ok]
     taus = []
     for lpr in lanes:
-        vg.set_launch(lanes_per_ray=lpr)
+        vg.set_launch(lanes_per_ray=lpr, fp64_lanes_per_ray=lpr)
         r64 = vg.trace(O, D, precision="fp64", segments=True, status=True)
         r32 = vg.trace(O, D, precision="fp32", segments=True, status=True)
         t32 = vg.trace(O, D, precision="fp32", stats=True)
@@ -376,3 +376,67 @@ def test_full_size_config4_batched_sampled():
         t = single.astype(np.float64)[sample]
         ok = ref.near_tie == 0
         assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
+
+
+def test_interaction_matches_oracle():
+    g, rays = gen.config1(4000)
+    ref = oracle_full(g, rays)
+    rng = gen.rng_for(300)
+    tau_int = (-np.log(rng.random(len(rays.origin)))).astype(np.float32)
+    w = rng.uniform(0.5, 2.0, len(rays.origin)).astype(np.float32)
+    cell_o, s_o, ab_o, amb = oracle.interact(ref, g.rho.astype(np.float64), tau_int.astype(np.float64),
+                                             weight=w.astype(np.float64))
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    cell, s, ab = vg.interact(O, D, dev(tau_int), dev(w), absorbed=True)
+    cell = cell.cpu().numpy()
+    s = s.cpu().numpy().astype(np.float64)
+    ab = ab.cpu().numpy().astype(np.float64)
+    ok = (ref.near_tie == 0) & ~amb
+    assert ok.sum() > 0.9 * len(ok)
+    np.testing.assert_array_equal(cell[ok], cell_o[ok])
+    # float32 tau and lengths: the interaction distance moves by tau error / (kappa rho)
+    L = ref.length
+    assert np.all(np.abs(s[ok] - s_o[ok]) <= 2e-5 * np.maximum(L[ok], 1e-3) + 1e-6)
+    # per cell, within float32 rounding of the sum of what each ray removed
+    np.testing.assert_allclose(ab.sum(), ab_o.sum(), rtol=1e-5)
+    assert np.all(np.abs(ab - ab_o) <= 2e-4 * np.abs(ab_o) + 1e-6 * ab_o.max())
+
+
+def test_rays_entering_from_outside():
+    g, _ = gen.config1(10)
+    rng = gen.rng_for(310)
+    O = gen.uniform_points(3000, rng, np.array([-2.5, -2.5, -2.5, 2.5, 2.5, 2.5]))
+    D = gen.isotropic_dirs(3000, rng)
+    E = oracle.enter_points(g.box, O, D)
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    ref = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), E, D, off=off, idx=idx)
+    vg = make(g)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    r64 = vg.trace(dev(O), dev(D), precision="fp64", segments=True, status=True, enter=True)
+    t32 = vg.trace(dev(O), dev(D), precision="fp32", status=True, enter=True)
+    from paper_1310_1854_gb300 import _lib
+    st = r64.status.cpu().numpy()
+    hit = ref.status == 0
+    assert hit.sum() > 500 and (~hit).sum() > 500
+    assert np.all(st[~hit] == _lib.RAY_OUTSIDE) and np.all(st[hit] == 0)
+    ok = np.nonzero(hit & (ref.near_tie == 0))[0]
+    check_segments(ref, ok, r64.seg_off, r64.seg_cell, r64.seg_len, diag, LEN64_REL)
+    t = t32.tau.cpu().numpy().astype(np.float64)[ok]
+    assert np.all(np.abs(t - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
+    assert np.all(t32.tau.cpu().numpy()[~hit] == 0)
+
+
+def test_grid_quality_matches_oracle_locate():
+    """Table 1's measure on a small disk grid: the GPU's C(r) gives the same
+    cells as the oracle's brute force, hence the same statistic."""
+    from paper_1310_1854_gb300.quality import grid_quality, sample_points
+    g = gen.make_disk_grid(20_000, 320)
+    vg = make(g)
+    q = grid_quality(vg, g.rho, gen.disk_density, n_points=20_000, seed=5)
+    P = sample_points(g.box, 20_000, 5)
+    cell = oracle.locate(g.sites, g.box, P)
+    d = gen.disk_density(P) - g.rho.astype(np.float64)[cell]
+    assert q["std"] == pytest.approx(float(d.std()), rel=1e-12)
+    assert q["mean"] == pytest.approx(float(d.mean()), rel=1e-9, abs=1e-15)

@@ -379,3 +379,81 @@ def test_status_codes():
     assert tr.status[0] in (0, 3)
     tr = oracle.trace(g.sites, g.box, g.rho, O[:1], D[:1], off=off, idx=idx, max_steps=1)
     assert tr.status[0] == 2 or tr.nseg[0] == 1
+
+
+# --------------------------------------------------------------------------
+# interaction sampling (the Monte Carlo step that consumes the path)
+# --------------------------------------------------------------------------
+
+def test_interaction_hand_worked():
+    """Two sites at (1,1,1), (3,1,1) in [0,4]^3, rho 2 and 3, ray from
+    (0.5,1,1) along +x: tau is 3 at x = 2 (after 1.5 in cell 0), so
+    tau_int = 4 is reached 1/3 further, in cell 1; the package loses
+    1 - e^-3 in cell 0 and e^-3 - e^-4 in cell 1. tau_int = 10 exceeds the
+    total 3 + 3*2 = 9: the ray leaves after 3.5."""
+    S = np.array([[1.0, 1, 1], [3.0, 1, 1]])
+    box = np.array([0.0, 0, 0, 4, 4, 4])
+    rho = np.array([2.0, 3.0])
+    c, off, idx = _full(S, box)
+    tr = oracle.trace(S, box, rho, np.array([[0.5, 1, 1]] * 2), np.array([[1.0, 0, 0]] * 2), off=off, idx=idx)
+    cell, s, ab, amb = oracle.interact(tr, rho, [4.0, 10.0], weight=[1.0, 2.0])
+    assert list(cell) == [1, -1]
+    np.testing.assert_allclose(s, [1.5 + 1.0 / 3.0, 3.5], rtol=1e-14)
+    np.testing.assert_allclose(ab, [(1 - np.exp(-3)) * 3.0, (np.exp(-3) - np.exp(-4)) + 2 * (np.exp(-3) - np.exp(-9))],
+                               rtol=1e-13)
+    assert not amb.any()
+
+
+def test_interaction_uniform_closed_form_and_conservation(grid300):
+    g, c, off, idx = grid300
+    rays = gen.uniform_rays(400, 61)
+    rho = np.full(len(g.sites), 0.8)
+    tr = oracle.trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, kappa=1.5)
+    rng = gen.rng_for(62)
+    tau_int = -np.log(rng.random(400))
+    w = rng.uniform(0.5, 2.0, 400)
+    cell, s, ab, amb = oracle.interact(tr, rho, tau_int, weight=w, kappa=1.5)
+    L = slab_length(g.box, rays.origin, rays.dir)
+    inside = tau_int < 1.5 * 0.8 * L
+    # uniform medium: the interaction distance is tau_int / (kappa rho)
+    np.testing.assert_allclose(s[inside], tau_int[inside] / 1.2, rtol=1e-12)
+    np.testing.assert_allclose(s[~inside], L[~inside], rtol=1e-12)
+    assert np.all(cell[~inside] == -1) and np.all(cell[inside] >= 0)
+    # the interaction point lies in the reported cell
+    pts = rays.origin[inside] + s[inside, None] * rays.dir[inside]
+    ok = ~amb[inside]
+    np.testing.assert_array_equal(nearest_site(g.sites, pts[ok]), cell[inside][ok])
+    # what the cells remove is what the package lost
+    lost = w * (1 - np.exp(-np.minimum(tau_int, 1.2 * L)))
+    np.testing.assert_allclose(ab.sum(), lost.sum(), rtol=1e-12)
+
+
+def test_enter_points_closed_form():
+    box = gen.CUBE_BOX
+    O = np.array([[-2.0, 0.1, 0.2], [0.5, 3.0, -0.25], [2.0, 2.0, 2.0], [-3.0, 0.0, 0.0], [0.1, 0.2, 0.3]])
+    D = np.array([[1.0, 0, 0], [0.0, -1, 0], [-1.0, -1, -1], [-1.0, 0, 0], [0.6, 0.8, 0.0]])
+    D = D / np.linalg.norm(D, axis=1)[:, None]
+    E = oracle.enter_points(box, O, D)
+    np.testing.assert_allclose(E[0], [-1.0, 0.1, 0.2])
+    np.testing.assert_allclose(E[1], [0.5, 1.0, -0.25])
+    np.testing.assert_allclose(E[2], [1.0, 1.0, 1.0], rtol=1e-15)      # enters at the corner
+    np.testing.assert_array_equal(E[3], O[3])                            # points away: misses
+    np.testing.assert_array_equal(E[4], O[4])                            # already inside
+    # random rays: an entry point is on the boundary and continues into the box
+    rng = gen.rng_for(71)
+    O = gen.uniform_points(2000, rng, np.array([-3.0, -3, -3, 3, 3, 3]))
+    D = gen.isotropic_dirs(2000, rng)
+    E = oracle.enter_points(box, O, D)
+    outside = ~np.all((O >= -1) & (O <= 1), axis=1)
+    moved = outside & np.any(E != O, axis=1)
+    assert moved.sum() > 100
+    on_face = np.any(np.isclose(np.abs(E[moved]), 1.0, rtol=0, atol=1e-14), axis=1)
+    assert np.all(on_face)
+    ahead = E[moved] + 1e-9 * D[moved]
+    assert np.all(np.abs(ahead) <= 1 + 1e-12)
+    # the missed rays never reach the box (checked by dense sampling)
+    missed = outside & ~np.any(E != O, axis=1)
+    ts = np.linspace(0, 12, 4001)
+    for i in np.nonzero(missed)[0][:100]:
+        p = O[i] + ts[:, None] * D[i]
+        assert not np.any(np.all(np.abs(p) <= 1 - 1e-9, axis=1))
