@@ -94,6 +94,9 @@ typedef struct {
                                   only vgrid_info, vgrid_get_neighbors,
                                   vgrid_get_cells and vgrid_destroy accept such a
                                   grid (no GPU needed) */
+    int32_t gpu_build;         /* 1: construct the cells on the current GPU (one
+                                  thread per cell; cells that exceed its fixed
+                                  capacities are rebuilt on the host) */
 } vgrid_opts;
 
 typedef struct {
@@ -115,6 +118,7 @@ typedef struct {
     double box[6];         /* xmin, ymin, zmin, xmax, ymax, zmax */
     double build_seconds;  /* host time of vgrid_create */
     int64_t device_bytes;  /* device memory held by the grid */
+    int64_t host_fallback_cells; /* gpu_build: cells rebuilt on the host */
 } vgrid_info_t;
 
 /* launch shape of the traversal kernels */

@@ -68,7 +68,7 @@ class VoronoiGrid:
     """
 
     def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=2.0,
-                 max_steps=100_000, threads=0, device=None, host_only=False):
+                 max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False):
         lib = load()
         S = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 3))
         B = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(6))
@@ -80,6 +80,7 @@ class VoronoiGrid:
         opts.blocks_per_site = float(blocks_per_site)
         opts.max_steps = int(max_steps)
         opts.host_only = int(bool(host_only))
+        opts.gpu_build = int(bool(gpu_build))
         h = ctypes.c_void_p()
         args = (S.ctypes.data_as(ctypes.c_void_p), S.shape[0], B.ctypes.data_as(ctypes.c_void_p),
                 ctypes.byref(opts), ctypes.byref(h))
@@ -110,7 +111,8 @@ class VoronoiGrid:
         i = _lib.Info()
         check(load().vgrid_info(self._h, ctypes.byref(i)))
         return {"M": i.M, "nnz": i.nnz, "block_entries": i.block_entries, "block_dim": list(i.block_dim),
-                "box": list(i.box), "build_seconds": i.build_seconds, "device_bytes": i.device_bytes}
+                "box": list(i.box), "build_seconds": i.build_seconds, "device_bytes": i.device_bytes,
+                "host_fallback_cells": i.host_fallback_cells}
 
     def neighbors(self):
         """CSR (off int64[M+1], idx int32) in the caller's ids, walls -1..-6."""

@@ -40,7 +40,8 @@ RAY_OK, RAY_OUTSIDE, RAY_STEP_LIMIT, RAY_BAD_DIR = 0, 1, 2, 3
 
 class Opts(ctypes.Structure):
     _fields_ = [("threads", c_int32), ("round_sites", c_int32), ("reorder", c_int32),
-                ("blocks_per_site", c_double), ("max_steps", c_int64), ("host_only", c_int32)]
+                ("blocks_per_site", c_double), ("max_steps", c_int64), ("host_only", c_int32),
+                ("gpu_build", c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -53,7 +54,8 @@ class Stats(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("M", c_int64), ("nnz", c_int64), ("block_entries", c_int64), ("block_dim", c_int32 * 3),
-                ("box", c_double * 6), ("build_seconds", c_double), ("device_bytes", c_int64)]
+                ("box", c_double * 6), ("build_seconds", c_double), ("device_bytes", c_int64),
+                ("host_fallback_cells", c_int64)]
 
 
 class Launch(ctypes.Structure):

@@ -102,6 +102,7 @@ struct vgrid {
     int64_t entry_cap = 0;
     double build_seconds = 0;
     int64_t device_bytes = 0;
+    int64_t host_fallback_cells = 0;
     // optional event record: {locate start, locate end} or {trace start, trace end}
     bool timing = false;
     std::vector<std::array<cudaEvent_t, 2>> ev_loc, ev_trace;
@@ -137,6 +138,7 @@ void vgrid_default_opts(vgrid_opts *o) {
     o->blocks_per_site = 2.0;
     o->max_steps = 100000;
     o->host_only = 0;
+    o->gpu_build = 0;
 }
 
 static void free_events(vgrid_t *g) {
@@ -219,9 +221,15 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         for (int c = 0; c < 3; c++) Si[3 * i + c] = S[3 * (int64_t)g->perm[i] + c];
 
     std::string err;
-    if (vg::build_cells(Si.data(), M, bbox, o.threads, g->cells, err) != 0) {
+    if (o.gpu_build && o.host_only) {
         delete g;
-        return fail(VGRID_ERR_BUILD, err);
+        return fail(VGRID_ERR_ARG, "gpu_build and host_only exclude each other");
+    }
+    const int brc = o.gpu_build ? vg::build_cells_gpu(Si.data(), M, bbox, o.threads, g->cells, err, &g->host_fallback_cells)
+                                : vg::build_cells(Si.data(), M, bbox, o.threads, g->cells, err);
+    if (brc != 0) {
+        delete g;
+        return fail(o.gpu_build ? VGRID_ERR_CUDA : VGRID_ERR_BUILD, err);
     }
     vg::build_blocks(bbox, g->cells.bbox, M, o.blocks_per_site, g->blocks);
     if ((int64_t)g->blocks.idx.size() >= ((int64_t)1 << 31)) {
@@ -374,6 +382,7 @@ int vgrid_info(const vgrid_t *g, vgrid_info_t *info) {
     }
     info->build_seconds = g->build_seconds;
     info->device_bytes = g->device_bytes;
+    info->host_fallback_cells = g->host_fallback_cells;
     return VGRID_OK;
 }
 

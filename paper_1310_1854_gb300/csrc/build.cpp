@@ -392,18 +392,17 @@ struct CellResult {
 // driver
 // ---------------------------------------------------------------------------
 
-int build_cells(const double *S, int64_t M, const double *box, int threads, CellsOut &out, std::string &err) {
+// Cells of the listed sites (all sites if ids == nullptr): neighbour lists
+// into nbr[m], volumes into vol[m], bounding boxes into bbox[6m].
+int build_cells_into(const double *S, int64_t M, const double *box, int threads, const std::vector<int32_t> *ids,
+                     std::vector<std::vector<int32_t>> &nbr, double *volume, double *bbox_out, std::string &err) {
     KdTree tree;
     tree.build(S, M);
     const double diag = std::sqrt((box[3] - box[0]) * (box[3] - box[0]) + (box[4] - box[1]) * (box[4] - box[1]) +
                                   (box[5] - box[2]) * (box[5] - box[2]));
     const double eps = 1e-12 * diag;
     const double vbox = (box[3] - box[0]) * (box[4] - box[1]) * (box[5] - box[2]);
-
-    out.off.assign(M + 1, 0);
-    out.vol.assign(M, 0.0);
-    out.bbox.assign(6 * M, 0.0);
-    std::vector<std::vector<int32_t>> nbr(M);
+    const int64_t count = ids ? (int64_t)ids->size() : M;
     std::atomic<int64_t> next{0};
     std::atomic<int64_t> failed{-1};
 
@@ -413,9 +412,10 @@ int build_cells(const double *S, int64_t M, const double *box, int threads, Cell
         std::vector<int32_t> stack;
         for (;;) {
             int64_t m0 = next.fetch_add(64);
-            if (m0 >= M || failed.load() >= 0) break;
-            int64_t m1 = std::min<int64_t>(M, m0 + 64);
-            for (int64_t m = m0; m < m1; m++) {
+            if (m0 >= count || failed.load() >= 0) break;
+            int64_t m1 = std::min<int64_t>(count, m0 + 64);
+            for (int64_t mi = m0; mi < m1; mi++) {
+                const int64_t m = ids ? (*ids)[mi] : mi;
                 const double *pm = S + 3 * m;
                 P.make_box(box);
                 double rmax = P.rmax(pm);
@@ -466,19 +466,19 @@ int build_cells(const double *S, int64_t M, const double *box, int threads, Cell
                 }
                 std::sort(nb.begin(), nb.end());
                 nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
-                double *bb = &out.bbox[6 * m];
+                double *bb = &bbox_out[6 * m];
                 for (int c = 0; c < 3; c++) { bb[c] = INFINITY; bb[3 + c] = -INFINITY; }
                 for (size_t i = 0; i < P.V.size(); i += 3)
                     for (int c = 0; c < 3; c++) {
                         bb[c] = std::min(bb[c], P.V[i + c]);
                         bb[3 + c] = std::max(bb[3 + c], P.V[i + c]);
                     }
-                out.vol[m] = vol;
+                volume[m] = vol;
             }
         }
     };
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
-    threads = (int)std::min<int64_t>(threads, std::max<int64_t>(1, M / 64 + 1));
+    threads = (int)std::min<int64_t>(threads, std::max<int64_t>(1, count / 64 + 1));
     std::vector<std::thread> pool;
     for (int t = 1; t < threads; t++) pool.emplace_back(work);
     work();
@@ -487,9 +487,24 @@ int build_cells(const double *S, int64_t M, const double *box, int threads, Cell
         err = "cell construction failed for site " + std::to_string(failed.load());
         return -1;
     }
+    return 0;
+}
+
+void cells_to_csr(const std::vector<std::vector<int32_t>> &nbr, CellsOut &out) {
+    const int64_t M = (int64_t)nbr.size();
+    out.off.assign(M + 1, 0);
     for (int64_t m = 0; m < M; m++) out.off[m + 1] = out.off[m] + (int64_t)nbr[m].size();
     out.idx.resize(out.off[M]);
     for (int64_t m = 0; m < M; m++) std::copy(nbr[m].begin(), nbr[m].end(), out.idx.begin() + out.off[m]);
+}
+
+int build_cells(const double *S, int64_t M, const double *box, int threads, CellsOut &out, std::string &err) {
+    std::vector<std::vector<int32_t>> nbr(M);
+    out.vol.assign(M, 0.0);
+    out.bbox.assign(6 * M, 0.0);
+    int rc = build_cells_into(S, M, box, threads, nullptr, nbr, out.vol.data(), out.bbox.data(), err);
+    if (rc) return rc;
+    cells_to_csr(nbr, out);
     return 0;
 }
 

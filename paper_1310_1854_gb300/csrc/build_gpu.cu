@@ -1,0 +1,434 @@
+// GPU construction of the Voronoi cells: the parallel set-up the paper
+// names as future work (Sect. 3.6). Same definition as the host builder: the
+// cell of site m is the domain box cut by the bisector half-space of every
+// site that can reach it (Sect. 2.1, Eq. 1-3); a site farther than twice the
+// largest vertex radius cannot, so the search stops once every unvisited
+// site is that far (security radius).
+//
+// Sites are first sorted into a uniform grid of buckets (counting sort; each
+// bucket's list is then ordered by site index so the result does not depend
+// on atomic order). One thread builds one cell: a convex polyhedron in
+// float64 with shared vertices and faces as vertex loops, cut plane by plane
+// while the buckets are visited ring by ring around the site. Fixed
+// capacities keep the polyhedron in local memory; a cell that would overflow
+// them is flagged and rebuilt by the host builder.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace vg {
+namespace {
+
+constexpr int kNV = 96;    // vertices of the polyhedron
+constexpr int kNF = 48;    // faces
+constexpr int kNL = 320;   // entries of all face loops
+constexpr int kNE = 64;    // crossed edges of one cut
+constexpr int kCap = 64;   // neighbour ids written back per cell
+
+struct BucketGrid {
+    double lo[3];
+    double inv[3];   // buckets per unit length
+    double wmin;     // smallest bucket width
+    int dim[3];
+};
+
+struct DPoly {
+    double x[kNV], y[kNV], z[kNV];
+    int nv;
+    int fid[kNF];
+    short fbeg[kNF], flen[kNF];
+    int nf;
+    unsigned char L[kNL];
+    int nl;
+};
+
+struct Scratch {
+    double fv[kNV];
+    int fid[kNF];
+    short fbeg[kNF], flen[kNF];
+    unsigned char L[kNL];
+    unsigned char seg_a[kNF], seg_b[kNF];
+    int ekey[kNE];
+    unsigned char evid[kNE];
+    unsigned char remap[kNV];
+    double x[kNV], y[kNV], z[kNV];
+};
+
+__device__ __forceinline__ int bucket_coord(double v, double lo, double inv, int dim) {
+    int i = (int)((v - lo) * inv);
+    return max(0, min(i, dim - 1));
+}
+
+__global__ void bucket_count_kernel(const double *S, int64_t M, BucketGrid bg, int *bidx, int64_t *cnt) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        const int i = bucket_coord(S[3 * m], bg.lo[0], bg.inv[0], bg.dim[0]);
+        const int j = bucket_coord(S[3 * m + 1], bg.lo[1], bg.inv[1], bg.dim[1]);
+        const int k = bucket_coord(S[3 * m + 2], bg.lo[2], bg.inv[2], bg.dim[2]);
+        const int b = (i * bg.dim[1] + j) * bg.dim[2] + k;
+        bidx[m] = b;
+        atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[b]), 1ull);
+    }
+}
+
+__global__ void bucket_fill_kernel(const int *bidx, int64_t M, int64_t *cursor, int *bsites) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long at = atomicAdd(reinterpret_cast<unsigned long long *>(&cursor[bidx[m]]), 1ull);
+        bsites[at] = (int)m;
+    }
+}
+
+// order every bucket's list by site index (insertion sort; lists are short)
+__global__ void bucket_sort_kernel(const int64_t *off, int64_t K, int *bsites) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < K; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = off[b], e = off[b + 1];
+        for (int64_t i = s + 1; i < e; i++) {
+            const int v = bsites[i];
+            int64_t k = i - 1;
+            while (k >= s && bsites[k] > v) {
+                bsites[k + 1] = bsites[k];
+                k--;
+            }
+            bsites[k + 1] = v;
+        }
+    }
+}
+
+__device__ void poly_box(DPoly &P, const double *box) {
+    P.nv = 8;
+    for (int i = 0; i < 8; i++) {
+        P.x[i] = (i & 4) ? box[3] : box[0];
+        P.y[i] = (i & 2) ? box[4] : box[1];
+        P.z[i] = (i & 1) ? box[5] : box[2];
+    }
+    // counter-clockwise seen from outside; walls -1..-6 = x min, x max, y min, y max, z min, z max
+    const unsigned char quad[6][4] = {{0, 1, 3, 2}, {4, 6, 7, 5}, {0, 4, 5, 1}, {2, 3, 7, 6}, {0, 2, 6, 4}, {1, 5, 7, 3}};
+    P.nf = 6;
+    P.nl = 24;
+    for (int w = 0; w < 6; w++) {
+        P.fid[w] = -(w + 1);
+        P.fbeg[w] = (short)(4 * w);
+        P.flen[w] = 4;
+        for (int k = 0; k < 4; k++) P.L[4 * w + k] = quad[w][k];
+    }
+}
+
+__device__ double poly_rmax2(const DPoly &P, double px, double py, double pz) {
+    double r2 = 0.0;
+    for (int i = 0; i < P.nv; i++) {
+        const double dx = P.x[i] - px, dy = P.y[i] - py, dz = P.z[i] - pz;
+        r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+    }
+    return r2;
+}
+
+// Cut P by {x : n.x <= d}. 1: changed, 0: untouched, -1: capacity exceeded
+// or topology broken (the caller rebuilds the cell on the host).
+__device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, double d, int id, double eps) {
+    bool any_out = false;
+    for (int i = 0; i < P.nv; i++) {
+        W.fv[i] = nx * P.x[i] + ny * P.y[i] + nz * P.z[i] - d;
+        any_out |= W.fv[i] > eps;
+    }
+    if (!any_out) return 0;
+    int ne = 0, nseg = 0, nf2 = 0, nl2 = 0, nv = P.nv;
+    for (int f = 0; f < P.nf; f++) {
+        const int b = P.fbeg[f], k = P.flen[f];
+        int out_count = 0;
+        for (int i = 0; i < k; i++) out_count += W.fv[P.L[b + i]] > eps;
+        if (out_count == k) continue;
+        if (nf2 >= kNF) return -1;
+        const int start = nl2;
+        int entry = -1, exit_ = -1;
+        for (int i = 0; i < k; i++) {
+            const int va = P.L[b + i], vb = P.L[b + (i + 1) % k];
+            const bool ao = W.fv[va] > eps, bo = W.fv[vb] > eps;
+            if (!ao) {
+                if (nl2 >= kNL) return -1;
+                W.L[nl2++] = (unsigned char)va;
+            }
+            if (ao != bo) {
+                const bool strict = !ao ? W.fv[va] < -eps : W.fv[vb] < -eps;
+                int x = !ao ? va : vb;
+                if (strict) {
+                    // the vertex on edge (va, vb), made once from the lower index
+                    const int lo = min(va, vb), hi = max(va, vb);
+                    const int key = lo * 256 + hi;
+                    x = -1;
+                    for (int e = 0; e < ne; e++)
+                        if (W.ekey[e] == key) { x = W.evid[e]; break; }
+                    if (x < 0) {
+                        if (ne >= kNE || nv >= kNV) return -1;
+                        const double t = W.fv[lo] / (W.fv[lo] - W.fv[hi]);
+                        P.x[nv] = P.x[lo] + t * (P.x[hi] - P.x[lo]);
+                        P.y[nv] = P.y[lo] + t * (P.y[hi] - P.y[lo]);
+                        P.z[nv] = P.z[lo] + t * (P.z[hi] - P.z[lo]);
+                        W.fv[nv] = 0.0;
+                        W.ekey[ne] = key;
+                        W.evid[ne] = (unsigned char)nv;
+                        ne++;
+                        x = nv++;
+                    }
+                    if (nl2 >= kNL) return -1;
+                    W.L[nl2++] = (unsigned char)x;
+                }
+                if (!ao) exit_ = x;
+                else entry = x;
+            }
+        }
+        if (entry >= 0 && exit_ >= 0 && entry != exit_) {
+            if (nseg >= kNF) return -1;
+            W.seg_a[nseg] = (unsigned char)entry;
+            W.seg_b[nseg] = (unsigned char)exit_;
+            nseg++;
+        }
+        if (nl2 - start >= 3) {
+            W.fid[nf2] = P.fid[f];
+            W.fbeg[nf2] = (short)start;
+            W.flen[nf2] = (short)(nl2 - start);
+            nf2++;
+        } else {
+            nl2 = start;
+        }
+    }
+    if (nseg > 0) {
+        // cap face: chain the cut segments entry -> exit
+        const int start = nl2;
+        int cur = W.seg_a[0];
+        const int first = cur;
+        bool ok = true;
+        unsigned long long used = 0ull;
+        for (int step = 0; step < nseg; step++) {
+            int pick = -1;
+            for (int i = 0; i < nseg; i++)
+                if (!((used >> i) & 1ull) && W.seg_a[i] == cur) { pick = i; break; }
+            if (pick < 0) { ok = false; break; }
+            used |= 1ull << pick;
+            if (nl2 >= kNL) return -1;
+            W.L[nl2++] = W.seg_a[pick];
+            cur = W.seg_b[pick];
+        }
+        if (!ok || cur != first) return -1;  // inconsistent topology: leave it to the host
+        if (nl2 - start >= 3) {
+            if (nf2 >= kNF) return -1;
+            W.fid[nf2] = id;
+            W.fbeg[nf2] = (short)start;
+            W.flen[nf2] = (short)(nl2 - start);
+            nf2++;
+        } else {
+            nl2 = start;
+        }
+    }
+    // compact the vertices that are still referenced
+    for (int i = 0; i < nv; i++) W.remap[i] = 255;
+    int nv2 = 0;
+    for (int i = 0; i < nl2; i++) {
+        const int v = W.L[i];
+        if (W.remap[v] == 255) {
+            W.remap[v] = (unsigned char)nv2;
+            W.x[nv2] = P.x[v];
+            W.y[nv2] = P.y[v];
+            W.z[nv2] = P.z[v];
+            nv2++;
+        }
+        P.L[i] = W.remap[v];
+    }
+    for (int i = 0; i < nv2; i++) {
+        P.x[i] = W.x[i];
+        P.y[i] = W.y[i];
+        P.z[i] = W.z[i];
+    }
+    P.nv = nv2;
+    P.nl = nl2;
+    P.nf = nf2;
+    for (int f = 0; f < nf2; f++) {
+        P.fid[f] = W.fid[f];
+        P.fbeg[f] = W.fbeg[f];
+        P.flen[f] = W.flen[f];
+    }
+    return nf2 >= 4 ? 1 : -1;
+}
+
+__global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, BucketGrid bg, const int64_t *boff,
+                                                    const int *bsites, double box0, double box1, double box2,
+                                                    double box3, double box4, double box5, double eps, int *out_cnt,
+                                                    int *out_nbr, double *out_vol, double *out_bbox, int *out_fail) {
+    DPoly P;
+    Scratch W;
+    const double box[6] = {box0, box1, box2, box3, box4, box5};
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        const double px = S[3 * m], py = S[3 * m + 1], pz = S[3 * m + 2];
+        poly_box(P, box);
+        double rmax = sqrt(poly_rmax2(P, px, py, pz));
+        const int bi = bucket_coord(px, bg.lo[0], bg.inv[0], bg.dim[0]);
+        const int bj = bucket_coord(py, bg.lo[1], bg.inv[1], bg.dim[1]);
+        const int bk = bucket_coord(pz, bg.lo[2], bg.inv[2], bg.dim[2]);
+        const int smax = max(bg.dim[0], max(bg.dim[1], bg.dim[2]));
+        int fail = 0;
+        for (int s = 0; s <= smax && !fail; s++) {
+            for (int di = -s; di <= s && !fail; di++) {
+                const int i = bi + di;
+                if (i < 0 || i >= bg.dim[0]) continue;
+                for (int dj = -s; dj <= s && !fail; dj++) {
+                    const int j = bj + dj;
+                    if (j < 0 || j >= bg.dim[1]) continue;
+                    const bool shell = abs(di) == s || abs(dj) == s;
+                    for (int dk = -s; dk <= s && !fail; dk += (shell || s == 0) ? 1 : 2 * s) {
+                        const int k = bk + dk;
+                        if (k < 0 || k >= bg.dim[2]) continue;
+                        const int b = (i * bg.dim[1] + j) * bg.dim[2] + k;
+                        for (int64_t q = boff[b]; q < boff[b + 1]; q++) {
+                            const int jj = bsites[q];
+                            if (jj == (int)m) continue;
+                            const double qx = S[3 * (int64_t)jj], qy = S[3 * (int64_t)jj + 1], qz = S[3 * (int64_t)jj + 2];
+                            const double dx = qx - px, dy = qy - py, dz = qz - pz;
+                            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+                            if (dist > 2.0 * rmax + 4.0 * eps) continue;
+                            const double nx = dx / dist, ny = dy / dist, nz = dz / dist;
+                            const double d = nx * 0.5 * (qx + px) + ny * 0.5 * (qy + py) + nz * 0.5 * (qz + pz);
+                            const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps);
+                            if (rc < 0) { fail = 1; break; }
+                            if (rc > 0) rmax = sqrt(poly_rmax2(P, px, py, pz));
+                        }
+                    }
+                }
+            }
+            // every unvisited site is at least s bucket widths away
+            if (2.0 * rmax + 4.0 * eps < (double)s * bg.wmin) break;
+        }
+        // faces of positive area -> neighbours; volume as pyramids from the site; bounding box
+        int cnt = 0;
+        double vol = 0.0;
+        double bb[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
+        for (int f = 0; f < P.nf && !fail; f++) {
+            const int b = P.fbeg[f], k = P.flen[f];
+            const int v0 = P.L[b];
+            double sx = 0, sy = 0, sz = 0, sv = 0;
+            for (int t = 1; t + 1 < k; t++) {
+                const int v1 = P.L[b + t], v2 = P.L[b + t + 1];
+                const double ax = P.x[v1] - P.x[v0], ay = P.y[v1] - P.y[v0], az = P.z[v1] - P.z[v0];
+                const double cx = P.x[v2] - P.x[v0], cy = P.y[v2] - P.y[v0], cz = P.z[v2] - P.z[v0];
+                const double ux = ay * cz - az * cy, uy = az * cx - ax * cz, uz = ax * cy - ay * cx;
+                sx += ux;
+                sy += uy;
+                sz += uz;
+                // signed volume of the tetrahedron (site, v0, v1, v2)
+                sv += ((P.x[v0] - px) * ux + (P.y[v0] - py) * uy + (P.z[v0] - pz) * uz) / 6.0;
+            }
+            vol += fabs(sv);
+            const double area2 = sx * sx + sy * sy + sz * sz;
+            if (area2 > 0.0) {
+                if (cnt >= kCap) { fail = 1; break; }
+                out_nbr[m * kCap + cnt] = P.fid[f];
+                cnt++;
+            }
+        }
+        for (int i = 0; i < P.nv; i++) {
+            bb[0] = fmin(bb[0], P.x[i]);
+            bb[1] = fmin(bb[1], P.y[i]);
+            bb[2] = fmin(bb[2], P.z[i]);
+            bb[3] = fmax(bb[3], P.x[i]);
+            bb[4] = fmax(bb[4], P.y[i]);
+            bb[5] = fmax(bb[5], P.z[i]);
+        }
+        out_cnt[m] = cnt;
+        out_vol[m] = vol;
+        for (int c = 0; c < 6; c++) out_bbox[6 * m + c] = bb[c];
+        out_fail[m] = fail;
+    }
+}
+
+}  // namespace
+
+int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, CellsOut &out, std::string &err,
+                    int64_t *host_fallback_cells) {
+    const double ext[3] = {box[3] - box[0], box[4] - box[1], box[5] - box[2]};
+    const double diag = std::sqrt(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
+    const double eps = 1e-12 * diag;
+    BucketGrid bg;
+    const double target = std::max(1.0, 0.5 * (double)M);  // about two sites per bucket
+    const double w = std::cbrt(ext[0] * ext[1] * ext[2] / target);
+    bg.wmin = 1e300;
+    int64_t K = 1;
+    for (int c = 0; c < 3; c++) {
+        bg.dim[c] = (int)std::min<long>(std::max<long>(std::lround(ext[c] / w), 1), 512);
+        bg.lo[c] = box[c];
+        bg.inv[c] = bg.dim[c] / ext[c];
+        bg.wmin = std::min(bg.wmin, ext[c] / bg.dim[c]);
+        K *= bg.dim[c];
+    }
+    double *dS = nullptr;
+    int *bidx = nullptr, *bsites = nullptr, *cnt = nullptr, *nbr = nullptr, *fail = nullptr;
+    int64_t *boff = nullptr, *cursor = nullptr, *tmp = nullptr;
+    double *vol = nullptr, *bbox = nullptr;
+    auto cleanup = [&]() {
+        void *ptrs[] = {dS, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    };
+    auto bad = [&](cudaError_t e, const char *what) {
+        err = std::string("GPU cell construction: ") + what + ": " + cudaGetErrorString(e);
+        cleanup();
+        return -1;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&dS, sizeof(double) * 3 * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&bidx, sizeof(int) * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&bsites, sizeof(int) * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&boff, sizeof(int64_t) * (K + 1))) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&cursor, sizeof(int64_t) * (K + 1))) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&tmp, sizeof(int64_t) * scan_tmp_elems(K))) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&cnt, sizeof(int) * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&nbr, sizeof(int) * kCap * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&fail, sizeof(int) * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&vol, sizeof(double) * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMalloc(&bbox, sizeof(double) * 6 * M)) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMemcpy(dS, S, sizeof(double) * 3 * M, cudaMemcpyHostToDevice)) != cudaSuccess) return bad(e, "upload");
+    if ((e = cudaMemset(boff, 0, sizeof(int64_t) * (K + 1))) != cudaSuccess) return bad(e, "memset");
+    const int blocks = (int)std::min<int64_t>((M + 255) / 256, 65535);
+    bucket_count_kernel<<<blocks, 256>>>(dS, M, bg, bidx, boff);
+    if ((e = launch_exclusive_scan(boff, K, tmp, 0)) != cudaSuccess) return bad(e, "scan");
+    if ((e = cudaMemcpy(cursor, boff, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToDevice)) != cudaSuccess)
+        return bad(e, "copy");
+    bucket_fill_kernel<<<blocks, 256>>>(bidx, M, cursor, bsites);
+    bucket_sort_kernel<<<(int)std::min<int64_t>((K + 255) / 256, 65535), 256>>>(boff, K, bsites);
+    const int cblocks = (int)std::min<int64_t>((M + 127) / 128, 1 << 20);
+    cells_kernel<<<cblocks, 128>>>(dS, M, bg, boff, bsites, box[0], box[1], box[2], box[3], box[4], box[5], eps, cnt,
+                                   nbr, vol, bbox, fail);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cells kernel");
+    std::vector<int> hcnt(M), hfail(M), hnbr((size_t)kCap * M);
+    out.vol.assign(M, 0.0);
+    out.bbox.assign(6 * M, 0.0);
+    if ((e = cudaMemcpy(hcnt.data(), cnt, sizeof(int) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(hfail.data(), fail, sizeof(int) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(hnbr.data(), nbr, sizeof(int) * kCap * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(out.vol.data(), vol, sizeof(double) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (e = cudaMemcpy(out.bbox.data(), bbox, sizeof(double) * 6 * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bad(e, "download");
+    cleanup();
+    std::vector<std::vector<int32_t>> lists(M);
+    std::vector<int32_t> redo;
+    for (int64_t m = 0; m < M; m++) {
+        if (hfail[m]) {
+            redo.push_back((int32_t)m);
+            continue;
+        }
+        lists[m].assign(hnbr.begin() + m * kCap, hnbr.begin() + m * kCap + hcnt[m]);
+        std::sort(lists[m].begin(), lists[m].end());
+        lists[m].erase(std::unique(lists[m].begin(), lists[m].end()), lists[m].end());
+    }
+    if (host_fallback_cells) *host_fallback_cells = (int64_t)redo.size();
+    if (!redo.empty()) {
+        if (build_cells_into(S, M, box, threads, &redo, lists, out.vol.data(), out.bbox.data(), err) != 0) return -1;
+    }
+    cells_to_csr(lists, out);
+    return 0;
+}
+
+}  // namespace vg

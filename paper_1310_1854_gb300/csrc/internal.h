@@ -25,6 +25,13 @@ struct BlocksOut {
 };
 
 int build_cells(const double *sites, int64_t M, const double *box, int threads, CellsOut &out, std::string &err);
+int build_cells_into(const double *sites, int64_t M, const double *box, int threads, const std::vector<int32_t> *ids,
+                     std::vector<std::vector<int32_t>> &nbr, double *volume, double *bbox, std::string &err);
+void cells_to_csr(const std::vector<std::vector<int32_t>> &nbr, CellsOut &out);
+// GPU construction (build_gpu.cu); cells the device could not hold are rebuilt
+// on the host. Returns 0, or -1 with err set.
+int build_cells_gpu(const double *sites, int64_t M, const double *box, int threads, CellsOut &out, std::string &err,
+                    int64_t *host_fallback_cells);
 void morton_order(const double *sites, int64_t M, const double *box, std::vector<int32_t> &perm);
 void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M, double blocks_per_site,
                   BlocksOut &out);
