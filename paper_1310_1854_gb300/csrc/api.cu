@@ -237,8 +237,10 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
     }
 
-    // cell blocks: header (caller id, count, rho = 1, internal id), then one
-    // record per neighbour (site of the neighbour, its block offset) or wall
+    // cell blocks: header (caller id, count, rho = 1, N1max), then one record
+    // per neighbour (site of the neighbour, its block offset) or wall.
+    // N1max bounds |p_j - p_i|_1 over the cell's neighbours from above (with
+    // room for the float32 rounding of the differences on the device).
     std::vector<int64_t> boffs(M + 1, 0);
     for (int64_t i = 0; i < M; i++) boffs[i + 1] = boffs[i] + 1 + (g->cells.off[i + 1] - g->cells.off[i]);
     if (boffs[M] + 8 >= ((int64_t)1 << 31)) {
@@ -255,7 +257,17 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         put_int(h + 0, g->perm[i]);
         put_int(h + 1, (int32_t)(e - b));
         h[2] = 1.0f;
-        put_int(h + 3, (int32_t)i);
+        double n1max = 0.0;
+        for (int64_t q = b; q < e; q++) {
+            const int32_t j = g->cells.idx[q];
+            if (j < 0) continue;
+            double n1 = 0.0;
+            for (int c = 0; c < 3; c++) n1 += std::fabs(Si[3 * (int64_t)j + c] - Si[3 * i + c]);
+            n1max = std::max(n1max, n1);
+        }
+        float n1f = (float)(n1max * (1.0 + 1e-6));
+        if ((double)n1f < n1max * (1.0 + 1e-6)) n1f = std::nextafter(n1f, INFINITY);
+        h[3] = n1f;
         for (int64_t q = b; q < e; q++) {
             float *r = &blocks[4 * (boffs[i] + 1 + (q - b))];
             const int32_t j = g->cells.idx[q];

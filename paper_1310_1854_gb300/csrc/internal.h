@@ -45,9 +45,10 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 //
 // cells    cell blocks, float4: cell i starts at block offset B_i with a
 //          header (bits of the caller's id, bits of the neighbour count c,
-//          rho, bits of i) followed by c records (x, y, z of the neighbour's
-//          site, bits of the neighbour's block offset B_j, or of a wall id
-//          -1..-6). Each cell has at least four records.
+//          rho, N1max = an upper bound of |p_j - p_i|_1 over the neighbours)
+//          followed by c records (x, y, z of the neighbour's site, bits of the
+//          neighbour's block offset B_j, or of a wall id -1..-6). Each cell
+//          has at least four records.
 // site[i]  float4 (x, y, z, bits of B_i): positions for C(r) and ray starts.
 // perm[i]  caller's id of internal cell i.
 // blk_off, blk_rec  block lists of Sect. 2.3: for every block, records

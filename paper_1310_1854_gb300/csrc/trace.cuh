@@ -269,23 +269,24 @@ struct Cand32 {
 
 // Terms of the bisector of the current site (origin of the local frame) and
 // site q, with their rounding-error bounds (u = 2^-24, n~ = fl(q - p),
-// r~ within 2u|r| + e_r):
-//   |den~ - n.k|  <= dden = 6u |n~|_1               (two roundings of n, three of the dot)
-//   |num~ - n.w|  <= dnum = |n~|_1 (4u |n~|_1 + 8u |r~|_1 + 2 e_r),   w = n/2 - r
+// r~ within 2u|r| + e_r, N = the cell's bound on |n|_1 from its header):
+//   |den~ - n.k|  <= dden = 6u N                    (two roundings of n, three of the dot)
+//   |num~ - n.w|  <= dnum = N (4u N + 8u |r~|_1 + 2 e_r),   w = n/2 - r
+// dden and dnum are the same for every plane of the cell (computed once per
+// crossing from N).
 struct Plane32 {
     float num, den, dnum, dden;
 };
 
 __device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float pmz, float rx, float ry, float rz,
-                                           float rr, float Kx, float Ky, float Kz) {
+                                           float dnum, float dden, float Kx, float Ky, float Kz) {
     Plane32 p;
     const float nx = __fsub_rn(q.x, pmx), ny = __fsub_rn(q.y, pmy), nz = __fsub_rn(q.z, pmz);
     p.den = __fmaf_rn(nz, Kz, __fmaf_rn(ny, Ky, __fmul_rn(nx, Kx)));
-    const float n1 = __fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz));
-    p.dden = __fmul_rn(kCDen, n1);
+    p.dden = dden;
     const float wx = __fmaf_rn(0.5f, nx, -rx), wy = __fmaf_rn(0.5f, ny, -ry), wz = __fmaf_rn(0.5f, nz, -rz);
     p.num = __fmaf_rn(nz, wz, __fmaf_rn(ny, wy, __fmul_rn(nx, wx)));
-    p.dnum = __fmul_rn(n1, __fmaf_rn(kCA, n1, rr));
+    p.dnum = dnum;
     return p;
 }
 
@@ -297,8 +298,9 @@ __device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float
 // Walls (handled by the wall candidate t_max - t) and positions past the
 // count are masked the same way.
 __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float pmx, float pmy, float pmz, float rx,
-                                           float ry, float rz, float rr, float Kx, float Ky, float Kz, Cand32 &c) {
-    const Plane32 p = plane32(q, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz);
+                                           float ry, float rz, float dnum, float dden, float Kx, float Ky, float Kz,
+                                           Cand32 &c) {
+    const Plane32 p = plane32(q, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz);
     const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
     float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
@@ -311,25 +313,35 @@ __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float 
 
 // Records blk[1..cnt]; lane gl of the group takes records gl+1, gl+1+LPR, ...
 // four at a time. Every cell has at least four faces, so the first four
-// records exist.
+// records exist; with one lane per ray the caller loads them (f0..f3)
+// together with the header, so they do not wait for the count.
 template <int LPR>
-__device__ __forceinline__ void exit32(const float4 *blk, int cnt, float pmx, float pmy, float pmz, float rx,
-                                       float ry, float rz, float rr, float Kx, float Ky, float Kz, unsigned gmask,
-                                       int gl, int gbase, Cand32 &c) {
+__device__ __forceinline__ void exit32(const float4 *blk, int cnt, float4 f0, float4 f1, float4 f2, float4 f3,
+                                       float pmx, float pmy, float pmz, float rx, float ry, float rz, float dnum,
+                                       float dden, float Kx, float Ky, float Kz, unsigned gmask, int gl, int gbase,
+                                       Cand32 &c) {
     c.L1 = __int_as_float(0x7f800000);
     c.L2 = c.L1;
     c.p1 = 0;
-    for (int p = 1 + gl; p <= cnt; p += 4 * LPR) {
+    int p = 1 + gl;
+    if (LPR == 1) {
+        consider32(1, true, f0, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(2, true, f1, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(3, true, f2, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(4, true, f3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        p = 5;
+    }
+    for (; p <= cnt; p += 4 * LPR) {
         const int p0 = p, p1 = p + LPR, p2 = p + 2 * LPR, p3 = p + 3 * LPR;
         const float4 z4 = make_float4(0.f, 0.f, 0.f, __int_as_float(-8));
         const float4 q0 = __ldg(blk + p0);
         const float4 q1 = p1 <= cnt ? __ldg(blk + p1) : z4;
         const float4 q2 = p2 <= cnt ? __ldg(blk + p2) : z4;
         const float4 q3 = p3 <= cnt ? __ldg(blk + p3) : z4;
-        consider32(p0, true, q0, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(p1, p1 <= cnt, q1, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(p2, p2 <= cnt, q2, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
-        consider32(p3, p3 <= cnt, q3, pmx, pmy, pmz, rx, ry, rz, rr, Kx, Ky, Kz, c);
+        consider32(p0, true, q0, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(p1, p1 <= cnt, q1, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(p2, p2 <= cnt, q2, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(p3, p3 <= cnt, q3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
     }
     if (LPR > 1) {
         int win = gl;
@@ -520,13 +532,24 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         if (FP64) {
             win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
         } else {
+            float4 f0{}, f1{}, f2{}, f3{};
+            if (LPR == 1) {
+                f0 = __ldg(blk + 1);
+                f1 = __ldg(blk + 2);
+                f2 = __ldg(blk + 3);
+                f3 = __ldg(blk + 4);
+            }
             const float rx = local_coord(R0h[0], R0l[0], Kh[0], Kl[0], th, tl, pmx);
             const float ry = local_coord(R0h[1], R0l[1], Kh[1], Kl[1], th, tl, pmy);
             const float rz = local_coord(R0h[2], R0l[2], Kh[2], Kl[2], th, tl, pmz);
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
             const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
+            const float n1m = hdr.w;  // the cell's bound on |n|_1
+            const float dden = __fmul_ru(kCDen, n1m);
+            const float dnum = __fmul_ru(n1m, __fmaf_ru(kCA, n1m, rr));
             Cand32 c;
-            exit32<LPR>(blk, cnt, pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
+            exit32<LPR>(blk, cnt, f0, f1, f2, f3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl,
+                        gbase, c);
             // the wall ahead is one more candidate: s_w = t_max - t
             float sw, swl;
             two_sum(tmh, -th, sw, swl);
@@ -547,7 +570,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 upper = __fadd_ru(sw, Ew);
             } else {
                 // the winner's terms again (same operations, same values)
-                w1 = plane32(__ldg(blk + c.p1), pmx, pmy, pmz, rx, ry, rz, rr, Kh[0], Kh[1], Kh[2]);
+                w1 = plane32(__ldg(blk + c.p1), pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
                 const float den_lo = __fsub_rd(w1.den, w1.dden);
                 const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
                 upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : __int_as_float(0x7f800000);
