@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -84,6 +85,7 @@ struct vgrid {
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
     float4 *d_cells = nullptr;
+    float4 *d_rel = nullptr;
     int32_t *d_perm = nullptr;
     int32_t *d_blk_off = nullptr;
     float4 *d_blk_rec = nullptr;
@@ -155,7 +157,7 @@ static void free_events(vgrid_t *g) {
 static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
-    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_perm, g->d_blk_off, g->d_blk_rec,
+    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_rel, g->d_perm, g->d_blk_off, g->d_blk_rec,
                     g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan, g->d_entry};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -237,55 +239,91 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
     }
 
-    // cell blocks: header (caller id, count, rho = 1, N1max), then one record
-    // per neighbour (site of the neighbour, its block offset) or wall.
-    // N1max bounds |p_j - p_i|_1 over the cell's neighbours from above (with
-    // room for the float32 rounding of the differences on the device).
-    std::vector<int64_t> boffs(M + 1, 0);
-    for (int64_t i = 0; i < M; i++) boffs[i + 1] = boffs[i] + 1 + (g->cells.off[i + 1] - g->cells.off[i]);
-    if (boffs[M] + 8 >= ((int64_t)1 << 31)) {
+    // absolute cell blocks (offsets A): header (caller id, count, rho = 1,
+    // F), then one record per neighbour (site of the neighbour, its A) or
+    // wall. Relative cell blocks (offsets F, even): (site, record count),
+    // (caller id, rho = 1, N1max, A), then one record per cell neighbour
+    // (fl(p_j - p_i) in float32, its F), NaN-padded to a multiple of four
+    // records (at least four). N1max bounds |fl(p_j - p_i)|_1 over the
+    // records from above.
+    std::vector<int64_t> boffs(M + 1, 0), foffs(M + 1, 0);
+    std::vector<int32_t> ncell(M, 0);
+    for (int64_t i = 0; i < M; i++) {
+        const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
+        for (int64_t q = b; q < e; q++) ncell[i] += g->cells.idx[q] >= 0;
+        boffs[i + 1] = boffs[i] + 1 + (e - b);
+        foffs[i + 1] = foffs[i] + 2 + std::max<int64_t>(4, (ncell[i] + 3) & ~(int64_t)3);
+    }
+    if (boffs[M] + 8 >= ((int64_t)1 << 31) || foffs[M] + 8 >= ((int64_t)1 << 31)) {
         delete g;
         return fail(VGRID_ERR_NOMEM, "cell blocks exceed 2^31 records");
     }
-    const int64_t nrec = boffs[M] + 8;  // room past the end for the last block's reads
-    std::vector<float> blocks(4 * nrec, 0.0f);
+    const int64_t nrec = boffs[M] + 8;   // room past the end for the last block's reads
+    const int64_t nrel = foffs[M] + 8;
+    std::vector<float> blocks(4 * nrec, 0.0f), rel(4 * nrel, 0.0f);
     std::vector<float> site4(4 * M);
     auto put_int = [](float *dst, int32_t v) { std::memcpy(dst, &v, 4); };
+    const float fnan = std::numeric_limits<float>::quiet_NaN();
     for (int64_t i = 0; i < M; i++) {
         const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
+        const float pi[3] = {(float)Si[3 * i + 0], (float)Si[3 * i + 1], (float)Si[3 * i + 2]};
         float *h = &blocks[4 * boffs[i]];
         put_int(h + 0, g->perm[i]);
         put_int(h + 1, (int32_t)(e - b));
         h[2] = 1.0f;
+        put_int(h + 3, (int32_t)foffs[i]);
+        float *f = &rel[4 * foffs[i]];
+        const int64_t c4 = foffs[i + 1] - foffs[i] - 2;
+        f[0] = pi[0];
+        f[1] = pi[1];
+        f[2] = pi[2];
+        put_int(f + 3, (int32_t)c4);
+        put_int(f + 4, g->perm[i]);
+        f[5] = 1.0f;
+        put_int(f + 7, (int32_t)boffs[i]);
         double n1max = 0.0;
-        for (int64_t q = b; q < e; q++) {
-            const int32_t j = g->cells.idx[q];
-            if (j < 0) continue;
-            double n1 = 0.0;
-            for (int c = 0; c < 3; c++) n1 += std::fabs(Si[3 * (int64_t)j + c] - Si[3 * i + c]);
-            n1max = std::max(n1max, n1);
-        }
-        float n1f = (float)(n1max * (1.0 + 1e-6));
-        if ((double)n1f < n1max * (1.0 + 1e-6)) n1f = std::nextafter(n1f, INFINITY);
-        h[3] = n1f;
+        int64_t k = 0;
         for (int64_t q = b; q < e; q++) {
             float *r = &blocks[4 * (boffs[i] + 1 + (q - b))];
             const int32_t j = g->cells.idx[q];
             if (j >= 0) {
-                r[0] = (float)Si[3 * (int64_t)j + 0];
-                r[1] = (float)Si[3 * (int64_t)j + 1];
-                r[2] = (float)Si[3 * (int64_t)j + 2];
+                float pj[3];
+                for (int c = 0; c < 3; c++) pj[c] = (float)Si[3 * (int64_t)j + c];
+                r[0] = pj[0];
+                r[1] = pj[1];
+                r[2] = pj[2];
                 put_int(r + 3, (int32_t)boffs[j]);
+                float *rr = &f[4 * (2 + k++)];
+                double n1 = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    volatile float d = pj[c] - pi[c];  // one float32 rounding, as on the device
+                    rr[c] = d;
+                    n1 += std::fabs((double)rr[c]);
+                }
+                put_int(rr + 3, (int32_t)foffs[j]);
+                n1max = std::max(n1max, n1);
             } else {
                 put_int(r + 3, j);
             }
         }
-        site4[4 * i + 0] = (float)Si[3 * i + 0];
-        site4[4 * i + 1] = (float)Si[3 * i + 1];
-        site4[4 * i + 2] = (float)Si[3 * i + 2];
-        put_int(&site4[4 * i + 3], (int32_t)boffs[i]);
+        for (; k < c4; k++) {
+            float *rr = &f[4 * (2 + k)];
+            rr[0] = rr[1] = rr[2] = fnan;
+            put_int(rr + 3, -8);
+        }
+        float n1f = (float)(n1max * (1.0 + 1e-6));
+        if ((double)n1f < n1max * (1.0 + 1e-6)) n1f = std::nextafter(n1f, INFINITY);
+        f[6] = n1f;
+        site4[4 * i + 0] = pi[0];
+        site4[4 * i + 1] = pi[1];
+        site4[4 * i + 2] = pi[2];
+        put_int(&site4[4 * i + 3], (int32_t)foffs[i]);
     }
     for (int64_t r = boffs[M]; r < nrec; r++) put_int(&blocks[4 * r + 3], -8);
+    for (int64_t r = foffs[M]; r < nrel; r++) {
+        rel[4 * r] = rel[4 * r + 1] = rel[4 * r + 2] = fnan;
+        put_int(&rel[4 * r + 3], -8);
+    }
     std::vector<int32_t> boff(g->blocks.off.size());
     for (size_t i = 0; i < boff.size(); i++) boff[i] = (int32_t)g->blocks.off[i];
 
@@ -314,6 +352,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     }
     VG_ALLOC(g->d_site, M);
     VG_ALLOC(g->d_cells, nrec);
+    VG_ALLOC(g->d_rel, nrel);
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
     VG_ALLOC(g->d_blk_rec, g->blocks.idx.size());
@@ -325,6 +364,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(g->d_site, site4.data(), sizeof(float) * 4 * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, blocks.data(), sizeof(float) * 4 * nrec, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rel, rel.data(), sizeof(float) * 4 * nrel, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !g->blocks.idx.empty()) {
@@ -342,6 +382,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     GridDev &hd = g->hd;
     hd.site = g->d_site;
     hd.cells = g->d_cells;
+    hd.rel = g->d_rel;
     hd.perm = g->d_perm;
     hd.blk_off = g->d_blk_off;
     hd.blk_rec = g->d_blk_rec;
@@ -438,7 +479,7 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
     if (!std::isfinite(kappa)) return fail(VGRID_ERR_ARG, "kappa is not finite");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
-    VG_CUDA(vg::launch_permute_density(rho, g->d_perm, g->d_site, g->M, g->d_cells, s));
+    VG_CUDA(vg::launch_permute_density(rho, g->d_perm, g->d_site, g->M, g->d_cells, g->d_rel, s));
     g->hd.kappa = kappa;
     VG_CUDA(vg::launch_put_grid(g->d_desc, g->hd, s));
     return VGRID_OK;

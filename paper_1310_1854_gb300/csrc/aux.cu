@@ -111,21 +111,24 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
     return cudaGetLastError();
 }
 
-// rho (caller order) into the headers of the cell blocks
+// rho (caller order) into the headers of both forms of the cell blocks
 __global__ void permute_density_kernel(const float *__restrict__ rho_caller, const int32_t *__restrict__ perm,
-                                       const float4 *__restrict__ site, int64_t M, float4 *cells) {
+                                       const float4 *__restrict__ site, int64_t M, float4 *cells, float4 *rel) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int b = __float_as_int(__ldg(&site[i]).w);
-        cells[b].z = __ldg(&rho_caller[__ldg(&perm[i])]);
+        const int f = __float_as_int(__ldg(&site[i]).w);
+        const float v = __ldg(&rho_caller[__ldg(&perm[i])]);
+        float4 *h1 = rel + f + 1;
+        h1->y = v;
+        cells[__float_as_int(h1->w)].z = v;
     }
 }
 
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,
-                                   float4 *cells, cudaStream_t s) {
+                                   float4 *cells, float4 *rel, cudaStream_t s) {
     if (M <= 0) return cudaSuccess;
     int64_t blocks = (M + 255) / 256;
     if (blocks > 65535) blocks = 65535;
-    permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, site, M, cells);
+    permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, site, M, cells, rel);
     return cudaGetLastError();
 }
 

@@ -43,13 +43,18 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 // stored in an array for batched launches. Cells are in the library's
 // internal (Morton) order.
 //
-// cells    cell blocks, float4: cell i starts at block offset B_i with a
-//          header (bits of the caller's id, bits of the neighbour count c,
-//          rho, N1max = an upper bound of |p_j - p_i|_1 over the neighbours)
-//          followed by c records (x, y, z of the neighbour's site, bits of the
-//          neighbour's block offset B_j, or of a wall id -1..-6). Each cell
-//          has at least four records.
-// site[i]  float4 (x, y, z, bits of B_i): positions for C(r) and ray starts.
+// cells    absolute cell blocks (float64 form and rechecks), float4: cell i
+//          starts at A_i with a header (bits of the caller's id, bits of the
+//          neighbour count c, rho, bits of F_i) followed by c records (x, y, z
+//          of the neighbour's site, bits of the neighbour's offset A_j, or of
+//          a wall id -1..-6).
+// rel      relative cell blocks (float32 form), float4: cell i starts at F_i
+//          (even) with (x, y, z of p_i, bits of the record count c4) and
+//          (bits of the caller's id, rho, N1max, bits of A_i), followed by c4
+//          records: (fl(p_j - p_i) as float32, bits of F_j) for every cell
+//          neighbour j, then NaN records up to c4 = max(4, multiple of 4).
+//          N1max bounds |fl(p_j - p_i)|_1 over the records from above.
+// site[i]  float4 (x, y, z, bits of F_i): positions for C(r) and ray starts.
 // perm[i]  caller's id of internal cell i.
 // blk_off, blk_rec  block lists of Sect. 2.3: for every block, records
 //          (x, y, z of a site, bits of its internal id) of the cells whose
@@ -58,6 +63,7 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 struct GridDev {
     const float4 *site;
     const float4 *cells;
+    const float4 *rel;
     const int32_t *perm;
     const int32_t *blk_off;
     const float4 *blk_rec;

@@ -58,7 +58,7 @@ enum { PREP_CELL32 = 0, PREP_FP32 = 1, PREP_FP64 = 2, PREP_CELL64 = 3 };
 cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,
                           int32_t *out_caller, int sms, cudaStream_t s);
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,
-                                   float4 *cells, cudaStream_t s);
+                                   float4 *cells, float4 *rel, cudaStream_t s);
 // exclusive scan of counts[0..n-1] (int64) into off[0..n]; tmp holds
 // scan_tmp_elems(n) int64 values
 int64_t scan_tmp_elems(int64_t n);

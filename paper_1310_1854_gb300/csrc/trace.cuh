@@ -7,11 +7,16 @@
 // lanes idle. Inside a crossing the group's lanes stride over the current
 // cell's block and reduce the exit with shuffles.
 //
-// Cell blocks: cell i owns a contiguous run of float4 starting at B_i: a
-// header (caller's id, neighbour count, rho, internal id) and one record per
-// neighbour (x, y, z of the neighbour's site, and the neighbour's block
-// offset B_j, or a wall id -1..-6). A crossing therefore reads one contiguous
-// block; the winner's record already holds the next cell's site and block.
+// Cell blocks, in two forms; each crossing reads one contiguous block.
+//  * absolute (float64 form, rechecks): cell i owns a run of float4 at A_i:
+//    a header (caller's id, neighbour count, rho, F_i) and one record per
+//    neighbour (x, y, z of the neighbour's site, and its offset A_j, or a
+//    wall id -1..-6); the winner's record holds the next site and block.
+//  * relative (float32 form): cell i owns a run at F_i: (x, y, z of p_i,
+//    record count), (caller's id, rho, N1max, A_i), then one record per cell
+//    neighbour (n~ = fl(p_j - p_i), the neighbour's offset F_j), padded with
+//    NaN records to a multiple of four. Walls are not records there: the
+//    wall ahead is one candidate from the ray's start record.
 //
 // Two arithmetic forms of the exit search (Sect. 2.2, steps 1-3, Eq. 1-5):
 //  * float64: Eq. 4 and Eq. 5 evaluated as written, in the same operation
@@ -100,8 +105,9 @@ __device__ __forceinline__ float local_coord(float R0h, float R0l, float Kh, flo
 // ---------------------------------------------------------------------------
 
 struct Hot {
-    const float4 *__restrict__ cells;  // cell blocks
-    const float4 *__restrict__ site;   // (x, y, z, bits of block offset) per internal cell
+    const float4 *__restrict__ cells;  // absolute cell blocks (float64 form, rechecks)
+    const float4 *__restrict__ rel;    // relative cell blocks (float32 form)
+    const float4 *__restrict__ site;   // (x, y, z, bits of the relative block offset) per internal cell
 };
 
 __device__ __forceinline__ int rec_w(float4 q) { return __float_as_int(q.w); }
@@ -267,10 +273,12 @@ struct Cand32 {
     int p1;              // record position (1-based) of the smallest, 0 if none
 };
 
-// Terms of the bisector of the current site (origin of the local frame) and
-// site q, with their rounding-error bounds (u = 2^-24, n~ = fl(q - p),
-// r~ within 2u|r| + e_r, N = the cell's bound on |n|_1 from its header):
-//   |den~ - n.k|  <= dden = 6u N                    (two roundings of n, three of the dot)
+// Terms of the bisector of the current site p (origin of the local frame)
+// and a neighbour's site q, from the record's n~ = fl(q - p) (rounded once,
+// on the host, exactly as a float32 subtraction here would), with their
+// rounding-error bounds (u = 2^-24, r~ within 2u|r| + e_r, N = the cell's
+// bound on |n~|_1 from its header):
+//   |den~ - n.k|  <= dden = 6u N                    (the rounding of n, three of the dot, K)
 //   |num~ - n.w|  <= dnum = N (4u N + 8u |r~|_1 + 2 e_r),   w = n/2 - r
 // dden and dnum are the same for every plane of the cell (computed once per
 // crossing from N).
@@ -278,10 +286,10 @@ struct Plane32 {
     float num, den, dnum, dden;
 };
 
-__device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float pmz, float rx, float ry, float rz,
-                                           float dnum, float dden, float Kx, float Ky, float Kz) {
+__device__ __forceinline__ Plane32 plane32(float4 q, float rx, float ry, float rz, float dnum, float dden, float Kx,
+                                           float Ky, float Kz) {
     Plane32 p;
-    const float nx = __fsub_rn(q.x, pmx), ny = __fsub_rn(q.y, pmy), nz = __fsub_rn(q.z, pmz);
+    const float nx = q.x, ny = q.y, nz = q.z;
     p.den = __fmaf_rn(nz, Kz, __fmaf_rn(ny, Ky, __fmul_rn(nx, Kx)));
     p.dden = dden;
     const float wx = __fmaf_rn(0.5f, nx, -rx), wy = __fmaf_rn(0.5f, ny, -ry), wz = __fmaf_rn(0.5f, nz, -rz);
@@ -292,56 +300,64 @@ __device__ __forceinline__ Plane32 plane32(float4 q, float pmx, float pmy, float
 
 // Planes with den~ <= -dden face away for certain (R2); the others get the
 // lower bound max(num~ - dnum, 0) / (den~ + dden) on s (Eq. 4), rounded down.
-// Branch-free: in a warp some lane nearly always has a plane facing ahead,
-// so skipping the numerator for planes facing away (the sign shortcut of
-// Sect. 2.2) would only add divergence; a masked result costs nothing more.
-// Walls (handled by the wall candidate t_max - t) and positions past the
-// count are masked the same way.
-__device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float pmx, float pmy, float pmz, float rx,
-                                           float ry, float rz, float dnum, float dden, float Kx, float Ky, float Kz,
-                                           Cand32 &c) {
-    const Plane32 p = plane32(q, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz);
+// den~ + dden rounded up is > 0 exactly when den~ > -dden, so that one test
+// masks the planes facing away, and the NaN records that pad a block (for
+// which it is false) too. Branch-free: in a warp some lane nearly always has
+// a plane facing ahead, so skipping the numerator for planes facing away (the
+// sign shortcut of Sect. 2.2) would only add divergence; a masked result
+// costs nothing more. Positions past the count (several lanes per ray) are
+// masked by `valid`.
+__device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float rx, float ry, float rz, float dnum,
+                                           float dden, float Kx, float Ky, float Kz, Cand32 &c) {
+    const Plane32 p = plane32(q, rx, ry, rz, dnum, dden, Kx, Ky, Kz);
     const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
     float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
-    lower = (valid && rec_w(q) >= 0 && p.den > -p.dden) ? lower : __int_as_float(0x7f800000);
+    lower = (valid && den_hi > 0.0f) ? lower : __int_as_float(0x7f800000);
     const bool b = lower < c.L1;
     c.L2 = b ? c.L1 : fminf(c.L2, lower);
     c.p1 = b ? pos : c.p1;
     c.L1 = fminf(c.L1, lower);
 }
 
-// Records blk[1..cnt]; lane gl of the group takes records gl+1, gl+1+LPR, ...
-// four at a time. Every cell has at least four faces, so the first four
-// records exist; with one lane per ray the caller loads them (f0..f3)
-// together with the header, so they do not wait for the count.
+// Records recs[1..cnt] (cnt a multiple of four, at least four); lane gl of
+// the group takes records gl+1, gl+1+LPR, ... four at a time. With one lane
+// per ray the caller loads the first four (f0..f3) together with the header,
+// so they do not wait for the count, and no position is ever past the count.
 template <int LPR>
-__device__ __forceinline__ void exit32(const float4 *blk, int cnt, float4 f0, float4 f1, float4 f2, float4 f3,
-                                       float pmx, float pmy, float pmz, float rx, float ry, float rz, float dnum,
-                                       float dden, float Kx, float Ky, float Kz, unsigned gmask, int gl, int gbase,
-                                       Cand32 &c) {
+__device__ __forceinline__ void exit32(const float4 *recs, int cnt, float4 f0, float4 f1, float4 f2, float4 f3,
+                                       float rx, float ry, float rz, float dnum, float dden, float Kx, float Ky,
+                                       float Kz, unsigned gmask, int gl, int gbase, Cand32 &c) {
     c.L1 = __int_as_float(0x7f800000);
     c.L2 = c.L1;
     c.p1 = 0;
-    int p = 1 + gl;
     if (LPR == 1) {
-        consider32(1, true, f0, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(2, true, f1, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(3, true, f2, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(4, true, f3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        p = 5;
-    }
-    for (; p <= cnt; p += 4 * LPR) {
-        const int p0 = p, p1 = p + LPR, p2 = p + 2 * LPR, p3 = p + 3 * LPR;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, __int_as_float(-8));
-        const float4 q0 = __ldg(blk + p0);
-        const float4 q1 = p1 <= cnt ? __ldg(blk + p1) : z4;
-        const float4 q2 = p2 <= cnt ? __ldg(blk + p2) : z4;
-        const float4 q3 = p3 <= cnt ? __ldg(blk + p3) : z4;
-        consider32(p0, true, q0, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(p1, p1 <= cnt, q1, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(p2, p2 <= cnt, q2, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(p3, p3 <= cnt, q3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(1, true, f0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(2, true, f1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(3, true, f2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32(4, true, f3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        for (int p = 5; p <= cnt; p += 4) {
+            const float4 q0 = __ldg(recs + p), q1 = __ldg(recs + p + 1), q2 = __ldg(recs + p + 2),
+                         q3 = __ldg(recs + p + 3);
+            consider32(p, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p + 1, true, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p + 2, true, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p + 3, true, q3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        }
+    } else {
+        const float nan = __int_as_float(0x7fc00000);
+        const float4 pad = make_float4(nan, nan, nan, __int_as_float(-8));
+        for (int p = 1 + gl; p <= cnt; p += 4 * LPR) {
+            const int p0 = p, p1 = p + LPR, p2 = p + 2 * LPR, p3 = p + 3 * LPR;
+            const float4 q0 = __ldg(recs + p0);
+            const float4 q1 = p1 <= cnt ? __ldg(recs + p1) : pad;
+            const float4 q2 = p2 <= cnt ? __ldg(recs + p2) : pad;
+            const float4 q3 = p3 <= cnt ? __ldg(recs + p3) : pad;
+            consider32(p0, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p1, p1 <= cnt, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p2, p2 <= cnt, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32(p3, p3 <= cnt, q3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        }
     }
     if (LPR > 1) {
         int win = gl;
@@ -397,7 +413,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     int set = 0;
     int64_t li = 0;         // index within the set
     const GridDev *gp = a.grids;  // device copy of the descriptor (cold paths)
-    Hot h{a.g1.cells, a.g1.site};
+    Hot h{a.g1.cells, a.g1.rel, a.g1.site};
     float kappa = a.g1.kappa;
     int max_steps = (int)min(a.g1.max_steps, (int64_t)0x7fffffff);
     // float64 form: current point and direction
@@ -442,6 +458,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 li = ray - rs->first;
                 gp = a.grids + rs->grid;
                 h.cells = gp->cells;
+                h.rel = gp->rel;
                 h.site = gp->site;
                 kappa = gp->kappa;
                 max_steps = (int)min(gp->max_steps, (int64_t)0x7fffffff);
@@ -495,6 +512,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 pmy = q.y;
                 pmz = q.z;
                 B = rec_w(q);
+                if (FP64) B = rec_w(__ldg(h.rel + B + 1));  // absolute block of the cell
             }
             if (status != RAY_OK) {
                 if (gl == 0) {
@@ -520,36 +538,53 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         if (ray < 0) continue;
 
         // ---------------- one exit decision ----------------
-        const float4 *blk = h.cells + B;
+        // float64 form: absolute block A (header: caller, count, rho, F);
+        // float32 form: relative block F (site and count, then caller, rho,
+        // N1max, A).
+        const float4 *blk = FP64 ? h.cells + B : h.rel + B;
         const float4 hdr = __ldg(blk);
-        const int cnt = hdr_count(hdr);
+        const float4 hdr1 = FP64 ? hdr : __ldg(blk + 1);
+        const int cnt = FP64 ? hdr_count(hdr) : __float_as_int(hdr.w);
+        const int caller = hdr_caller(hdr1);
+        const float rho = FP64 ? hdr.z : hdr1.y;
         bool ended = false;
         double s64 = 0.0;      // float64 length (float64 form or recheck)
         bool from64 = FP64;
         float len = 0.f;
-        int win = 0;           // winning record position, 0 none
-        bool to_wall = false;
+        bool found = false;    // an exit was found
+        bool to_wall = false;  // ... and it is a wall
+        int nextB = 0;         // block offset of the next cell (same form as B)
+        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);  // float64 form: the winner's record
         if (FP64) {
-            win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
+            const int win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
+            if (win > 0) {
+                qn = __ldg(blk + win);
+                found = true;
+                to_wall = rec_w(qn) < 0;
+                nextB = rec_w(qn);
+            }
         } else {
+            const float4 *recs = blk + 1;  // records recs[1..cnt]
             float4 f0{}, f1{}, f2{}, f3{};
             if (LPR == 1) {
-                f0 = __ldg(blk + 1);
-                f1 = __ldg(blk + 2);
-                f2 = __ldg(blk + 3);
-                f3 = __ldg(blk + 4);
+                f0 = __ldg(recs + 1);
+                f1 = __ldg(recs + 2);
+                f2 = __ldg(recs + 3);
+                f3 = __ldg(recs + 4);
             }
+            pmx = hdr.x;
+            pmy = hdr.y;
+            pmz = hdr.z;
             const float rx = local_coord(R0h[0], R0l[0], Kh[0], Kl[0], th, tl, pmx);
             const float ry = local_coord(R0h[1], R0l[1], Kh[1], Kl[1], th, tl, pmy);
             const float rz = local_coord(R0h[2], R0l[2], Kh[2], Kl[2], th, tl, pmz);
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
             const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
-            const float n1m = hdr.w;  // the cell's bound on |n|_1
+            const float n1m = hdr1.z;  // the cell's bound on |n|_1
             const float dden = __fmul_ru(kCDen, n1m);
             const float dnum = __fmul_ru(n1m, __fmaf_ru(kCA, n1m, rr));
             Cand32 c;
-            exit32<LPR>(blk, cnt, f0, f1, f2, f3, pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl,
-                        gbase, c);
+            exit32<LPR>(recs, cnt, f0, f1, f2, f3, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
             // the wall ahead is one more candidate: s_w = t_max - t
             float sw, swl;
             two_sum(tmh, -th, sw, swl);
@@ -564,29 +599,32 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             } else if (lw < c.L2) {
                 c.L2 = lw;
             }
-            float upper;
+            float upper = __int_as_float(0x7f800000);
             Plane32 w1{0.f, 1.f, 0.f, 0.f};
+            float4 qw = make_float4(0.f, 0.f, 0.f, 0.f);
             if (wall_wins) {
                 upper = __fadd_ru(sw, Ew);
-            } else {
+            } else if (c.p1 > 0) {
                 // the winner's terms again (same operations, same values)
-                w1 = plane32(__ldg(blk + c.p1), pmx, pmy, pmz, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
+                qw = __ldg(recs + c.p1);
+                w1 = plane32(qw, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
                 const float den_lo = __fsub_rd(w1.den, w1.dden);
                 const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
-                upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : __int_as_float(0x7f800000);
+                upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : upper;
             }
             if (upper < c.L2) {
+                found = true;
                 if (wall_wins) {
                     len = fmaxf(sw, 0.0f);
                     to_wall = true;
-                    win = -1;
                 } else {
                     // den > dden > 0 here; 2-ulp division (the length only feeds tau and t)
                     len = __fdividef(fmaxf(w1.num, 0.0f), w1.den);
-                    win = c.p1;
+                    nextB = rec_w(qw);
                 }
             } else {
-                // float64 recheck of this crossing from r = r0 + t k
+                // float64 recheck of this crossing from r = r0 + t k, on the
+                // absolute block of the cell
                 if (gl == 0) VG_STAT(S_RE, 1);
                 const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
                 const double *o = rs->origin + 3 * li;
@@ -597,21 +635,25 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     kd[cc] = __ldg(d + cc);
                     rp[cc] = __fma_rn(t, kd[cc], __ldg(o + cc));
                 }
-                win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask, gl, s64);
+                const float4 *ablk = h.cells + rec_w(hdr1);
+                const int acnt = hdr_count(__ldg(ablk));
+                const int win = exit64<LPR>(h, gp, ablk, acnt, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask,
+                                            gl, s64);
+                if (win > 0) {
+                    const float4 qa = __ldg(ablk + win);
+                    found = true;
+                    to_wall = rec_w(qa) < 0;
+                    if (!to_wall) nextB = rec_w(__ldg(h.cells + rec_w(qa)));  // F of the next cell
+                }
                 len = __double2float_rn(s64);
                 from64 = true;
             }
         }
         bool interacted = false;  // interaction mode: the package interacts in this cell
-        float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (win > 0) {
-            qn = __ldg(blk + win);
-            to_wall = rec_w(qn) < 0;
-        }
 
         steps++;
         bool relocate = false;
-        if (win == 0) {
+        if (!found) {
             relocate = true;  // no exit found (Sect. 2.2): nudge over epsilon and locate again
         } else {
             const bool positive = FP64 ? (s64 > 0.0) : (len > 0.0f);
@@ -619,39 +661,39 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 if (MODE == MODE_FILL && gl == 0) {
                     const int64_t at = seg_base + nseg;
                     if (at < a.seg_cap) {  // the count pass sized the buffer; never write past it
-                        a.seg_cell[at] = hdr_caller(hdr);
+                        a.seg_cell[at] = caller;
                         if (FP64) ((double *)a.seg_len)[at] = s64;
                         else ((float *)a.seg_len)[at] = len;
                     }
                 }
-                if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[hdr_caller(hdr)], dLr * kappa * len);
+                if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[caller], dLr * kappa * len);
                 if (MODE == MODE_INTERACT) {
                     // the package is attenuated by exp(-dtau) in this cell; it
                     // interacts here if the running tau reaches tau_int
-                    const float krho = __fmul_rn(kappa, hdr.z);
+                    const float krho = __fmul_rn(kappa, rho);
                     const float dtau = __fmul_rn(krho, len);
                     const float left = __fsub_rn(tint, tau32);
                     if (left <= __fsub_rn(dtau, tauc)) {
                         const float part = fmaxf(left, 0.0f);
                         if (gl == 0) {
-                            if (a.absorbed) atomicAdd(&a.absorbed[hdr_caller(hdr)], wgt * att * -expm1f(-part));
-                            a.int_cell[ray] = hdr_caller(hdr);
+                            if (a.absorbed) atomicAdd(&a.absorbed[caller], wgt * att * -expm1f(-part));
+                            a.int_cell[ray] = caller;
                             const float ds = krho > 0.0f ? fminf(__fdividef(part, krho), len) : 0.0f;
                             a.int_s[ray] = __fadd_rn(__fadd_rn(th, tl), ds);
                         }
                         interacted = true;
                     } else {
                         if (gl == 0 && a.absorbed)
-                            atomicAdd(&a.absorbed[hdr_caller(hdr)], wgt * att * -expm1f(-dtau));
+                            atomicAdd(&a.absorbed[caller], wgt * att * -expm1f(-dtau));
                         att = __fmul_rn(att, __expf(-dtau));
                     }
                 }
                 nseg++;
                 if (FP64) {
-                    tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)hdr.z), s64));
+                    tau64 = __dadd_rn(tau64, __dmul_rn(__dmul_rn((double)kappa, (double)rho), s64));
                 } else {
                     // Kahan-compensated sum of kappa rho l
-                    const float y = __fsub_rn(__fmul_rn(__fmul_rn(kappa, hdr.z), len), tauc);
+                    const float y = __fsub_rn(__fmul_rn(__fmul_rn(kappa, rho), len), tauc);
                     const float tt = __fadd_rn(tau32, y);
                     tauc = __fsub_rn(__fsub_rn(tt, tau32), y);
                     tau32 = tt;
@@ -673,10 +715,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             if (to_wall) {
                 ended = true;
             } else {
-                pmx = qn.x;
-                pmy = qn.y;
-                pmz = qn.z;
-                B = rec_w(qn);
+                if (FP64) {  // the float32 form reads the site from the next block
+                    pmx = qn.x;
+                    pmy = qn.y;
+                    pmz = qn.z;
+                }
+                B = nextB;
                 relocate = zrun > kZeroRunMax;
             }
         }
@@ -702,6 +746,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 pmy = q.y;
                 pmz = q.z;
                 B = rec_w(q);
+                if (FP64) B = rec_w(__ldg(h.rel + B + 1));  // absolute block of the cell
             }
         }
         if (!ended && steps >= max_steps) {
