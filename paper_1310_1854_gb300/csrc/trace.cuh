@@ -111,6 +111,15 @@ struct Hot {
 };
 
 __device__ __forceinline__ int rec_w(float4 q) { return __float_as_int(q.w); }
+
+// Two consecutive float4 in one 256-bit load (p 32-byte aligned). The lanes of
+// a warp read unrelated blocks, so every lane touches its own 32-byte sector:
+// one request per sector instead of one per half sector.
+__device__ __forceinline__ void ldg_pair(const float4 *p, float4 &a, float4 &b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
 __device__ __forceinline__ int hdr_caller(float4 h) { return __float_as_int(h.x); }
 __device__ __forceinline__ int hdr_count(float4 h) { return __float_as_int(h.y); }
 
@@ -337,8 +346,9 @@ __device__ __forceinline__ void exit32(const float4 *recs, int cnt, float4 f0, f
         consider32(3, true, f2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
         consider32(4, true, f3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
         for (int p = 5; p <= cnt; p += 4) {
-            const float4 q0 = __ldg(recs + p), q1 = __ldg(recs + p + 1), q2 = __ldg(recs + p + 2),
-                         q3 = __ldg(recs + p + 3);
+            float4 q0, q1, q2, q3;
+            ldg_pair(recs + p, q0, q1);
+            ldg_pair(recs + p + 2, q2, q3);
             consider32(p, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
             consider32(p + 1, true, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
             consider32(p + 2, true, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
@@ -542,8 +552,13 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         // float32 form: relative block F (site and count, then caller, rho,
         // N1max, A).
         const float4 *blk = FP64 ? h.cells + B : h.rel + B;
-        const float4 hdr = __ldg(blk);
-        const float4 hdr1 = FP64 ? hdr : __ldg(blk + 1);
+        float4 hdr, hdr1;
+        if (FP64) {
+            hdr = __ldg(blk);
+            hdr1 = hdr;
+        } else {
+            ldg_pair(blk, hdr, hdr1);  // relative blocks start on 32-byte boundaries
+        }
         const int cnt = FP64 ? hdr_count(hdr) : __float_as_int(hdr.w);
         const int caller = hdr_caller(hdr1);
         const float rho = FP64 ? hdr.z : hdr1.y;
@@ -567,10 +582,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             const float4 *recs = blk + 1;  // records recs[1..cnt]
             float4 f0{}, f1{}, f2{}, f3{};
             if (LPR == 1) {
-                f0 = __ldg(recs + 1);
-                f1 = __ldg(recs + 2);
-                f2 = __ldg(recs + 3);
-                f3 = __ldg(recs + 4);
+                ldg_pair(recs + 1, f0, f1);
+                ldg_pair(recs + 3, f2, f3);
             }
             pmx = hdr.x;
             pmy = hdr.y;
