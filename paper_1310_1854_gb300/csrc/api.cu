@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "fsplit.h"
 #include "internal.h"
 #include "kernels.h"
 #include "vgrid.h"
@@ -234,7 +235,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         return fail(o.gpu_build ? VGRID_ERR_CUDA : VGRID_ERR_BUILD, err);
     }
     vg::build_blocks(bbox, g->cells.bbox, M, o.blocks_per_site, g->blocks);
-    if ((int64_t)g->blocks.idx.size() >= ((int64_t)1 << 31)) {
+    if ((int64_t)(g->blocks.idx.size() + g->blocks.off.size()) + 2 >= ((int64_t)1 << 31)) {  // with the padding
         delete g;
         return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
     }
@@ -324,8 +325,15 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         rel[4 * r] = rel[4 * r + 1] = rel[4 * r + 2] = fnan;
         put_int(&rel[4 * r + 3], -8);
     }
-    std::vector<int32_t> boff(g->blocks.off.size());
-    for (size_t i = 0; i < boff.size(); i++) boff[i] = (int32_t)g->blocks.off[i];
+    // block lists on the device: each padded to an even length with NaN
+    // records (id -1), so every list starts on a 32-byte boundary and is read
+    // in 256-bit pairs
+    const size_t nblk = g->blocks.off.size() - 1;
+    std::vector<int32_t> boff(nblk + 1, 0);
+    for (size_t i = 0; i < nblk; i++) {
+        const int64_t len = g->blocks.off[i + 1] - g->blocks.off[i];
+        boff[i + 1] = boff[i] + (int32_t)((len + 1) & ~(int64_t)1);
+    }
 
     if (o.host_only) {
         g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -355,7 +363,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     VG_ALLOC(g->d_rel, nrel);
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
-    VG_ALLOC(g->d_blk_rec, g->blocks.idx.size());
+    VG_ALLOC(g->d_blk_rec, (size_t)boff[nblk] + 2);
     VG_ALLOC(g->d_desc, 1);
     VG_ALLOC(g->d_queue, 1);
     VG_ALLOC(g->d_stats, 1);
@@ -367,14 +375,22 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (e == cudaSuccess) e = cudaMemcpy(g->d_rel, rel.data(), sizeof(float) * 4 * nrel, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !g->blocks.idx.empty()) {
-        std::vector<float> brec(4 * g->blocks.idx.size());
-        for (size_t q = 0; q < g->blocks.idx.size(); q++) {
-            const int32_t c = g->blocks.idx[q];
-            brec[4 * q + 0] = (float)Si[3 * (int64_t)c + 0];
-            brec[4 * q + 1] = (float)Si[3 * (int64_t)c + 1];
-            brec[4 * q + 2] = (float)Si[3 * (int64_t)c + 2];
-            put_int(&brec[4 * q + 3], c);
+    if (e == cudaSuccess) {
+        const float fnan = std::numeric_limits<float>::quiet_NaN();
+        std::vector<float> brec(4 * ((size_t)boff[nblk] + 2));
+        for (size_t q = 0; q < brec.size() / 4; q++) {
+            brec[4 * q + 0] = brec[4 * q + 1] = brec[4 * q + 2] = fnan;
+            put_int(&brec[4 * q + 3], -1);
+        }
+        for (size_t b = 0; b < nblk; b++) {
+            for (int64_t q = g->blocks.off[b]; q < g->blocks.off[b + 1]; q++) {
+                const int32_t c = g->blocks.idx[q];
+                float *r = &brec[4 * ((size_t)boff[b] + (size_t)(q - g->blocks.off[b]))];
+                r[0] = (float)Si[3 * (int64_t)c + 0];
+                r[1] = (float)Si[3 * (int64_t)c + 1];
+                r[2] = (float)Si[3 * (int64_t)c + 2];
+                put_int(r + 3, c);
+            }
         }
         e = cudaMemcpy(g->d_blk_rec, brec.data(), sizeof(float) * brec.size(), cudaMemcpyHostToDevice);
     }
@@ -392,6 +408,11 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         hd.hi[c] = bbox[3 + c];
         hd.bdim[c] = g->blocks.dim[c];
         hd.bscale[c] = (double)g->blocks.dim[c] / (bbox[3 + c] - bbox[c]);
+        hd.lokey[c] = vg::dkey(bbox[c]);
+        hd.hikey[c] = vg::dkey(bbox[3 + c]);
+        hd.flo_hi[c] = (float)bbox[c];
+        hd.flo_lo[c] = (float)(bbox[c] - (double)hd.flo_hi[c]);
+        hd.fbscale[c] = (float)hd.bscale[c];
         dmax = std::max(dmax, std::max(std::fabs(bbox[c]), std::fabs(bbox[3 + c])));
     }
     const double dx = bbox[3] - bbox[0], dy = bbox[4] - bbox[1], dz = bbox[5] - bbox[2];

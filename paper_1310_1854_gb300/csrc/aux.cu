@@ -42,9 +42,9 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         const int64_t li = w - rs.first;
         const GridDev *gp = grids + rs.grid;
         const double *o = rs.origin + 3 * li;
-        const double r0[3] = {__ldg(o), __ldg(o + 1), __ldg(o + 2)};
+        const LocPt P = loc_point(__ldg(o), __ldg(o + 1), __ldg(o + 2));
         RayPrep *out = rs.start + li;
-        int m = locate_point(gp, r0[0], r0[1], r0[2], prep == PREP_CELL32 || prep == PREP_FP32, nullptr);
+        int m = locate_point<true>(gp, P, prep == PREP_CELL32 || prep == PREP_FP32, nullptr);
         if (out_caller) out_caller[w] = m >= 0 ? __ldg(&gp->perm[m]) : -1;
         if (prep == PREP_CELL32 || prep == PREP_CELL64) {
             out->cell = m;
@@ -52,28 +52,44 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         }
         const double *d = rs.dir + 3 * li;
         const double k[3] = {__ldg(d), __ldg(d + 1), __ldg(d + 2)};
-        const double kk = __dadd_rn(__dadd_rn(__dmul_rn(k[0], k[0]), __dmul_rn(k[1], k[1])), __dmul_rn(k[2], k[2]));
-        if (!(fabs(kk - 1.0) <= 2.000001e-6)) m = -2;
+        RayPrep p;
+        for (int c = 0; c < 3; c++) {
+            p.r0_hi[c] = P.h[c];
+            p.r0_lo[c] = P.l[c];
+            split_pair(k[c], p.k_hi[c], p.k_lo[c]);
+        }
+        // |k.k - 1| <= 2.000001e-6, in float32 from the pairs (error below
+        // 1e-6) unless that is too close to call, then in float64
+        float kkf = 0.0f;
+        for (int c = 0; c < 3; c++)
+            kkf = __fmaf_rn(p.k_hi[c], p.k_hi[c], __fmaf_rn(2.0f * p.k_hi[c], p.k_lo[c], kkf));
+        const float dev = fabsf(__fsub_rn(kkf, 1.0f));
+        bool unit;
+        if (dev <= 1.000001e-6f) {
+            unit = true;
+        } else if (dev > 3.000001e-6f || !(dev == dev)) {
+            unit = false;
+        } else {
+            const double kk = __dadd_rn(__dadd_rn(__dmul_rn(k[0], k[0]), __dmul_rn(k[1], k[1])), __dmul_rn(k[2], k[2]));
+            unit = fabs(kk - 1.0) <= 2.000001e-6;
+        }
+        if (!unit) m = -2;
         if (prep == PREP_FP64) {
             out->cell = m;
             continue;
         }
-        RayPrep p;
         p.cell = m;
-        for (int c = 0; c < 3; c++) {
-            split_double(r0[c], p.r0_hi[c], p.r0_lo[c]);
-            split_double(k[c], p.k_hi[c], p.k_lo[c]);
-        }
         // distance to the wall ahead (Eq. 5 for the walls the ray faces), as
         // a float pair: q1 = n/k rounded, the exact remainder n - q1 k by
         // fma, then q2 = remainder / k (relative error a few 2^-48)
         float th = 3.0e38f, tl = 0.0f;
         int wid = -1;
         for (int c = 0; c < 3; c++) {
-            if (k[c] == 0.0) continue;
-            const bool up = k[c] > 0.0;
+            const uint64_t kb = dbits(k[c]);
+            if ((kb << 1) == 0) continue;  // k_c = +-0
+            const bool up = (kb >> 63) == 0;
             float nh, nl;
-            split_double(__dsub_rn(up ? gp->hi[c] : gp->lo[c], r0[c]), nh, nl);
+            split_pair(__dsub_rn(up ? gp->hi[c] : gp->lo[c], P.x[c]), nh, nl);
             const float kh = p.k_hi[c], kl = p.k_lo[c];
             const float q1 = __fdiv_rn(nh, kh);
             float rem = __fmaf_rn(-q1, kh, nh);

@@ -549,7 +549,11 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
     }
     const int64_t K = (int64_t)out.dim[0] * out.dim[1] * out.dim[2];
     const double diag = std::sqrt(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
-    const double pad = 1e-7 * diag;  // covers rounding of the block index on the device
+    double maxabs = 0.0;
+    for (int c = 0; c < 6; c++) maxabs = std::max(maxabs, std::fabs(box[c]));
+    // covers the float32 block index on the device (error below
+    // 4u |x - lo| + 4u^2 max|coordinate|, u = 2^-24)
+    const double pad = 1e-6 * diag + 1e-13 * maxabs;
     auto range = [&](int64_t m, int c, int32_t &a, int32_t &b) {
         double lo = (bbox[6 * m + c] - pad - box[c]) / ext[c] * out.dim[c];
         double hi = (bbox[6 * m + 3 + c] + pad - box[c]) / ext[c] * out.dim[c];

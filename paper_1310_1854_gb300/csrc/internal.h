@@ -69,6 +69,9 @@ struct GridDev {
     const float4 *blk_rec;
     double lo[3], hi[3];      // domain box
     double bscale[3];         // blocks per unit length along each axis
+    int64_t lokey[3], hikey[3];        // order keys of lo and hi (exact box test)
+    float flo_hi[3], flo_lo[3];        // lo as float pairs
+    float fbscale[3];                  // bscale in float32
     int32_t bdim[3];
     int32_t M;
     float kappa;

@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "fsplit.h"
 #include "internal.h"
 #include "kernels.h"
 
@@ -77,6 +78,11 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float x) {
 __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
     hi = __double2float_rn(x);
     lo = __double2float_rn(__dsub_rn(x, (double)hi));
+}
+
+// The same split with integer operations where they cover x (nearly always)
+__device__ __forceinline__ void split_pair(double x, float &hi, float &lo) {
+    if (!split_double_int(x, hi, lo)) split_double(x, hi, lo);
 }
 
 __device__ __forceinline__ void ff_add_double(float &hi, float &lo, double x) {
@@ -204,19 +210,44 @@ __device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const flo
 // C(r): nearest site among the candidates of r's block (Sect. 2.3)
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ bool inside(const GridDev *gp, double x, double y, double z) {
-    return x >= gp->lo[0] && x <= gp->hi[0] && y >= gp->lo[1] && y <= gp->hi[1] && z >= gp->lo[2] &&
-           z <= gp->hi[2];
+// A query point: float64 coordinates and their float pairs.
+struct LocPt {
+    double x[3];
+    float h[3], l[3];
+};
+
+__device__ __forceinline__ LocPt loc_point(double x, double y, double z) {
+    LocPt P;
+    P.x[0] = x;
+    P.x[1] = y;
+    P.x[2] = z;
+    for (int c = 0; c < 3; c++) split_pair(P.x[c], P.h[c], P.l[c]);
+    return P;
 }
 
-__device__ __forceinline__ int block_of(const GridDev *gp, double x, double y, double z) {
-    int i = (int)__dmul_rn(__dsub_rn(x, gp->lo[0]), gp->bscale[0]);
-    int j = (int)__dmul_rn(__dsub_rn(y, gp->lo[1]), gp->bscale[1]);
-    int k = (int)__dmul_rn(__dsub_rn(z, gp->lo[2]), gp->bscale[2]);
-    i = max(0, min(i, gp->bdim[0] - 1));
-    j = max(0, min(j, gp->bdim[1] - 1));
-    k = max(0, min(k, gp->bdim[2] - 1));
-    return (i * gp->bdim[1] + j) * gp->bdim[2] + k;
+// Closed box test, exact (integer order keys of the float64 values)
+__device__ __forceinline__ bool inside(const GridDev *gp, const LocPt &P) {
+    bool in = true;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int64_t k = dkey(P.x[c]);
+        in = in && !disnan(P.x[c]) && k >= gp->lokey[c] && k <= gp->hikey[c];
+    }
+    return in;
+}
+
+// Block of the point, from its float pairs: (x - lo) is formed to within
+// 2u|x - lo| + 4u^2 max|coordinate|, so the index may be off only for points
+// closer to a block face than the padding of the block lists, and those
+// lists name every cell within that padding.
+__device__ __forceinline__ int block_of(const GridDev *gp, const LocPt &P) {
+    int i[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float d = __fadd_rn(__fsub_rn(P.h[c], gp->flo_hi[c]), __fsub_rn(P.l[c], gp->flo_lo[c]));
+        i[c] = max(0, min(__float2int_rz(__fmul_rn(d, gp->fbscale[c])), gp->bdim[c] - 1));
+    }
+    return (i[0] * gp->bdim[1] + i[1]) * gp->bdim[2] + i[2];
 }
 
 // float64 scan of a block list, distances as ((dx dx + dy dy) + dz dz)
@@ -228,6 +259,7 @@ static __device__ __noinline__ int locate64(const GridDev *gp, double x, double 
     for (int i = beg; i < end; i++) {
         const float4 q = __ldg(&rec[i]);
         const int c = __float_as_int(q.w);
+        if (c < 0) continue;  // padding
         const double dx = __dsub_rn(x, (double)q.x), dy = __dsub_rn(y, (double)q.y), dz = __dsub_rn(z, (double)q.z);
         const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         if (best < 0 || d2 < bd || (d2 == bd && __ldg(&perm[c]) < __ldg(&perm[best]))) {
@@ -243,34 +275,46 @@ static __device__ __noinline__ int locate64(const GridDev *gp, double x, double 
 // D2 - E(D2) > D1 + E(D1), E(D) = u (10 D + 4 X sqrt D), X = max |x_c|,
 // which bounds the rounding error of a float32 squared distance; otherwise
 // the list is rescanned in float64. *rechecked is set when that happened.
-static __device__ __noinline__ int locate_point(const GridDev *gp, double x, double y, double z, bool fp32,
-                                                int *rechecked) {
-    if (!inside(gp, x, y, z)) return -1;
-    const int b = block_of(gp, x, y, z);
+// Block lists start on 32-byte boundaries and have an even length (NaN
+// records pad them; a NaN distance never wins), so they can be read in pairs
+// (PAIRS; the traversal kernel's rare relocation reads them one by one).
+template <bool PAIRS>
+static __device__ __noinline__ int locate_point(const GridDev *gp, const LocPt P, bool fp32, int *rechecked) {
+    if (!inside(gp, P)) return -1;
+    const int b = block_of(gp, P);
     const int beg = __ldg(&gp->blk_off[b]), end = __ldg(&gp->blk_off[b + 1]);
     if (fp32) {
         const float4 *rec = gp->blk_rec;
-        const float xf = __double2float_rn(x), yf = __double2float_rn(y), zf = __double2float_rn(z);
+        const float xf = P.h[0], yf = P.h[1], zf = P.h[2];
         const float X = fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
         float D1 = __int_as_float(0x7f800000), D2 = D1;
         int i1 = -1;
-        for (int i = beg; i < end; i++) {
-            const float4 q = __ldg(&rec[i]);
-            const float dx = __fsub_rn(xf, q.x), dy = __fsub_rn(yf, q.y), dz = __fsub_rn(zf, q.z);
-            const float D = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            const bool better = D < D1;
-            D2 = better ? D1 : fminf(D2, D);
-            i1 = better ? __float_as_int(q.w) : i1;
-            D1 = fminf(D1, D);
+        for (int i = beg; i < end; i += 2) {
+            float4 q[2];
+            if (PAIRS) {
+                ldg_pair(rec + i, q[0], q[1]);
+            } else {
+                q[0] = __ldg(rec + i);
+                q[1] = __ldg(rec + i + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const float dx = __fsub_rn(xf, q[u].x), dy = __fsub_rn(yf, q[u].y), dz = __fsub_rn(zf, q[u].z);
+                const float D = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                const bool better = D < D1;
+                D2 = better ? D1 : fminf(D2, D);
+                i1 = better ? __float_as_int(q[u].w) : i1;
+                D1 = fminf(D1, D);
+            }
         }
-        if (end - beg <= 1) return i1;
+        if (i1 >= 0 && D2 == __int_as_float(0x7f800000)) return i1;  // a single candidate
         const float s1 = sqrtf(D1), s2 = sqrtf(D2);
         const float E1 = 1.0001f * kU * __fmaf_rn(10.0f, D1, 4.0f * X * s1);
         const float E2 = 1.0001f * kU * __fmaf_rn(10.0f, D2, 4.0f * X * s2);
-        if (s2 > 8.0f * kU * X && __fsub_rd(D2, E2) > __fadd_ru(D1, E1)) return i1;
+        if (i1 >= 0 && s2 > 8.0f * kU * X && __fsub_rd(D2, E2) > __fadd_ru(D1, E1)) return i1;
         if (rechecked) *rechecked = 1;
     }
-    return locate64(gp, x, y, z, beg, end);
+    return locate64(gp, P.x[0], P.x[1], P.x[2], beg, end);
 }
 
 // ---------------------------------------------------------------------------
@@ -750,7 +794,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 const double t = __dadd_rn((double)th, (double)tl);
                 for (int c = 0; c < 3; c++) x[c] = __fma_rn(t, __ldg(rs->dir + 3 * li + c), __ldg(rs->origin + 3 * li + c));
             }
-            const int nm = locate_point(gp, x[0], x[1], x[2], !FP64, nullptr);
+            const int nm = locate_point<false>(gp, loc_point(x[0], x[1], x[2]), !FP64, nullptr);
             if (nm < 0) {
                 ended = true;
             } else {
