@@ -131,15 +131,17 @@ class VoronoiGrid:
         return vol, bb
 
     # -------------------------------------------------------------- launch
-    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, fp64_lanes_per_ray=4):
-        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), int(fp64_lanes_per_ray))
+    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, fp64_lanes_per_ray=4, order=0):
+        """Launch shape of the traversal kernels; order: 1 = longest estimated
+        path first, -1 = the caller's order, 0 = automatic (see vgrid.h)."""
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), int(fp64_lanes_per_ray), int(order))
         check(load().vgrid_set_launch(self._h, ctypes.byref(l)))
 
     def get_launch(self):
         l = _lib.Launch()
         check(load().vgrid_get_launch(self._h, ctypes.byref(l)))
         return {"lanes_per_ray": l.lanes_per_ray, "block": l.block, "blocks_per_sm": l.blocks_per_sm,
-                "fp64_lanes_per_ray": l.fp64_lanes_per_ray}
+                "fp64_lanes_per_ray": l.fp64_lanes_per_ray, "order": l.order}
 
     def enable_timing(self, enable=True):
         check(load().vgrid_enable_timing(self._h, int(bool(enable))))

@@ -60,7 +60,7 @@ class Info(ctypes.Structure):
 
 class Launch(ctypes.Structure):
     _fields_ = [("lanes_per_ray", c_int32), ("block", c_int32), ("blocks_per_sm", c_int32),
-                ("fp64_lanes_per_ray", c_int32)]
+                ("fp64_lanes_per_ray", c_int32), ("order", c_int32)]
 
 
 class Rayset(ctypes.Structure):

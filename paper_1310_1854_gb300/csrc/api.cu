@@ -81,7 +81,7 @@ struct vgrid {
     int sms = 1;
     int64_t M = 0;
     vgrid_opts opts{};
-    vgrid_launch launch{1, 128, 0, 4};
+    vgrid_launch launch{1, 128, 0, 4, 0};
     GridDev hd{};
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
@@ -90,6 +90,7 @@ struct vgrid {
     int32_t *d_perm = nullptr;
     int32_t *d_blk_off = nullptr;
     float4 *d_blk_rec = nullptr;
+    float *d_dens = nullptr;         // coarse density grid for the ray order
     std::vector<int32_t> perm, inv;  // internal -> caller, caller -> internal
     vg::CellsOut cells;              // internal order
     vg::BlocksOut blocks;
@@ -103,6 +104,10 @@ struct vgrid {
     int64_t scan_cap = 0;
     double *d_entry = nullptr;   // entry points of VGRID_ENTER calls
     int64_t entry_cap = 0;
+    uint8_t *d_bin = nullptr;    // ray order: bins, counts, permutation
+    uint32_t *d_hist = nullptr;
+    int32_t *d_order = nullptr;
+    int64_t order_cap = 0;
     double build_seconds = 0;
     int64_t device_bytes = 0;
     int64_t host_fallback_cells = 0;
@@ -117,7 +122,7 @@ struct vgrid_batch {
     int sms = 1;
     int32_t G = 0;
     int64_t total = 0;
-    vgrid_launch launch{1, 128, 0, 4};
+    vgrid_launch launch{1, 128, 0, 4, 0};
     GridDev *d_grids = nullptr;
     RaySetDev *d_sets = nullptr;
     RayPrep *d_start = nullptr;
@@ -158,8 +163,9 @@ static void free_events(vgrid_t *g) {
 static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
-    void *ptrs[] = {g->d_desc, g->d_site, g->d_cells, g->d_rel, g->d_perm, g->d_blk_off, g->d_blk_rec,
-                    g->d_queue, g->d_stats, g->d_set, g->d_start, g->d_scan, g->d_entry};
+    void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
+                    g->d_order, g->d_perm,  g->d_blk_off, g->d_blk_rec, g->d_queue, g->d_stats, g->d_set,
+                    g->d_start, g->d_scan,  g->d_entry};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -335,6 +341,32 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         boff[i + 1] = boff[i] + (int32_t)((len + 1) & ~(int64_t)1);
     }
 
+    // coarse density grid for the ray order: about 2^18 near-cubic cells
+    // over the box, each holding (sites per unit volume)^(1/3), which is
+    // proportional to the cell faces a ray crosses per unit length
+    int32_t ddim[3];
+    {
+        const double ext[3] = {bbox[3] - bbox[0], bbox[4] - bbox[1], bbox[5] - bbox[2]};
+        const double cs = std::cbrt(ext[0] * ext[1] * ext[2] / 262144.0);
+        for (int c = 0; c < 3; c++) ddim[c] = (int32_t)std::min<long>(std::max<long>(std::lround(ext[c] / cs), 1), 256);
+    }
+    std::vector<float> dens((size_t)ddim[0] * ddim[1] * ddim[2], 0.0f);
+    {
+        std::vector<int64_t> cnt(dens.size(), 0);
+        for (int64_t i = 0; i < M; i++) {
+            int64_t idx = 0;
+            for (int c = 0; c < 3; c++) {
+                const double f = (Si[3 * i + c] - bbox[c]) / (bbox[3 + c] - bbox[c]) * ddim[c];
+                const int64_t ic = std::min<int64_t>(std::max<int64_t>((int64_t)f, 0), ddim[c] - 1);
+                idx = idx * ddim[c] + ic;
+            }
+            cnt[idx]++;
+        }
+        const double vol = (bbox[3] - bbox[0]) * (bbox[4] - bbox[1]) * (bbox[5] - bbox[2]) /
+                           ((double)ddim[0] * ddim[1] * ddim[2]);
+        for (size_t q = 0; q < dens.size(); q++) dens[q] = (float)std::cbrt(std::max(0.25, (double)cnt[q]) / vol);
+    }
+
     if (o.host_only) {
         g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int c = 0; c < 3; c++) {
@@ -364,6 +396,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
     VG_ALLOC(g->d_blk_rec, (size_t)boff[nblk] + 2);
+    VG_ALLOC(g->d_dens, dens.size());
     VG_ALLOC(g->d_desc, 1);
     VG_ALLOC(g->d_queue, 1);
     VG_ALLOC(g->d_stats, 1);
@@ -375,6 +408,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (e == cudaSuccess) e = cudaMemcpy(g->d_rel, rel.data(), sizeof(float) * 4 * nrel, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_dens, dens.data(), sizeof(float) * dens.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         const float fnan = std::numeric_limits<float>::quiet_NaN();
         std::vector<float> brec(4 * ((size_t)boff[nblk] + 2));
@@ -402,6 +436,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     hd.perm = g->d_perm;
     hd.blk_off = g->d_blk_off;
     hd.blk_rec = g->d_blk_rec;
+    hd.dens = g->d_dens;
     double dmax = 0;
     for (int c = 0; c < 3; c++) {
         hd.lo[c] = bbox[c];
@@ -413,6 +448,8 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         hd.flo_hi[c] = (float)bbox[c];
         hd.flo_lo[c] = (float)(bbox[c] - (double)hd.flo_hi[c]);
         hd.fbscale[c] = (float)hd.bscale[c];
+        hd.ddim[c] = ddim[c];
+        hd.dscale[c] = (float)((double)ddim[c] / (bbox[3 + c] - bbox[c]));
         dmax = std::max(dmax, std::max(std::fabs(bbox[c]), std::fabs(bbox[3 + c])));
     }
     const double dx = bbox[3] - bbox[0], dy = bbox[4] - bbox[1], dz = bbox[5] - bbox[2];
@@ -509,7 +546,7 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
 int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (!l) {
-        g->launch = vgrid_launch{1, 128, 0, 4};
+        g->launch = vgrid_launch{1, 128, 0, 4, 0};
         return VGRID_OK;
     }
     if (!valid_lpr(l->lanes_per_ray)) return fail(VGRID_ERR_ARG, "lanes_per_ray must be 1, 2, 4 or 8");
@@ -517,6 +554,7 @@ int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
         return fail(VGRID_ERR_ARG, "fp64_lanes_per_ray must be 0, 1, 2, 4 or 8");
     if (l->block < 32 || l->block > 256 || l->block % 32) return fail(VGRID_ERR_ARG, "block must be 32..256, multiple of 32");
     if (l->blocks_per_sm < 0) return fail(VGRID_ERR_ARG, "blocks_per_sm must be >= 0");
+    if (l->order < -1 || l->order > 1) return fail(VGRID_ERR_ARG, "order must be -1, 0 or 1");
     g->launch = *l;
     return VGRID_OK;
 }
@@ -578,6 +616,25 @@ int ensure_entry(vgrid_t *g, int64_t N) {
     return VGRID_OK;
 }
 
+int ensure_order(vgrid_t *g, int64_t N) {
+    if (!g->d_hist) {
+        int rc = dmalloc(&g->d_hist, 2 * vg::kOrderBins, g->device_bytes);
+        if (rc) return rc;
+    }
+    if (N <= g->order_cap) return VGRID_OK;
+    if (g->d_bin) cudaFree(g->d_bin);
+    if (g->d_order) cudaFree(g->d_order);
+    g->device_bytes -= g->order_cap * (int64_t)(sizeof(uint8_t) + sizeof(int32_t));
+    g->d_bin = nullptr;
+    g->d_order = nullptr;
+    g->order_cap = 0;
+    int rc = dmalloc(&g->d_bin, (size_t)N, g->device_bytes);
+    if (!rc) rc = dmalloc(&g->d_order, (size_t)N, g->device_bytes);
+    if (rc) return rc;
+    g->order_cap = N;
+    return VGRID_OK;
+}
+
 int ensure_scan(vgrid_t *g, int64_t N) {
     const int64_t need = vg::scan_tmp_elems(N);
     if (need <= g->scan_cap) return VGRID_OK;
@@ -609,6 +666,30 @@ int launch_trace(const void *fn, const vgrid_launch &l, int sms, int64_t total, 
     const int blocks = persistent_blocks(fn, l, sms, total);
     void *args[] = {&a};
     VG_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(l.block), args, 0, s));
+    return VGRID_OK;
+}
+
+// resident lanes of a persistent float32 launch
+int64_t resident_lanes(vgrid_t *g, const void *fn, const vgrid_launch &l) {
+    return (int64_t)persistent_blocks(fn, l, g->sms, INT64_MAX / 16) * l.block / l.lanes_per_ray;
+}
+
+// float32 start records for the set in g->d_set; with the ray order (see
+// vgrid_launch.order) also the permutation, which goes to *order
+int locate_fp32(vgrid_t *g, const void *fn, const vgrid_launch &l, int64_t N, const int32_t **order, cudaStream_t s) {
+    *order = nullptr;
+    const bool want = l.order == 1 || (l.order == 0 && N >= 2 * resident_lanes(g, fn, l));
+    if (!want || N > INT32_MAX) {
+        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
+        return VGRID_OK;
+    }
+    int rc = ensure_order(g, N);
+    if (rc) return rc;
+    const vg::RayOrder ord{g->d_bin, g->d_hist, g->d_order};
+    VG_CUDA(cudaMemsetAsync(g->d_hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), s));
+    VG_CUDA(vg::launch_locate_ordered(g->d_desc, g->d_set, 1, N, ord, g->sms, s));
+    VG_CUDA(vg::launch_order(ord, N, g->sms, s));
+    *order = g->d_order;
     return VGRID_OK;
 }
 
@@ -687,9 +768,16 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, fp64 ? vg::PREP_FP64 : vg::PREP_FP32, nullptr, g->sms, s));
+    const int32_t *order = nullptr;
+    if (fp64) {
+        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP64, nullptr, g->sms, s));
+    } else {
+        const void *fn = ks.fn[0][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_COUNT];
+        if ((rc = locate_fp32(g, fn, L, N, &order, s))) return rc;
+    }
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
+    a.order = order;
     a.grids = g->d_desc;
     a.sets = g->d_set;
     a.nsets = 1;
@@ -741,9 +829,11 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
     RaySetDev set{origin, dir, nullptr, nullptr, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
+    const int32_t *order = nullptr;
+    if ((rc = locate_fp32(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_GRAD], g->launch, N, &order, s))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
+    a.order = order;
     a.grids = g->d_desc;
     a.sets = g->d_set;
     a.nsets = 1;
@@ -804,9 +894,11 @@ int vgrid_interact(vgrid_t *g, const double *origin, const double *dir, int64_t 
     RaySetDev set{origin, dir, nullptr, nullptr, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
-    VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
+    const int32_t *order = nullptr;
+    if ((rc = locate_fp32(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_INTERACT], g->launch, N, &order, s))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
+    a.order = order;
     a.grids = g->d_desc;
     a.sets = g->d_set;
     a.nsets = 1;

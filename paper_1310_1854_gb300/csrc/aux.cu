@@ -35,7 +35,13 @@ cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long
 // float pairs of origin and direction); PREP_FP64: float64 form (cell and
 // direction check). The caller's id of the cell goes to out_caller if given.
 __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const RaySetDev *sets, int nsets,
-                                                     int64_t total, int prep, int32_t *out_caller) {
+                                                     int64_t total, int prep, int32_t *out_caller, uint8_t *bin,
+                                                     uint32_t *hist) {
+    __shared__ uint32_t s_hist[kOrderBins];
+    if (bin) {
+        for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) s_hist[b] = 0u;
+        __syncthreads();
+    }
     for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int set = find_set(sets, nsets, w);
         const RaySetDev &rs = sets[set];
@@ -115,7 +121,83 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         const float4 *src = reinterpret_cast<const float4 *>(&p);
         float4 *dst = reinterpret_cast<float4 *>(out);
         for (int q = 0; q < 4; q++) dst[q] = src[q];
+        if (bin) {
+            // estimated crossings: (sites per volume)^(1/3) integrated along
+            // the in-box segment [0, t_max] with 16 midpoint samples
+            int b = 0;
+            if (m >= 0 && th > 0.0f) {
+                const float dt = th * 0.0625f;
+                float acc = 0.0f;
+                for (int i = 0; i < 16; i++) {
+                    const float t = (i + 0.5f) * dt;
+                    int idx = 0;
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        const float x = __fmaf_rn(t, p.k_hi[c], P.h[c]);
+                        const int ic = __float2int_rz(__fmul_rn(__fsub_rn(x, gp->flo_hi[c]), gp->dscale[c]));
+                        idx = idx * gp->ddim[c] + max(0, min(ic, gp->ddim[c] - 1));
+                    }
+                    acc += __ldg(gp->dens + idx);
+                }
+                b = max(0, min(kOrderBins - 1, __float2int_rz(4.0f * __log2f(1.0f + acc * dt))));
+            }
+            bin[w] = (uint8_t)b;
+            atomicAdd(&s_hist[b], 1u);
+        }
     }
+    if (bin) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x)
+            if (s_hist[b]) atomicAdd(&hist[b], s_hist[b]);
+    }
+}
+
+cudaError_t launch_locate_ordered(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total,
+                                  const RayOrder &ord, int sms, cudaStream_t s) {
+    if (total <= 0) return cudaSuccess;
+    int64_t blocks = (total + 255) / 256;
+    blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
+    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, PREP_FP32, nullptr, ord.bin, ord.hist);
+    return cudaGetLastError();
+}
+
+// cursor[b] = number of rays in longer bins (the longest bin goes first)
+__global__ void order_scan_kernel(uint32_t *hist) {
+    __shared__ uint32_t h[kOrderBins];
+    const int b = threadIdx.x;
+    h[b] = hist[b];
+    __syncthreads();
+    uint32_t sum = 0u;
+    for (int q = b + 1; q < kOrderBins; q++) sum += h[q];
+    hist[kOrderBins + b] = sum;
+}
+
+// order[cursor[bin[w]]++] = w, one atomic per warp and bin (all lanes of a
+// warp run every iteration, so the full-mask match is safe)
+__global__ void order_scatter_kernel(const uint8_t *__restrict__ bin, int64_t total, uint32_t *cursor,
+                                     int32_t *__restrict__ order) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = warp0; base < total; base += stride) {
+        const int64_t w = base + lane;
+        const int b = w < total ? (int)__ldg(bin + w) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t pos = 0u;
+        if (lane == leader && b >= 0) pos = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (b >= 0) order[pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)w;
+    }
+}
+
+cudaError_t launch_order(const RayOrder &ord, int64_t total, int sms, cudaStream_t s) {
+    if (total <= 0) return cudaSuccess;
+    order_scan_kernel<<<1, kOrderBins, 0, s>>>(ord.hist);
+    int64_t blocks = (total + 255) / 256;
+    blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
+    order_scatter_kernel<<<(unsigned)blocks, 256, 0, s>>>(ord.bin, total, ord.hist + kOrderBins, ord.order);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,
@@ -123,7 +205,7 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
-    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, prep, out_caller);
+    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, prep, out_caller, nullptr, nullptr);
     return cudaGetLastError();
 }
 

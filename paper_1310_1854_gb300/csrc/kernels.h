@@ -32,6 +32,7 @@ struct TraceArgs {
     // parameter space) instead of from `grids` / `sets`
     GridDev g1;
     RaySetDev s1;
+    const int32_t *order;     // nullable: queue position -> ray (longest predicted first)
 };
 
 
@@ -55,6 +56,24 @@ cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long
                            cudaStream_t s);
 // what the start-cell kernel writes per ray (see locate_kernel)
 enum { PREP_CELL32 = 0, PREP_FP32 = 1, PREP_FP64 = 2, PREP_CELL64 = 3 };
+// Longest-predicted-first ray order. A persistent launch ends when its last
+// ray does, so long rays handed out late leave most lanes idle at the end;
+// handing the longest out first fixes that. The start-cell kernel estimates
+// each ray's crossings (sum of the coarse (sites per volume)^(1/3) grid at 16
+// points of its in-box segment, times the segment length) and counts rays
+// per quarter-octave bin of the estimate; a scan and a scatter turn the bins
+// into the permutation the traversal takes its rays from.
+constexpr int kOrderBins = 64;
+struct RayOrder {
+    uint8_t *bin;     // per ray
+    uint32_t *hist;   // kOrderBins counts, then kOrderBins cursors (zeroed by the caller)
+    int32_t *order;   // queue position -> ray
+};
+// the float32 start records (PREP_FP32) plus the bins and their counts
+cudaError_t launch_locate_ordered(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total,
+                                  const RayOrder &ord, int sms, cudaStream_t s);
+// bins -> permutation (scan of the counts, longest bin first, and scatter)
+cudaError_t launch_order(const RayOrder &ord, int64_t total, int sms, cudaStream_t s);
 cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,
                           int32_t *out_caller, int sms, cudaStream_t s);
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,

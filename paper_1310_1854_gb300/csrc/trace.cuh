@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             if (need) {
                 const int rank = __popc(needmask & ((1u << gbase) - 1u));
                 const int64_t w = (int64_t)base + rank;
-                ray = w < a.total ? w : -2;
+                ray = w < a.total ? (a.order ? (int64_t)__ldg(a.order + w) : w) : -2;
             }
         }
         if (!__any_sync(0xffffffffu, ray != -2)) break;

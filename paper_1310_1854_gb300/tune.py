@@ -83,9 +83,11 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
         if hit:
             cur = grid.get_launch()
             if precision == "fp64":
-                grid.set_launch(cur["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], hit["lanes_per_ray"])
+                grid.set_launch(cur["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], hit["lanes_per_ray"],
+                                cur["order"])
             else:
-                grid.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], cur["fp64_lanes_per_ray"])
+                grid.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], cur["fp64_lanes_per_ray"],
+                                cur["order"])
             return dict(hit, cached=True, key=key)
     n = min(sample, origin.shape[0])
     g = torch.Generator(device="cpu").manual_seed(1310_1854)
@@ -98,9 +100,9 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
 
     def time_fn(shape):
         if precision == "fp64":
-            grid.set_launch(prev["lanes_per_ray"], shape[1], shape[2], shape[0])
+            grid.set_launch(prev["lanes_per_ray"], shape[1], shape[2], shape[0], prev["order"])
         else:
-            grid.set_launch(shape[0], shape[1], shape[2], fp64_lanes)
+            grid.set_launch(shape[0], shape[1], shape[2], fp64_lanes, prev["order"])
         grid.trace(o, d, precision=precision, out_tau=tau)  # warm
         grid.enable_timing(True)
         grid.read_timing()
@@ -112,7 +114,7 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
     try:
         best, table = search(space, time_fn)
     except Exception:
-        grid.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"], fp64_lanes)
+        grid.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"], fp64_lanes, prev["order"])
         raise
     time_fn(best)
     entry = {"lanes_per_ray": best[0], "block": best[1], "blocks_per_sm": best[2], "ms": table[f"{best[0]},{best[1]},{best[2]}"],

@@ -403,6 +403,37 @@ def test_interaction_matches_oracle():
     assert np.all(np.abs(ab - ab_o) <= 2e-4 * np.abs(ab_o) + 1e-6 * ab_o.max())
 
 
+def test_ray_order_does_not_change_results():
+    """The longest-first ray order (vgrid_launch.order) changes which lane
+    takes which ray, not what a ray computes: tau, segment lists and
+    interaction cells/distances are bit-identical to the caller's order, and
+    the gradient agrees up to the order of its float32 atomic sums."""
+    g, rays = gen.config2(n_rays=300_000)
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    rng = gen.rng_for(310)
+    tau_int = dev((-np.log(rng.random(len(rays.origin)))).astype(np.float32))
+    dL = dev(rng.uniform(0.5, 2.0, len(rays.origin)).astype(np.float32))
+    out = {}
+    for order in (-1, 1):
+        vg.set_launch(order=order)
+        t = vg.trace(O, D, precision="fp32", stats=True)
+        sg = vg.trace(O, D, precision="fp32", segments=True)
+        c, s_, _ = vg.interact(O, D, tau_int)
+        gr = torch.zeros(len(g.sites), dtype=torch.float32, device="cuda")
+        vg.trace_grad(O, D, dL, gr)
+        out[order] = (t.tau.cpu().numpy(), t.stats, sg.seg_off.cpu().numpy(), sg.seg_cell.cpu().numpy(),
+                      sg.seg_len.cpu().numpy(), c.cpu().numpy(), s_.cpu().numpy(), gr.cpu().numpy())
+    a, b = out[-1], out[1]
+    for k in (0, 2, 3, 4, 5, 6):
+        np.testing.assert_array_equal(a[k], b[k])
+    for key in ("rays", "crossings", "decisions", "rechecks"):
+        assert a[1][key] == b[1][key]
+    np.testing.assert_allclose(b[7], a[7], rtol=1e-4, atol=1e-6 * float(np.abs(a[7]).max()))
+    vg.set_launch()
+    assert vg.get_launch()["order"] == 0
+
+
 def test_rays_entering_from_outside():
     g, _ = gen.config1(10)
     rng = gen.rng_for(310)

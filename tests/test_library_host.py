@@ -157,3 +157,22 @@ def test_host_only_grid_refuses_device_calls(libvgrid):
     assert lib.vgrid_locate(vg._h, dummy, 1, 0, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_trace_grad(vg._h, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_enable_timing(vg._h, 1) == _lib.ERR_ARG
+
+
+def test_launch_shape_validation(libvgrid):
+    """vgrid_set_launch checks every field (host-only grid: no GPU needed)."""
+    from paper_1310_1854_gb300 import _lib
+    vg = _grid(gen.cubic_lattice(2), gen.CUBE_BOX)
+    assert vg.get_launch() == {"lanes_per_ray": 1, "block": 128, "blocks_per_sm": 0, "fp64_lanes_per_ray": 4,
+                               "order": 0}
+    vg.set_launch(lanes_per_ray=2, block=256, blocks_per_sm=3, fp64_lanes_per_ray=8, order=1)
+    assert vg.get_launch() == {"lanes_per_ray": 2, "block": 256, "blocks_per_sm": 3, "fp64_lanes_per_ray": 8,
+                               "order": 1}
+    for bad in ({"order": 2}, {"order": -2}, {"lanes_per_ray": 3}, {"block": 48}, {"block": 512},
+                {"blocks_per_sm": -1}, {"fp64_lanes_per_ray": 5}):
+        with pytest.raises(_lib.VGridError):
+            vg.set_launch(**bad)
+    assert vg.get_launch()["order"] == 1  # a refused shape leaves the last one
+    lib = _lib.load()
+    assert lib.vgrid_set_launch(vg._h, None) == 0
+    assert vg.get_launch()["order"] == 0
