@@ -134,9 +134,15 @@ typedef struct {
                                    when there are at least two rays per resident lane.
                                    Results do not depend on it; the time does: a
                                    persistent launch lasts until its last ray ends.
-                                   Used by vgrid_trace (float32), vgrid_trace_grad and
-                                   vgrid_interact; batches keep the given order. */
+                                   Used by vgrid_trace (float32), vgrid_trace_host,
+                                   vgrid_trace_grad and vgrid_interact; a batch orders
+                                   all its work items together only with order = 1
+                                   (that interleaves its grids, which then share L2). */
 } vgrid_launch;
+
+/* Kernels this library has launched in this process so far (every call
+ * adds the kernels it enqueued; a replayed batch graph adds those it holds). */
+int64_t vgrid_kernel_launches(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *vgrid_last_error(void);
@@ -225,6 +231,34 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
 int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, int output,
                 void *tau, int64_t *seg_off, int32_t *seg_cell, void *seg_len, int64_t seg_capacity,
                 int32_t *ray_status, vgrid_stats *stats, vgrid_stream_t stream);
+
+/*
+ * tau of N rays held in HOST memory (Sect. 2.2 as vgrid_trace, VGRID_TAU
+ * output), with the copies overlapped with the traversal. Each chunk of
+ * rays goes through one of two device slots that alternate across chunks and
+ * calls: its origins and directions are copied in on a copy stream as soon
+ * as the slot's previous traversal is done, it is traced on `stream`, and its
+ * tau (and status) are copied out on a second copy stream. Consecutive calls
+ * therefore overlap: the next call's rays go in while this call's traversal
+ * runs. Host buffers should be page-locked (cudaHostAlloc, pinned tensors)
+ * for the copies to overlap; pageable buffers work, serialised.
+ *   origin, dir   host float64[N*3], unit directions as for vgrid_trace
+ *   precision     VGRID_FP64 or VGRID_FP32_RECHECK
+ *   tau           host float64[N] (FP64) or float32[N] (FP32_RECHECK)
+ *   ray_status    host int32[N] or NULL
+ *   chunk         rays per chunk; 0 = N. A traversal launch lasts at least
+ *                 as long as its longest ray, so chunks only pay off for rays
+ *                 that do not fit on the device at once.
+ *   stats         host or NULL: counters summed over all chunks; the call
+ *                 then synchronises `stream` before it returns.
+ * Without stats the call returns once everything is queued: the results are
+ * in host memory when `stream` has been synchronised, and the host buffers
+ * must stay untouched until then. The first call with a larger chunk than
+ * before synchronises the device and allocates two device slots (56 bytes
+ * per ray each); the first call creates two copy streams.
+ */
+int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,
+                     int32_t *ray_status, int64_t chunk, vgrid_stats *stats, vgrid_stream_t stream);
 
 /*
  * Adjoint of tau = sum kappa rho l with respect to rho: for every ray r and

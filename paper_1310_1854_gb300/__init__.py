@@ -200,6 +200,36 @@ class VoronoiGrid:
         total = int(seg_off[N].item())
         return TraceResult(tau, seg_off, cells[:total], lens[:total], st, cs.as_dict())
 
+    def trace_host(self, origin, direction, precision="fp32", out_tau=None, status=False, stats=False, chunk=0,
+                   stream=None, wait=True) -> TraceResult:
+        """tau of rays held in host memory (CPU float64 tensors of shape
+        (N, 3); pinned for the copies to overlap the traversal), results in
+        host memory: vgrid_trace_host. With wait=False (and no stats) the call
+        only queues the work: the results are valid once the stream has been
+        synchronised, and consecutive calls overlap their copies with the
+        previous traversal."""
+        for t, name in ((origin, "origin"), (direction, "direction")):
+            if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.is_cuda:
+                raise TypeError(f"{name} must be a CPU float64 tensor of shape (N, 3)")
+            if t.dim() != 2 or t.shape[1] != 3:
+                raise ValueError(f"{name} must have shape (N, 3)")
+        O, D = origin.contiguous(), direction.contiguous()
+        N = O.shape[0]
+        if D.shape[0] != N:
+            raise ValueError("origin and direction differ in length")
+        prec = _PREC[precision]
+        tdt = torch.float64 if prec == _lib.FP64 else torch.float32
+        tau = out_tau if out_tau is not None else torch.empty(N, dtype=tdt, pin_memory=O.is_pinned())
+        if tau.is_cuda or tau.dtype != tdt or tau.numel() != N or not tau.is_contiguous():
+            raise ValueError(f"out_tau must be a contiguous CPU {tdt} tensor of N elements")
+        st = torch.empty(N, dtype=torch.int32, pin_memory=O.is_pinned()) if status else None
+        cs = _lib.Stats() if stats else None
+        check(load().vgrid_trace_host(self._h, _ptr(O), _ptr(D), N, prec, _ptr(tau), _ptr(st), int(chunk),
+                                      ctypes.byref(cs) if cs is not None else None, _stream(stream)))
+        if wait and N > 0:
+            (stream if stream is not None else torch.cuda.current_stream()).synchronize()
+        return TraceResult(tau, status=st, stats=cs.as_dict() if cs is not None else None)
+
     def interact(self, origin, direction, tau_int: torch.Tensor, weight: torch.Tensor | None = None,
                  absorbed: bool | torch.Tensor = False, stream=None):
         """Where each ray's running tau reaches tau_int: (cell int32, s float32,

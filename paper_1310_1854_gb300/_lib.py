@@ -90,6 +90,9 @@ SIGNATURES = [
     ("vgrid_locate", c_int32, [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]),
     ("vgrid_trace", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_void_p, c_void_p, c_void_p,
                               c_void_p, c_int64, c_void_p, ctypes.POINTER(Stats), c_void_p]),
+    ("vgrid_kernel_launches", c_int64, []),
+    ("vgrid_trace_host", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64,
+                                   c_void_p, c_void_p]),
     ("vgrid_trace_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     ("vgrid_set_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_get_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),

@@ -108,6 +108,15 @@ struct vgrid {
     uint32_t *d_hist = nullptr;
     int32_t *d_order = nullptr;
     int64_t order_cap = 0;
+    // host-pipelined calls: two device slots of rays and results, two copy
+    // streams and their events
+    double *d_hin[2] = {nullptr, nullptr};  // chunk origins then directions
+    void *d_hout[2] = {nullptr, nullptr};   // chunk tau (8 bytes per ray)
+    int32_t *d_hst[2] = {nullptr, nullptr}; // chunk status
+    int64_t host_cap = 0;
+    int host_slot = 0;
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_k[2] = {}, ev_out[2] = {};
     double build_seconds = 0;
     int64_t device_bytes = 0;
     int64_t host_fallback_cells = 0;
@@ -128,6 +137,10 @@ struct vgrid_batch {
     RayPrep *d_start = nullptr;
     unsigned long long *d_queue = nullptr;
     StatsDev *d_stats = nullptr;
+    uint8_t *d_bin = nullptr;    // ray order (when used): bins, counts, permutation
+    uint32_t *d_hist = nullptr;
+    int32_t *d_order = nullptr;
+    int64_t graph_kernels = 0;   // kernels in the captured graph
     int ngrids = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -160,9 +173,30 @@ static void free_events(vgrid_t *g) {
     g->n_loc = g->n_trace = 0;
 }
 
+static void free_pipe(vgrid_t *g) {
+    for (int k = 0; k < 2; k++) {
+        if (g->d_hin[k]) cudaFree(g->d_hin[k]);
+        if (g->d_hout[k]) cudaFree(g->d_hout[k]);
+        if (g->d_hst[k]) cudaFree(g->d_hst[k]);
+        g->d_hin[k] = nullptr;
+        g->d_hout[k] = nullptr;
+        g->d_hst[k] = nullptr;
+    }
+    g->device_bytes -= g->host_cap * (int64_t)(2 * (6 * sizeof(double) + sizeof(double) + sizeof(int32_t)));
+    g->host_cap = 0;
+}
+
 static void free_grid(vgrid_t *g) {
     if (!g) return;
     free_events(g);
+    free_pipe(g);
+    for (int k = 0; k < 2; k++) {
+        if (g->ev_in[k]) cudaEventDestroy(g->ev_in[k]);
+        if (g->ev_k[k]) cudaEventDestroy(g->ev_k[k]);
+        if (g->ev_out[k]) cudaEventDestroy(g->ev_out[k]);
+    }
+    if (g->s_h2d) cudaStreamDestroy(g->s_h2d);
+    if (g->s_d2h) cudaStreamDestroy(g->s_d2h);
     void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
                     g->d_order, g->d_perm,  g->d_blk_off, g->d_blk_rec, g->d_queue, g->d_stats, g->d_set,
                     g->d_start, g->d_scan,  g->d_entry};
@@ -666,6 +700,7 @@ int launch_trace(const void *fn, const vgrid_launch &l, int sms, int64_t total, 
     const int blocks = persistent_blocks(fn, l, sms, total);
     void *args[] = {&a};
     VG_CUDA(cudaLaunchKernel(fn, dim3(blocks), dim3(l.block), args, 0, s));
+    vg::count_launches(1);
     return VGRID_OK;
 }
 
@@ -690,6 +725,41 @@ int locate_fp32(vgrid_t *g, const void *fn, const vgrid_launch &l, int64_t N, co
     VG_CUDA(vg::launch_locate_ordered(g->d_desc, g->d_set, 1, N, ord, g->sms, s));
     VG_CUDA(vg::launch_order(ord, N, g->sms, s));
     *order = g->d_order;
+    return VGRID_OK;
+}
+
+// tau (and status) of n device-resident rays on s; the counters restart
+// only if reset_stats
+int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t n, int fp64, void *tau,
+                    int32_t *status, bool reset_stats, cudaStream_t s) {
+    int rc = ensure_start(g, n);
+    if (rc) return rc;
+    vgrid_launch L = g->launch;
+    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+    const vg::KernelSet &ks = kernels(L.lanes_per_ray);
+    RaySetDev set{origin, dir, tau, status, g->d_start, n, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, reset_stats ? g->d_stats : nullptr, s));
+    mark(g, 0, 0, s);
+    const int32_t *order = nullptr;
+    if (fp64) {
+        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, n, vg::PREP_FP64, nullptr, g->sms, s));
+    } else if ((rc = locate_fp32(g, ks.fn[0][vg::MODE_TAU], L, n, &order, s))) {
+        return rc;
+    }
+    mark(g, 0, 1, s);
+    vg::TraceArgs a{};
+    a.grids = g->d_desc;
+    a.sets = g->d_set;
+    a.nsets = 1;
+    a.total = n;
+    a.queue = g->d_queue;
+    a.stats = g->d_stats;
+    a.g1 = g->hd;
+    a.s1 = set;
+    a.order = order;
+    mark(g, 1, 0, s);
+    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], L, g->sms, n, a, s))) return rc;
+    mark(g, 1, 1, s);
     return VGRID_OK;
 }
 
@@ -816,6 +886,83 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     return read_stats(g->d_stats, stats, s);
 }
 
+int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,
+                     int32_t *ray_status, int64_t chunk, vgrid_stats *stats, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (N < 0 || (N > 0 && (!origin || !dir || !tau))) return fail(VGRID_ERR_ARG, "bad rays or tau");
+    if (chunk < 0) return fail(VGRID_ERR_ARG, "negative chunk");
+    DeviceGuard dg(g->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) {
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        return VGRID_OK;
+    }
+    const int fp64 = precision == VGRID_FP64;
+    const size_t tau_sz = fp64 ? sizeof(double) : sizeof(float);
+    // one launch per chunk, and a launch lasts at least as long as its
+    // longest ray, so by default the whole call is one chunk; the copies then
+    // overlap with the traversal of the previous call
+    if (chunk == 0) chunk = N;
+    chunk = std::min(chunk, N);
+    if (chunk > g->host_cap) {
+        VG_CUDA(cudaDeviceSynchronize());  // an earlier call may still use the slots
+        free_pipe(g);
+        for (int k = 0; k < 2; k++) {
+            int rc = dmalloc(&g->d_hin[k], (size_t)(6 * chunk), g->device_bytes);
+            if (!rc) rc = dmalloc(reinterpret_cast<double **>(&g->d_hout[k]), (size_t)chunk, g->device_bytes);
+            if (!rc) rc = dmalloc(&g->d_hst[k], (size_t)chunk, g->device_bytes);
+            if (rc) {
+                free_pipe(g);
+                return rc;
+            }
+        }
+        g->host_cap = chunk;
+    }
+    if (!g->s_h2d) {
+        VG_CUDA(cudaStreamCreateWithFlags(&g->s_h2d, cudaStreamNonBlocking));
+        VG_CUDA(cudaStreamCreateWithFlags(&g->s_d2h, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; k++) {
+            VG_CUDA(cudaEventCreateWithFlags(&g->ev_in[k], cudaEventDisableTiming));
+            VG_CUDA(cudaEventCreateWithFlags(&g->ev_k[k], cudaEventDisableTiming));
+            VG_CUDA(cudaEventCreateWithFlags(&g->ev_out[k], cudaEventDisableTiming));
+        }
+    }
+    // slots alternate across chunks and calls; a slot's events order its
+    // reuse after the traversal and the copy out that last used it
+    const int64_t nchunks = (N + chunk - 1) / chunk;
+    int k = g->host_slot;
+    for (int64_t c = 0; c < nchunks; c++, k ^= 1) {
+        const int64_t first = c * chunk, n = std::min(chunk, N - first);
+        double *dO = g->d_hin[k], *dD = g->d_hin[k] + 3 * chunk;
+        // rays in once the slot's previous traversal is done
+        VG_CUDA(cudaStreamWaitEvent(g->s_h2d, g->ev_k[k], 0));
+        VG_CUDA(cudaMemcpyAsync(dO, origin + 3 * first, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, g->s_h2d));
+        VG_CUDA(cudaMemcpyAsync(dD, dir + 3 * first, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, g->s_h2d));
+        VG_CUDA(cudaEventRecord(g->ev_in[k], g->s_h2d));
+        // trace once the rays are in and the slot's previous results are out
+        VG_CUDA(cudaStreamWaitEvent(s, g->ev_in[k], 0));
+        VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k], 0));
+        int rc = trace_tau_chunk(g, dO, dD, n, fp64, g->d_hout[k], ray_status ? g->d_hst[k] : nullptr, c == 0, s);
+        if (rc) return rc;
+        VG_CUDA(cudaEventRecord(g->ev_k[k], s));
+        // results out
+        VG_CUDA(cudaStreamWaitEvent(g->s_d2h, g->ev_k[k], 0));
+        VG_CUDA(cudaMemcpyAsync(static_cast<char *>(tau) + tau_sz * first, g->d_hout[k], tau_sz * n,
+                                cudaMemcpyDeviceToHost, g->s_d2h));
+        if (ray_status)
+            VG_CUDA(cudaMemcpyAsync(ray_status + first, g->d_hst[k], sizeof(int32_t) * n, cudaMemcpyDeviceToHost,
+                                    g->s_d2h));
+        VG_CUDA(cudaEventRecord(g->ev_out[k], g->s_d2h));
+    }
+    g->host_slot = k;
+    // `stream` continues after the last copy out
+    VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k ^ 1], 0));
+    if (stats) return read_stats(g->d_stats, stats, s);  // synchronises
+    return VGRID_OK;
+}
+
 int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *dL_dtau,
                      float *dL_drho, vgrid_stream_t stream) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
@@ -849,6 +996,8 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
     mark(g, 1, 1, s);
     return rc;
 }
+
+int64_t vgrid_kernel_launches(void) { return vg::launches_so_far(); }
 
 int vgrid_enable_timing(vgrid_t *g, int enable) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
@@ -926,7 +1075,7 @@ static void free_batch(vgrid_batch_t *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *ptrs[] = {b->d_grids, b->d_sets, b->d_start, b->d_queue, b->d_stats};
+    void *ptrs[] = {b->d_grids, b->d_sets, b->d_start, b->d_queue, b->d_stats, b->d_bin, b->d_hist, b->d_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete b;
@@ -937,7 +1086,7 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
     *out = nullptr;
     if (!sets || G < 1) return fail(VGRID_ERR_ARG, "need at least one ray set");
     if (launch && (!valid_lpr(launch->lanes_per_ray) || launch->block < 32 || launch->block > 256 ||
-                   launch->block % 32 || launch->blocks_per_sm < 0))
+                   launch->block % 32 || launch->blocks_per_sm < 0 || launch->order < -1 || launch->order > 1))
         return fail(VGRID_ERR_ARG, "bad launch shape");
     const int dev = sets[0].grid ? sets[0].grid->device : 0;
     std::vector<const vgrid_t *> uniq;
@@ -973,6 +1122,19 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
         free_batch(b);
         return rc;
     }
+    // longest-first ray order over all work items of the batch, only on
+    // request: it interleaves the grids, whose blocks together may not fit
+    // in L2, where the caller's order takes them one after another
+    {
+        const bool want = b->launch.order == 1;
+        if (want && total <= INT32_MAX && total > 0) {
+            if ((rc = dmalloc(&b->d_bin, (size_t)total, bytes)) || (rc = dmalloc(&b->d_order, (size_t)total, bytes)) ||
+                (rc = dmalloc(&b->d_hist, 2 * vg::kOrderBins, bytes))) {
+                free_batch(b);
+                return rc;
+            }
+        }
+    }
     for (int32_t i = 0; i < G; i++) rs[i].start = b->d_start + rs[i].first;
     cudaError_t e = cudaMemcpy(b->d_grids, descs.data(), sizeof(GridDev) * descs.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_sets, rs.data(), sizeof(RaySetDev) * G, cudaMemcpyHostToDevice);
@@ -987,8 +1149,16 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
 static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
     RaySetDev none{};
     VG_CUDA(vg::launch_prepare(nullptr, none, b->d_queue, b->d_stats, s));
-    VG_CUDA(vg::launch_locate(b->d_grids, b->d_sets, b->G, b->total, vg::PREP_FP32, nullptr, b->sms, s));
     vg::TraceArgs a{};
+    if (b->d_order) {
+        const vg::RayOrder ord{b->d_bin, b->d_hist, b->d_order};
+        VG_CUDA(cudaMemsetAsync(b->d_hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), s));
+        VG_CUDA(vg::launch_locate_ordered(b->d_grids, b->d_sets, b->G, b->total, ord, b->sms, s));
+        VG_CUDA(vg::launch_order(ord, b->total, b->sms, s));
+        a.order = b->d_order;
+    } else {
+        VG_CUDA(vg::launch_locate(b->d_grids, b->d_sets, b->G, b->total, vg::PREP_FP32, nullptr, b->sms, s));
+    }
     a.grids = b->d_grids;
     a.sets = b->d_sets;
     a.nsets = b->G;
@@ -1006,9 +1176,12 @@ int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_s
         if (!s) return fail(VGRID_ERR_ARG, "graph replay needs a non-default stream");
         if (!b->exec) {
             VG_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const int64_t before = vg::launches_so_far();
             int rc = batch_issue(b, s);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(s, &graph);
+            b->graph_kernels = vg::launches_so_far() - before;
+            vg::count_launches(-b->graph_kernels);  // captured, not launched
             if (rc) {
                 if (graph) cudaGraphDestroy(graph);
                 return rc;
@@ -1018,6 +1191,7 @@ int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_s
             VG_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
         }
         VG_CUDA(cudaGraphLaunch(b->exec, s));
+        vg::count_launches(b->graph_kernels);
     } else {
         int rc = batch_issue(b, s);
         if (rc) return rc;

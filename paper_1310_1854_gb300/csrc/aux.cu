@@ -1,17 +1,24 @@
 // Auxiliary kernels of libvgrid: start-cell location (C(r), Sect. 2.3),
 // per-call set-up, density reordering and the prefix sum that turns
 // per-ray segment counts into offsets.
+#include <atomic>
+
 #include "kernels.h"
 #include "trace.cuh"
 
 namespace vg {
 
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
 // Write the ray-set descriptor and clear the work counter and statistics
 // (one thread; the descriptor travels as a kernel argument, so the call is
-// stream-ordered and needs no host staging buffer).
+// stream-ordered and needs no host staging buffer). stats may be NULL.
 __global__ void prepare_kernel(RaySetDev *d_set, RaySetDev set, unsigned long long *queue, StatsDev *stats) {
     if (d_set) *d_set = set;
     *queue = 0ull;
+    if (!stats) return;  // counters keep adding up (host-pipelined chunks)
     unsigned long long *s = reinterpret_cast<unsigned long long *>(stats);
     for (int i = 0; i < (int)(sizeof(StatsDev) / sizeof(unsigned long long)); i++) s[i] = 0ull;
 }
@@ -20,12 +27,14 @@ __global__ void put_grid_kernel(GridDev *d, GridDev g) { *d = g; }
 
 cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s) {
     put_grid_kernel<<<1, 1, 0, s>>>(d, g);
+    count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long long *queue, StatsDev *stats,
                            cudaStream_t s) {
     prepare_kernel<<<1, 1, 0, s>>>(d_set, set, queue, stats);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -128,6 +137,7 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
             if (m >= 0 && th > 0.0f) {
                 const float dt = th * 0.0625f;
                 float acc = 0.0f;
+#pragma unroll
                 for (int i = 0; i < 16; i++) {
                     const float t = (i + 0.5f) * dt;
                     int idx = 0;
@@ -158,6 +168,7 @@ cudaError_t launch_locate_ordered(const GridDev *grids, const RaySetDev *sets, i
     int64_t blocks = (total + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
     locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, PREP_FP32, nullptr, ord.bin, ord.hist);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -172,31 +183,49 @@ __global__ void order_scan_kernel(uint32_t *hist) {
     hist[kOrderBins + b] = sum;
 }
 
-// order[cursor[bin[w]]++] = w, one atomic per warp and bin (all lanes of a
-// warp run every iteration, so the full-mask match is safe)
-__global__ void order_scatter_kernel(const uint8_t *__restrict__ bin, int64_t total, uint32_t *cursor,
-                                     int32_t *__restrict__ order) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = warp0; base < total; base += stride) {
-        const int64_t w = base + lane;
-        const int b = w < total ? (int)__ldg(bin + w) : -1;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        uint32_t pos = 0u;
-        if (lane == leader && b >= 0) pos = atomicAdd(&cursor[b], (uint32_t)__popc(peers));
-        pos = __shfl_sync(0xffffffffu, pos, leader);
-        if (b >= 0) order[pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)w;
+// order[cursor[bin[w]]++] = w in tiles of 2048 rays per block: ranks within
+// the tile from shared-memory counters, then one global atomic per bin and
+// tile reserves the tile's range (the order inside a bin is arbitrary)
+constexpr int kScatterThreads = 256, kScatterPer = 8;
+__global__ void __launch_bounds__(kScatterThreads) order_scatter_kernel(const uint8_t *__restrict__ bin,
+                                                                        int64_t total, uint32_t *cursor,
+                                                                        int32_t *__restrict__ order) {
+    __shared__ uint32_t s_cnt[kOrderBins], s_base[kOrderBins];
+    const int64_t tile = (int64_t)kScatterThreads * kScatterPer;
+    for (int64_t t0 = blockIdx.x * tile; t0 < total; t0 += (int64_t)gridDim.x * tile) {
+        if (threadIdx.x < kOrderBins) s_cnt[threadIdx.x] = 0u;
+        __syncthreads();
+        int b[kScatterPer];
+        uint32_t r[kScatterPer];
+#pragma unroll
+        for (int j = 0; j < kScatterPer; j++) {
+            const int64_t w = t0 + (int64_t)j * kScatterThreads + threadIdx.x;
+            b[j] = w < total ? (int)__ldg(bin + w) : -1;
+            r[j] = b[j] >= 0 ? atomicAdd(&s_cnt[b[j]], 1u) : 0u;
+        }
+        __syncthreads();
+        if (threadIdx.x < kOrderBins)
+            s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&cursor[threadIdx.x], s_cnt[threadIdx.x]) : 0u;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kScatterPer; j++) {
+            const int64_t w = t0 + (int64_t)j * kScatterThreads + threadIdx.x;
+            if (b[j] >= 0) order[s_base[b[j]] + r[j]] = (int32_t)w;
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_order(const RayOrder &ord, int64_t total, int sms, cudaStream_t s) {
     if (total <= 0) return cudaSuccess;
     order_scan_kernel<<<1, kOrderBins, 0, s>>>(ord.hist);
-    int64_t blocks = (total + 255) / 256;
+    count_launches(1);
+    const int64_t tile = (int64_t)kScatterThreads * kScatterPer;
+    int64_t blocks = (total + tile - 1) / tile;
     blocks = blocks < (int64_t)sms * 8 ? blocks : (int64_t)sms * 8;
-    order_scatter_kernel<<<(unsigned)blocks, 256, 0, s>>>(ord.bin, total, ord.hist + kOrderBins, ord.order);
+    order_scatter_kernel<<<(unsigned)blocks, kScatterThreads, 0, s>>>(ord.bin, total, ord.hist + kOrderBins,
+                                                                     ord.order);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -206,6 +235,7 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
     int64_t blocks = (total + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
     locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, prep, out_caller, nullptr, nullptr);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -227,6 +257,7 @@ cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm,
     int64_t blocks = (M + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     permute_density_kernel<<<(unsigned)blocks, 256, 0, s>>>(rho_caller, perm, site, M, cells, rel);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -272,6 +303,7 @@ cudaError_t launch_enter(const double *origin, const double *dir, int64_t N, con
     int64_t blocks = (N + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
     enter_kernel<<<(unsigned)blocks, 256, 0, s>>>(origin, dir, N, gp, out);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -360,8 +392,11 @@ cudaError_t launch_exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaSt
         return cudaMemsetAsync(data, 0, sizeof(int64_t), s);
     }
     scan_tiles_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, tmp);
+    count_launches(1);
     scan_sums_kernel<<<1, kScanThreads, 0, s>>>(tmp, tiles, data + n);
+    count_launches(1);
     scan_fix_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(data, n, tmp);
+    count_launches(1);
     return cudaGetLastError();
 }
 

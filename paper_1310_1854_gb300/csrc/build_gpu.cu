@@ -401,6 +401,7 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     const int cblocks = (int)std::min<int64_t>((M + 127) / 128, 1 << 20);
     cells_kernel<<<cblocks, 128>>>(dS, M, bg, boff, bsites, box[0], box[1], box[2], box[3], box[4], box[5], eps, cnt,
                                    nbr, vol, bbox, fail);
+    count_launches(4);  // bucket count, fill, sort, cells (the scan counts its own)
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cells kernel");
     std::vector<int> hcnt(M), hfail(M), hnbr((size_t)kCap * M);
     out.vol.assign(M, 0.0);

@@ -49,6 +49,11 @@ void kernel_table_lpr4(KernelSet &k);
 void kernel_table_lpr8(KernelSet &k);
 
 // auxiliary kernels (aux.cu)
+// kernels launched by this library in this process (every launch helper
+// adds the kernels it launched)
+void count_launches(int64_t n);
+int64_t launches_so_far();
+
 cudaError_t launch_put_grid(GridDev *d, const GridDev &g, cudaStream_t s);
 cudaError_t launch_enter(const double *origin, const double *dir, int64_t N, const GridDev *gp, double *out, int sms,
                          cudaStream_t s);

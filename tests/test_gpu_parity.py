@@ -434,6 +434,43 @@ def test_ray_order_does_not_change_results():
     assert vg.get_launch()["order"] == 0
 
 
+def test_host_pipelined_trace_matches_device_trace():
+    """vgrid_trace_host (rays and results in host memory, copies overlapped
+    with the traversal) gives the tau, status and counters of vgrid_trace on
+    the same rays: one chunk, several with a ragged last one, pageable
+    buffers, the float64 form, and calls queued back to back."""
+    g, rays = gen.config2(n_rays=300_000)
+    vg = make(g)
+    N = len(rays.origin)
+    O, D = dev(rays.origin), dev(rays.dir)
+    Oh = torch.from_numpy(rays.origin).pin_memory()
+    Dh = torch.from_numpy(rays.dir).pin_memory()
+    for prec in ("fp32", "fp64"):
+        ref = vg.trace(O, D, precision=prec, status=True, stats=True)
+        rt, rs = ref.tau.cpu().numpy(), ref.status.cpu().numpy()
+        for chunk in (0, 70_001, N):
+            r = vg.trace_host(Oh, Dh, precision=prec, status=True, stats=True, chunk=chunk)
+            assert not r.tau.is_cuda
+            np.testing.assert_array_equal(r.tau.numpy(), rt)
+            np.testing.assert_array_equal(r.status.numpy(), rs)
+            for key in ("rays", "crossings", "decisions", "outside"):
+                assert r.stats[key] == ref.stats[key], (prec, chunk, key)
+    r = vg.trace_host(torch.from_numpy(rays.origin), torch.from_numpy(rays.dir), chunk=123_457)
+    t32 = vg.trace(O, D).tau.cpu().numpy()
+    np.testing.assert_array_equal(r.tau.numpy(), t32)
+    assert vg.trace_host(Oh[:0], Dh[:0]).tau.numel() == 0
+    # queued calls back to back (the next call's copies overlap this traversal)
+    half = N // 2
+    outs = [torch.empty(n, dtype=torch.float32).pin_memory() for n in (N, half, N)]
+    vg.trace_host(Oh, Dh, out_tau=outs[0], wait=False)
+    vg.trace_host(Oh[:half], Dh[:half], out_tau=outs[1], wait=False)
+    vg.trace_host(Oh, Dh, out_tau=outs[2], wait=False)
+    torch.cuda.current_stream().synchronize()
+    np.testing.assert_array_equal(outs[0].numpy(), t32)
+    np.testing.assert_array_equal(outs[1].numpy(), t32[:half])
+    np.testing.assert_array_equal(outs[2].numpy(), t32)
+
+
 def test_rays_entering_from_outside():
     g, _ = gen.config1(10)
     rng = gen.rng_for(310)
