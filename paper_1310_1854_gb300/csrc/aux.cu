@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
             out->cell = m;
             continue;
         }
-        p.cell = m;
+        // the float32 traversal starts from the cell's relative block
+        p.cell = m >= 0 ? __float_as_int(__ldg(&gp->site[m]).w) : m;
         // distance to the wall ahead (Eq. 5 for the walls the ray faces), as
         // a float pair: q1 = n/k rounded, the exact remainder n - q1 k by
         // fma, then q2 = remainder / k (relative error a few 2^-48)

@@ -89,7 +89,8 @@ struct GridDev {
 // float64 set-up is cheap) and read once by the traversal kernel when the
 // ray starts (64 bytes).
 struct RayPrep {
-    int32_t cell;             // start cell (internal); -1 outside the box, -2 direction not unit
+    int32_t cell;             // start cell: internal id (float64 form), offset of its relative
+                              // block (float32 form); -1 outside the box, -2 direction not unit
     int32_t wall;             // wall the ray leaves through (Eq. 5), -1..-6
     float tmax_hi, tmax_lo;   // distance to that wall, as a float pair
     float r0_hi[3], r0_lo[3]; // origin as float pairs

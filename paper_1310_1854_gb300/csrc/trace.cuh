@@ -561,12 +561,15 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             }
             status = m == -2 ? RAY_BAD_DIR : (m < 0 ? RAY_OUTSIDE : RAY_OK);
             if (status == RAY_OK) {
-                const float4 q = __ldg(&h.site[m]);
-                pmx = q.x;
-                pmy = q.y;
-                pmz = q.z;
-                B = rec_w(q);
-                if (FP64) B = rec_w(__ldg(h.rel + B + 1));  // absolute block of the cell
+                if (FP64) {
+                    const float4 q = __ldg(&h.site[m]);
+                    pmx = q.x;
+                    pmy = q.y;
+                    pmz = q.z;
+                    B = rec_w(__ldg(h.rel + rec_w(q) + 1));  // absolute block of the cell
+                } else {
+                    B = m;  // relative block; the site comes with its header
+                }
             }
             if (status != RAY_OK) {
                 if (gl == 0) {
