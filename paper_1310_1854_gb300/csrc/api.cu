@@ -284,7 +284,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     // F), then one record per neighbour (site of the neighbour, its A) or
     // wall. Relative cell blocks (offsets F, even): (site, record count),
     // (caller id, rho = 1, N1max, A), then one record per cell neighbour
-    // (fl(p_j - p_i) in float32, its F), NaN-padded to a multiple of four
+    // (fl(p_j - p_i) in float32, its F), NaN-padded to an even count of
     // records (at least four). N1max bounds |fl(p_j - p_i)|_1 over the
     // records from above.
     std::vector<int64_t> boffs(M + 1, 0), foffs(M + 1, 0);
@@ -293,7 +293,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
         for (int64_t q = b; q < e; q++) ncell[i] += g->cells.idx[q] >= 0;
         boffs[i + 1] = boffs[i] + 1 + (e - b);
-        foffs[i + 1] = foffs[i] + 2 + std::max<int64_t>(4, (ncell[i] + 3) & ~(int64_t)3);
+        foffs[i + 1] = foffs[i] + 2 + std::max<int64_t>(4, (ncell[i] + 1) & ~(int64_t)1);
     }
     if (boffs[M] + 8 >= ((int64_t)1 << 31) || foffs[M] + 8 >= ((int64_t)1 << 31)) {
         delete g;

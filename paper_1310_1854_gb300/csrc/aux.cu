@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         for (int q = 0; q < 4; q++) dst[q] = src[q];
         if (bin) {
             // estimated crossings: (sites per volume)^(1/3) integrated along
-            // the in-box segment [0, t_max] with 16 midpoint samples
+            // the in-box segment [0, t_max] with 8 midpoint samples
             int b = 0;
             if (m >= 0 && th > 0.0f) {
-                const float dt = th * 0.0625f;
+                const float dt = th * 0.125f;
                 float acc = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 16; i++) {
+                for (int i = 0; i < 8; i++) {
                     const float t = (i + 0.5f) * dt;
                     int idx = 0;
 #pragma unroll

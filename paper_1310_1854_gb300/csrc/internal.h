@@ -52,7 +52,7 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
 //          (even) with (x, y, z of p_i, bits of the record count c4) and
 //          (bits of the caller's id, rho, N1max, bits of A_i), followed by c4
 //          records: (fl(p_j - p_i) as float32, bits of F_j) for every cell
-//          neighbour j, then NaN records up to c4 = max(4, multiple of 4).
+//          neighbour j, then NaN records up to c4 = max(4, an even count).
 //          N1max bounds |fl(p_j - p_i)|_1 over the records from above.
 // site[i]  float4 (x, y, z, bits of F_i): positions for C(r) and ray starts.
 // perm[i]  caller's id of internal cell i.

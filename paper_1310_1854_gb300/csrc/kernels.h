@@ -64,7 +64,7 @@ enum { PREP_CELL32 = 0, PREP_FP32 = 1, PREP_FP64 = 2, PREP_CELL64 = 3 };
 // Longest-predicted-first ray order. A persistent launch ends when its last
 // ray does, so long rays handed out late leave most lanes idle at the end;
 // handing the longest out first fixes that. The start-cell kernel estimates
-// each ray's crossings (sum of the coarse (sites per volume)^(1/3) grid at 16
+// each ray's crossings (sum of the coarse (sites per volume)^(1/3) grid at 8
 // points of its in-box segment, times the segment length) and counts rays
 // per quarter-octave bin of the estimate; a scan and a scatter turn the bins
 // into the permutation the traversal takes its rays from.

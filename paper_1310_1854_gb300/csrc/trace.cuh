@@ -15,7 +15,7 @@
 //  * relative (float32 form): cell i owns a run at F_i: (x, y, z of p_i,
 //    record count), (caller's id, rho, N1max, A_i), then one record per cell
 //    neighbour (n~ = fl(p_j - p_i), the neighbour's offset F_j), padded with
-//    NaN records to a multiple of four. Walls are not records there: the
+//    NaN records to an even count of at least four. Walls are not records there: the
 //    wall ahead is one candidate from the ray's start record.
 //
 // Two arithmetic forms of the exit search (Sect. 2.2, steps 1-3, Eq. 1-5):
@@ -373,7 +373,7 @@ __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float 
     c.L1 = fminf(c.L1, lower);
 }
 
-// Records recs[1..cnt] (cnt a multiple of four, at least four); lane gl of
+// Records recs[1..cnt] (cnt even, at least four); lane gl of
 // the group takes records gl+1, gl+1+LPR, ... four at a time. With one lane
 // per ray the caller loads the first four (f0..f3) together with the header,
 // so they do not wait for the count, and no position is ever past the count.
@@ -389,10 +389,12 @@ __device__ __forceinline__ void exit32(const float4 *recs, int cnt, float4 f0, f
         consider32(2, true, f1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
         consider32(3, true, f2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
         consider32(4, true, f3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        const float nan = __int_as_float(0x7fc00000);
         for (int p = 5; p <= cnt; p += 4) {
-            float4 q0, q1, q2, q3;
+            // the last group may hold one pair: the other reads as NaN records
+            float4 q0, q1, q2 = make_float4(nan, nan, nan, nan), q3 = q2;
             ldg_pair(recs + p, q0, q1);
-            ldg_pair(recs + p + 2, q2, q3);
+            if (p + 2 <= cnt) ldg_pair(recs + p + 2, q2, q3);
             consider32(p, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
             consider32(p + 1, true, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
             consider32(p + 2, true, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
