@@ -127,14 +127,14 @@ typedef struct {
     int32_t block;              /* threads per block (multiple of 32, 32..256; default 128) */
     int32_t blocks_per_sm;      /* persistent blocks per SM; 0 = as many as fit */
     int32_t fp64_lanes_per_ray; /* lanes per ray of the float64 form; 0 = lanes_per_ray (default 4) */
-    int32_t order;              /* order in which the float32 traversal takes the rays:
+    int32_t order;              /* order in which the traversal takes the rays:
                                    1 = longest estimated path first (crossings estimated
                                    from a coarse site-density grid along each ray),
                                    -1 = the caller's order, 0 (default) = longest first
                                    when there are at least two rays per resident lane.
                                    Results do not depend on it; the time does: a
                                    persistent launch lasts until its last ray ends.
-                                   Used by vgrid_trace (float32), vgrid_trace_host,
+                                   Used by vgrid_trace (both forms), vgrid_trace_host,
                                    vgrid_trace_grad and vgrid_interact; a batch orders
                                    all its work items together only with order = 1
                                    (that interleaves its grids, which then share L2). */

@@ -709,20 +709,23 @@ int64_t resident_lanes(vgrid_t *g, const void *fn, const vgrid_launch &l) {
     return (int64_t)persistent_blocks(fn, l, g->sms, INT64_MAX / 16) * l.block / l.lanes_per_ray;
 }
 
-// float32 start records for the set in g->d_set; with the ray order (see
-// vgrid_launch.order) also the permutation, which goes to *order
-int locate_fp32(vgrid_t *g, const void *fn, const vgrid_launch &l, int64_t N, const int32_t **order, cudaStream_t s) {
+// start records (float32 form, or float64 with fp64) for the set in
+// g->d_set; with the ray order (see vgrid_launch.order) also the
+// permutation, which goes to *order
+int locate_start(vgrid_t *g, const void *fn, const vgrid_launch &l, int64_t N, const int32_t **order, cudaStream_t s,
+                bool fp64 = false) {
     *order = nullptr;
+    const int prep = fp64 ? vg::PREP_FP64 : vg::PREP_FP32;
     const bool want = l.order == 1 || (l.order == 0 && N >= 2 * resident_lanes(g, fn, l));
     if (!want || N > INT32_MAX) {
-        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP32, nullptr, g->sms, s));
+        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, prep, nullptr, g->sms, s));
         return VGRID_OK;
     }
     int rc = ensure_order(g, N);
     if (rc) return rc;
     const vg::RayOrder ord{g->d_bin, g->d_hist, g->d_order};
     VG_CUDA(cudaMemsetAsync(g->d_hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), s));
-    VG_CUDA(vg::launch_locate_ordered(g->d_desc, g->d_set, 1, N, ord, g->sms, s));
+    VG_CUDA(vg::launch_locate_ordered(g->d_desc, g->d_set, 1, N, ord, prep, g->sms, s));
     VG_CUDA(vg::launch_order(ord, N, g->sms, s));
     *order = g->d_order;
     return VGRID_OK;
@@ -741,11 +744,7 @@ int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, reset_stats ? g->d_stats : nullptr, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
-    if (fp64) {
-        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, n, vg::PREP_FP64, nullptr, g->sms, s));
-    } else if ((rc = locate_fp32(g, ks.fn[0][vg::MODE_TAU], L, n, &order, s))) {
-        return rc;
-    }
+    if ((rc = locate_start(g, ks.fn[fp64][vg::MODE_TAU], L, n, &order, s, fp64 != 0))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.grids = g->d_desc;
@@ -839,11 +838,9 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
-    if (fp64) {
-        VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N, vg::PREP_FP64, nullptr, g->sms, s));
-    } else {
-        const void *fn = ks.fn[0][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_COUNT];
-        if ((rc = locate_fp32(g, fn, L, N, &order, s))) return rc;
+    {
+        const void *fn = ks.fn[fp64][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_COUNT];
+        if ((rc = locate_start(g, fn, L, N, &order, s, fp64 != 0))) return rc;
     }
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
@@ -977,7 +974,7 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
-    if ((rc = locate_fp32(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_GRAD], g->launch, N, &order, s))) return rc;
+    if ((rc = locate_start(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_GRAD], g->launch, N, &order, s))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.order = order;
@@ -1044,7 +1041,7 @@ int vgrid_interact(vgrid_t *g, const double *origin, const double *dir, int64_t 
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
-    if ((rc = locate_fp32(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_INTERACT], g->launch, N, &order, s))) return rc;
+    if ((rc = locate_start(g, kernels(g->launch.lanes_per_ray).fn[0][vg::MODE_INTERACT], g->launch, N, &order, s))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.order = order;
@@ -1153,7 +1150,7 @@ static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
     if (b->d_order) {
         const vg::RayOrder ord{b->d_bin, b->d_hist, b->d_order};
         VG_CUDA(cudaMemsetAsync(b->d_hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), s));
-        VG_CUDA(vg::launch_locate_ordered(b->d_grids, b->d_sets, b->G, b->total, ord, b->sms, s));
+        VG_CUDA(vg::launch_locate_ordered(b->d_grids, b->d_sets, b->G, b->total, ord, vg::PREP_FP32, b->sms, s));
         VG_CUDA(vg::launch_order(ord, b->total, b->sms, s));
         a.order = b->d_order;
     } else {

@@ -89,12 +89,13 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
             unit = fabs(kk - 1.0) <= 2.000001e-6;
         }
         if (!unit) m = -2;
-        if (prep == PREP_FP64) {
+        const bool fp64 = prep == PREP_FP64;  // the float64 form needs the cell only
+        if (fp64 && !bin) {
             out->cell = m;
             continue;
         }
         // the float32 traversal starts from the cell's relative block
-        p.cell = m >= 0 ? __float_as_int(__ldg(&gp->site[m]).w) : m;
+        p.cell = m >= 0 && !fp64 ? __float_as_int(__ldg(&gp->site[m]).w) : m;
         // distance to the wall ahead (Eq. 5 for the walls the ray faces), as
         // a float pair: q1 = n/k rounded, the exact remainder n - q1 k by
         // fma, then q2 = remainder / k (relative error a few 2^-48)
@@ -128,9 +129,13 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         p.wall = wid;
         p.tmax_hi = th;
         p.tmax_lo = tl;
-        const float4 *src = reinterpret_cast<const float4 *>(&p);
-        float4 *dst = reinterpret_cast<float4 *>(out);
-        for (int q = 0; q < 4; q++) dst[q] = src[q];
+        if (fp64) {
+            out->cell = m;
+        } else {
+            const float4 *src = reinterpret_cast<const float4 *>(&p);
+            float4 *dst = reinterpret_cast<float4 *>(out);
+            for (int q = 0; q < 4; q++) dst[q] = src[q];
+        }
         if (bin) {
             // estimated crossings: (sites per volume)^(1/3) integrated along
             // the in-box segment [0, t_max] with 8 midpoint samples
@@ -164,11 +169,11 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
 }
 
 cudaError_t launch_locate_ordered(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total,
-                                  const RayOrder &ord, int sms, cudaStream_t s) {
+                                  const RayOrder &ord, int prep, int sms, cudaStream_t s) {
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + 255) / 256;
     blocks = blocks < (int64_t)sms * 16 ? blocks : (int64_t)sms * 16;
-    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, PREP_FP32, nullptr, ord.bin, ord.hist);
+    locate_kernel<<<(unsigned)blocks, 256, 0, s>>>(grids, sets, nsets, total, prep, nullptr, ord.bin, ord.hist);
     count_launches(1);
     return cudaGetLastError();
 }

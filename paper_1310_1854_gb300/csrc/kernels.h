@@ -74,9 +74,9 @@ struct RayOrder {
     uint32_t *hist;   // kOrderBins counts, then kOrderBins cursors (zeroed by the caller)
     int32_t *order;   // queue position -> ray
 };
-// the float32 start records (PREP_FP32) plus the bins and their counts
+// the start records (PREP_FP32 or PREP_FP64) plus the bins and their counts
 cudaError_t launch_locate_ordered(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total,
-                                  const RayOrder &ord, int sms, cudaStream_t s);
+                                  const RayOrder &ord, int prep, int sms, cudaStream_t s);
 // bins -> permutation (scan of the counts, longest bin first, and scatter)
 cudaError_t launch_order(const RayOrder &ord, int64_t total, int sms, cudaStream_t s);
 cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets, int64_t total, int prep,

@@ -405,9 +405,10 @@ def test_interaction_matches_oracle():
 
 def test_ray_order_does_not_change_results():
     """The longest-first ray order (vgrid_launch.order) changes which lane
-    takes which ray, not what a ray computes: tau, segment lists and
-    interaction cells/distances are bit-identical to the caller's order, and
-    the gradient agrees up to the order of its float32 atomic sums."""
+    takes which ray, not what a ray computes: tau (both forms), segment
+    lists and interaction cells/distances are bit-identical to the caller's
+    order, and the gradient agrees up to the order of its float32 atomic
+    sums."""
     g, rays = gen.config2(n_rays=300_000)
     vg = make(g)
     O, D = dev(rays.origin), dev(rays.dir)
@@ -422,10 +423,12 @@ def test_ray_order_does_not_change_results():
         c, s_, _ = vg.interact(O, D, tau_int)
         gr = torch.zeros(len(g.sites), dtype=torch.float32, device="cuda")
         vg.trace_grad(O, D, dL, gr)
+        t64 = vg.trace(O, D, precision="fp64")
         out[order] = (t.tau.cpu().numpy(), t.stats, sg.seg_off.cpu().numpy(), sg.seg_cell.cpu().numpy(),
-                      sg.seg_len.cpu().numpy(), c.cpu().numpy(), s_.cpu().numpy(), gr.cpu().numpy())
+                      sg.seg_len.cpu().numpy(), c.cpu().numpy(), s_.cpu().numpy(), gr.cpu().numpy(),
+                      t64.tau.cpu().numpy())
     a, b = out[-1], out[1]
-    for k in (0, 2, 3, 4, 5, 6):
+    for k in (0, 2, 3, 4, 5, 6, 8):
         np.testing.assert_array_equal(a[k], b[k])
     for key in ("rays", "crossings", "decisions", "rechecks"):
         assert a[1][key] == b[1][key]
