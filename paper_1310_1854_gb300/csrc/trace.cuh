@@ -547,8 +547,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     }
                 }
             } else {
-                const float4 *p4 = reinterpret_cast<const float4 *>(pr);
-                const float4 a0 = __ldg(p4), a1 = __ldg(p4 + 1), a2 = __ldg(p4 + 2), a3 = __ldg(p4 + 3);
+                const float4 *p4 = reinterpret_cast<const float4 *>(pr);  // 64-byte aligned
+                float4 a0, a1, a2, a3;
+                ldg_pair(p4, a0, a1);
+                ldg_pair(p4 + 2, a2, a3);
                 m = __float_as_int(a0.x);
                 wall = __float_as_int(a0.y);
                 tmh = a0.z;

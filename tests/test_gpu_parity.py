@@ -130,6 +130,32 @@ def test_locate_parity():
         np.testing.assert_array_equal(out, ref)
 
 
+def test_locate_on_block_faces():
+    """C(r) for points on and next to the faces of the block grid: the
+    block index comes from float32 pairs, and the block lists are padded to
+    cover its rounding, so the nearest site must still be found."""
+    g = gen.make_disk_grid(20_000, 111)
+    vg = make(g)
+    info = vg.info()
+    lo, hi = np.asarray(g.box[:3]), np.asarray(g.box[3:])
+    dim = np.asarray(info["block_dim"])
+    rng = gen.rng_for(112)
+    n = 3000
+    P = lo + rng.random((n, 3)) * (hi - lo)
+    axis = rng.integers(0, 3, n)
+    k = rng.integers(1, dim[axis])
+    face = lo[axis] + k * (hi[axis] - lo[axis]) / dim[axis]
+    ext = (hi - lo)[axis]
+    delta = rng.choice(np.array([0.0, 1e-7, -1e-7, 3e-8, -3e-8, 1e-9, -1e-9]), n) * ext
+    P[np.arange(n), axis] = np.clip(face + delta, lo[axis], hi[axis])
+    P = np.concatenate([P, np.nextafter(P, np.inf), np.nextafter(P, -np.inf)])
+    P = np.clip(P, lo, hi)
+    ref = oracle.locate(g.sites, g.box, P)
+    for prec in ("fp32", "fp64"):
+        out = vg.locate(dev(P), precision=prec).cpu().numpy()
+        np.testing.assert_array_equal(out, ref)
+
+
 def test_full_size_config2_sampled():
     """10^5-site disk, 10^6 rays, the benchmark's launch shape; 200 rays
     compared with the oracle over all sites."""
