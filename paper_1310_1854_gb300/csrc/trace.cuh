@@ -4,8 +4,11 @@
 // Work mapping: a persistent grid of warps; each warp is split into groups of
 // LPR lanes, one ray per group. A group takes a new ray from a global counter
 // as soon as its ray ends, so rays of very different length do not leave
-// lanes idle. Inside a crossing the group's lanes stride over the current
-// cell's block and reduce the exit with shuffles.
+// lanes idle; with a ray order the counter indexes a permutation that hands
+// out the rays with the longest estimated paths first, so that the launch
+// does not end waiting for a few long rays started late. Inside a crossing
+// the group's lanes stride over the current cell's block (32-byte record
+// pairs, one 256-bit load each) and reduce the exit with shuffles.
 //
 // Cell blocks, in two forms; each crossing reads one contiguous block.
 //  * absolute (float64 form, rechecks): cell i owns a run of float4 at A_i:
@@ -15,8 +18,8 @@
 //  * relative (float32 form): cell i owns a run at F_i: (x, y, z of p_i,
 //    record count), (caller's id, rho, N1max, A_i), then one record per cell
 //    neighbour (n~ = fl(p_j - p_i), the neighbour's offset F_j), padded with
-//    NaN records to an even count of at least four. Walls are not records there: the
-//    wall ahead is one candidate from the ray's start record.
+//    NaN records to an even count of at least four. Walls are not records
+//    there: the wall ahead is one candidate from the ray's start record.
 //
 // Two arithmetic forms of the exit search (Sect. 2.2, steps 1-3, Eq. 1-5):
 //  * float64: Eq. 4 and Eq. 5 evaluated as written, in the same operation

@@ -569,3 +569,26 @@ def test_gpu_cell_construction_matches_host(kind):
     O, D = dev(rays.origin), dev(rays.dir)
     np.testing.assert_array_equal(a.trace(O, D, precision="fp32").tau.cpu().numpy(),
                                   dev_.trace(O, D, precision="fp32").tau.cpu().numpy())
+
+
+def test_autotune_applies_and_caches(tmp_path):
+    """The launch-shape tuner times its candidate shapes on the GPU, applies
+    the fastest, caches it, and a later call takes it from the cache; tau
+    does not depend on the shape."""
+    from paper_1310_1854_gb300 import tune
+    g, rays = gen.config2(n_rays=100_000)
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    ref = vg.trace(O, D).tau.cpu().numpy()
+    path = str(tmp_path / "tune.json")
+    space = ((1, 128, 0), (2, 128, 0), (1, 64, 0))
+    r = tune.autotune(vg, O, D, sample=50_000, space=space, path=path)
+    assert not r["cached"] and (r["lanes_per_ray"], r["block"], r["blocks_per_sm"]) in space
+    assert len(r["table"]) == len(space) and all(v > 0 for v in r["table"].values())
+    L = vg.get_launch()
+    assert (L["lanes_per_ray"], L["block"], L["blocks_per_sm"]) == (r["lanes_per_ray"], r["block"], r["blocks_per_sm"])
+    np.testing.assert_array_equal(vg.trace(O, D).tau.cpu().numpy(), ref)
+    vg.set_launch()
+    r2 = tune.autotune(vg, O, D, sample=50_000, space=space, path=path)
+    assert r2["cached"] and r2["lanes_per_ray"] == r["lanes_per_ray"]
+    assert vg.get_launch()["lanes_per_ray"] == r["lanes_per_ray"]
