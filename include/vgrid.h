@@ -226,7 +226,9 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  * cut at max_steps, after writing every output; in tau mode without stats
  * the call does not synchronise and those rays show only in ray_status.
  * The first call with more rays than any earlier call on this grid
- * allocates a larger work buffer (N int32).
+ * allocates larger work buffers: a 64-byte start record per ray, and with
+ * the ray order (vgrid_launch.order) 5 more bytes per ray; segment mode adds
+ * the scan's scratch.
  */
 int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, int output,
                 void *tau, int64_t *seg_off, int32_t *seg_cell, void *seg_len, int64_t seg_capacity,
