@@ -471,6 +471,14 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     hd.blk_off = g->d_blk_off;
     hd.blk_rec = g->d_blk_rec;
     hd.dens = g->d_dens;
+    {
+        // ray order: by length alone while the relative blocks fit in half of
+        // L2, else by (length, start-cell range) to keep the rays in flight
+        // on one part of the grid
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device);
+        hd.ospatial = (double)nrel * sizeof(float4) > 0.5 * (double)l2 ? 16 : 1;
+    }
     double dmax = 0;
     for (int c = 0; c < 3; c++) {
         hd.lo[c] = bbox[c];

@@ -155,7 +155,10 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
                     }
                     acc += __ldg(gp->dens + idx);
                 }
-                b = max(0, min(kOrderBins - 1, __float2int_rz(4.0f * __log2f(1.0f + acc * dt))));
+                const int S = max(1, gp->ospatial), NL = kOrderBins / S;
+                const float Q = S == 1 ? 4.0f : 2.0f;  // bins per octave of the estimate
+                const int lb = max(0, min(NL - 1, __float2int_rz(Q * __log2f(1.0f + acc * dt))));
+                b = lb * S + (S > 1 ? (int)(((int64_t)m * S) / gp->M) : 0);
             }
             bin[w] = (uint8_t)b;
             atomicAdd(&s_hist[b], 1u);

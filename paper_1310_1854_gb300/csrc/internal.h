@@ -75,6 +75,7 @@ struct GridDev {
     const float *dens;                 // coarse grid of (sites per unit volume)^(1/3), for the ray order
     int32_t ddim[3];                   // its cells per axis
     float dscale[3];                   // its cells per unit length
+    int32_t ospatial;                  // ray order: start-cell ranges per length bin (1: length only)
     int32_t bdim[3];
     int32_t M;
     float kappa;

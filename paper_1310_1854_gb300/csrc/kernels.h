@@ -66,9 +66,13 @@ enum { PREP_CELL32 = 0, PREP_FP32 = 1, PREP_FP64 = 2, PREP_CELL64 = 3 };
 // handing the longest out first fixes that. The start-cell kernel estimates
 // each ray's crossings (sum of the coarse (sites per volume)^(1/3) grid at 8
 // points of its in-box segment, times the segment length) and counts rays
-// per quarter-octave bin of the estimate; a scan and a scatter turn the bins
-// into the permutation the traversal takes its rays from.
-constexpr int kOrderBins = 64;
+// per bin; a scan and a scatter turn the bins into the permutation the
+// traversal takes its rays from, highest bin first. For a grid whose blocks
+// fit in L2 the bin is the quarter-octave of the estimate; for a larger one
+// it is (half-octave of the estimate, one of 16 ranges of the start cell's
+// Morton index), so that the rays in flight at a time start in one part of
+// the grid and share more of L2.
+constexpr int kOrderBins = 256;
 struct RayOrder {
     uint8_t *bin;     // per ray
     uint32_t *hist;   // kOrderBins counts, then kOrderBins cursors (zeroed by the caller)
