@@ -500,6 +500,42 @@ def test_host_pipelined_trace_matches_device_trace():
     np.testing.assert_array_equal(outs[2].numpy(), t32)
 
 
+def test_ray_order_edge_cases():
+    """The ray order forced on for inputs it was not built for: one ray, a
+    handful, rays outside the box, non-unit directions; statuses, tau and
+    segments equal the caller's order (both forms), and the host-resident
+    call agrees."""
+    from paper_1310_1854_gb300 import _lib
+    g, rays = gen.config1(2000)
+    vg = make(g)
+    rng = gen.rng_for(320)
+    o = np.concatenate([rays.origin, rng.uniform(1.5, 3.0, (50, 3)), rays.origin[:30]])
+    d = np.concatenate([rays.dir, rays.dir[:50], rays.dir[:30] * 1.5])  # last 30: not unit
+    for n in (1, 7, 120, len(o)):
+        O, D = dev(o[:n]), dev(d[:n])
+        res = {}
+        for order in (-1, 1):
+            vg.set_launch(order=order)
+            t32 = vg.trace(O, D, precision="fp32", status=True)
+            t64 = vg.trace(O, D, precision="fp64", status=True)
+            m = min(n, 2050)  # segment mode reports non-unit directions as an error
+            sg = vg.trace(O[:m], D[:m], precision="fp32", segments=True)
+            res[order] = [t32.tau.cpu().numpy(), t32.status.cpu().numpy(), t64.tau.cpu().numpy(),
+                          t64.status.cpu().numpy(), sg.seg_off.cpu().numpy(), sg.seg_cell.cpu().numpy(),
+                          sg.seg_len.cpu().numpy()]
+            if order == 1:
+                h = vg.trace_host(torch.from_numpy(o[:n]), torch.from_numpy(d[:n]), status=True)
+                np.testing.assert_array_equal(h.tau.numpy(), res[1][0])
+                np.testing.assert_array_equal(h.status.numpy(), res[1][1])
+        for a, b in zip(res[-1], res[1]):
+            np.testing.assert_array_equal(a, b)
+        st = res[1][1]
+        if n == len(o):
+            assert np.all(st[2000:2050] == _lib.RAY_OUTSIDE) and np.all(st[2050:] == _lib.RAY_BAD_DIR)
+            assert np.all(res[1][0][2000:] == 0.0)
+    vg.set_launch()
+
+
 def test_rays_entering_from_outside():
     g, _ = gen.config1(10)
     rng = gen.rng_for(310)
