@@ -119,6 +119,9 @@ typedef struct {
     double build_seconds;  /* host time of vgrid_create */
     int64_t device_bytes;  /* device memory held by the grid */
     int64_t host_fallback_cells; /* gpu_build: cells rebuilt on the host */
+    double phase_seconds[6];   /* vgrid_create by phase: checks and duplicates,
+                                  cell order, cells (host or GPU), block lists,
+                                  device layout, copies to the device */
 } vgrid_info_t;
 
 /* launch shape of the traversal kernels */

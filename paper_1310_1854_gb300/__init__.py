@@ -112,7 +112,7 @@ class VoronoiGrid:
         check(load().vgrid_info(self._h, ctypes.byref(i)))
         return {"M": i.M, "nnz": i.nnz, "block_entries": i.block_entries, "block_dim": list(i.block_dim),
                 "box": list(i.box), "build_seconds": i.build_seconds, "device_bytes": i.device_bytes,
-                "host_fallback_cells": i.host_fallback_cells}
+                "host_fallback_cells": i.host_fallback_cells, "phase_seconds": list(i.phase_seconds)}
 
     def neighbors(self):
         """CSR (off int64[M+1], idx int32) in the caller's ids, walls -1..-6."""

@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("M", c_int64), ("nnz", c_int64), ("block_entries", c_int64), ("block_dim", c_int32 * 3),
                 ("box", c_double * 6), ("build_seconds", c_double), ("device_bytes", c_int64),
-                ("host_fallback_cells", c_int64)]
+                ("host_fallback_cells", c_int64), ("phase_seconds", c_double * 6)]
 
 
 class Launch(ctypes.Structure):

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 #include <limits>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -118,6 +119,7 @@ struct vgrid {
     cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
     cudaEvent_t ev_in[2] = {}, ev_k[2] = {}, ev_out[2] = {};
     double build_seconds = 0;
+    double phase_seconds[6] = {0, 0, 0, 0, 0, 0};
     int64_t device_bytes = 0;
     int64_t host_fallback_cells = 0;
     // optional event record: {locate start, locate end} or {trace start, trace end}
@@ -236,7 +238,25 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         for (int c = 0; c < 3; c++)
             if (!(S[3 * i + c] >= bbox[c] && S[3 * i + c] <= bbox[3 + c]))
                 return fail(VGRID_ERR_OUTSIDE, "site " + std::to_string(i) + " lies outside the box");
-    {
+    // duplicates: coinciding sites share a Morton code, so with the Morton
+    // order they sit in one run of equal codes (runs are a few sites long);
+    // without it, a lexicographic sort puts them next to each other
+    std::vector<int32_t> perm;
+    std::vector<uint64_t> codes;
+    if (o.reorder) {
+        vg::morton_order(S.data(), M, bbox, perm, &codes, o.threads);
+        for (int64_t r0 = 0; r0 < M;) {
+            int64_t r1 = r0 + 1;
+            while (r1 < M && codes[r1] == codes[r0]) r1++;
+            for (int64_t a = r0; a < r1; a++)
+                for (int64_t b = a + 1; b < r1; b++)
+                    if (std::equal(&S[3 * (int64_t)perm[a]], &S[3 * (int64_t)perm[a]] + 3, &S[3 * (int64_t)perm[b]]))
+                        return fail(VGRID_ERR_DUP_SITE, "sites " + std::to_string(std::min(perm[a], perm[b])) +
+                                                            " and " + std::to_string(std::max(perm[a], perm[b])) +
+                                                            " coincide");
+            r0 = r1;
+        }
+    } else {
         std::vector<int32_t> ord(M);
         for (int64_t i = 0; i < M; i++) ord[i] = (int32_t)i;
         std::sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
@@ -247,22 +267,29 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
             if (std::equal(&S[3 * (int64_t)ord[i]], &S[3 * (int64_t)ord[i]] + 3, &S[3 * (int64_t)ord[i - 1]]))
                 return fail(VGRID_ERR_DUP_SITE, "sites " + std::to_string(ord[i - 1]) + " and " +
                                                     std::to_string(ord[i]) + " coincide");
+        perm.resize(M);
+        for (int64_t i = 0; i < M; i++) perm[i] = (int32_t)i;
     }
 
+    const auto t_checked = std::chrono::steady_clock::now();
     vgrid_t *g = new vgrid();
     g->M = M;
     g->opts = o;
-    if (o.reorder) vg::morton_order(S.data(), M, bbox, g->perm);
-    else {
-        g->perm.resize(M);
-        for (int64_t i = 0; i < M; i++) g->perm[i] = (int32_t)i;
-    }
+    auto lap = [&](int k, std::chrono::steady_clock::time_point &since) {
+        const auto now = std::chrono::steady_clock::now();
+        g->phase_seconds[k] = std::chrono::duration<double>(now - since).count();
+        since = now;
+    };
+    auto t_lap = t_checked;
+    g->phase_seconds[0] = std::chrono::duration<double>(t_checked - t0).count();
+    g->perm.swap(perm);
     g->inv.resize(M);
     for (int64_t i = 0; i < M; i++) g->inv[g->perm[i]] = (int32_t)i;
     std::vector<double> Si(3 * M);
     for (int64_t i = 0; i < M; i++)
         for (int c = 0; c < 3; c++) Si[3 * i + c] = S[3 * (int64_t)g->perm[i] + c];
 
+    lap(1, t_lap);
     std::string err;
     if (o.gpu_build && o.host_only) {
         delete g;
@@ -274,7 +301,9 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         delete g;
         return fail(o.gpu_build ? VGRID_ERR_CUDA : VGRID_ERR_BUILD, err);
     }
-    vg::build_blocks(bbox, g->cells.bbox, M, o.blocks_per_site, g->blocks);
+    lap(2, t_lap);
+    vg::build_blocks(bbox, g->cells.bbox, M, o.blocks_per_site, g->blocks, o.threads);
+    lap(3, t_lap);
     if ((int64_t)(g->blocks.idx.size() + g->blocks.off.size()) + 2 >= ((int64_t)1 << 31)) {  // with the padding
         delete g;
         return fail(VGRID_ERR_NOMEM, "block lists exceed 2^31 entries; lower blocks_per_site");
@@ -289,9 +318,12 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     // records from above.
     std::vector<int64_t> boffs(M + 1, 0), foffs(M + 1, 0);
     std::vector<int32_t> ncell(M, 0);
+    vg::parallel_for(M, o.threads, 1 << 14, [&](int64_t b0, int64_t e0) {
+        for (int64_t i = b0; i < e0; i++)
+            for (int64_t q = g->cells.off[i]; q < g->cells.off[i + 1]; q++) ncell[i] += g->cells.idx[q] >= 0;
+    });
     for (int64_t i = 0; i < M; i++) {
         const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
-        for (int64_t q = b; q < e; q++) ncell[i] += g->cells.idx[q] >= 0;
         boffs[i + 1] = boffs[i] + 1 + (e - b);
         foffs[i + 1] = foffs[i] + 2 + std::max<int64_t>(4, (ncell[i] + 1) & ~(int64_t)1);
     }
@@ -301,11 +333,15 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     }
     const int64_t nrec = boffs[M] + 8;   // room past the end for the last block's reads
     const int64_t nrel = foffs[M] + 8;
-    std::vector<float> blocks(4 * nrec, 0.0f), rel(4 * nrel, 0.0f);
+    // every float of both block arrays is written below (in parallel), so
+    // they are allocated without the sequential zero fill
+    std::unique_ptr<float[]> blocks(new float[4 * nrec]), rel(new float[4 * nrel]);
     std::vector<float> site4(4 * M);
     auto put_int = [](float *dst, int32_t v) { std::memcpy(dst, &v, 4); };
     const float fnan = std::numeric_limits<float>::quiet_NaN();
-    for (int64_t i = 0; i < M; i++) {
+    // every cell writes only its own blocks and site entry
+    vg::parallel_for(M, o.threads, 1 << 12, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; i++) {
         const int64_t b = g->cells.off[i], e = g->cells.off[i + 1];
         const float pi[3] = {(float)Si[3 * i + 0], (float)Si[3 * i + 1], (float)Si[3 * i + 2]};
         float *h = &blocks[4 * boffs[i]];
@@ -344,6 +380,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
                 put_int(rr + 3, (int32_t)foffs[j]);
                 n1max = std::max(n1max, n1);
             } else {
+                r[0] = r[1] = r[2] = 0.0f;
                 put_int(r + 3, j);
             }
         }
@@ -360,7 +397,11 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         site4[4 * i + 2] = pi[2];
         put_int(&site4[4 * i + 3], (int32_t)foffs[i]);
     }
-    for (int64_t r = boffs[M]; r < nrec; r++) put_int(&blocks[4 * r + 3], -8);
+    });
+    for (int64_t r = boffs[M]; r < nrec; r++) {
+        blocks[4 * r] = blocks[4 * r + 1] = blocks[4 * r + 2] = 0.0f;
+        put_int(&blocks[4 * r + 3], -8);
+    }
     for (int64_t r = foffs[M]; r < nrel; r++) {
         rel[4 * r] = rel[4 * r + 1] = rel[4 * r + 2] = fnan;
         put_int(&rel[4 * r + 3], -8);
@@ -401,6 +442,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         for (size_t q = 0; q < dens.size(); q++) dens[q] = (float)std::cbrt(std::max(0.25, (double)cnt[q]) / vol);
     }
 
+    lap(4, t_lap);
     if (o.host_only) {
         g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int c = 0; c < 3; c++) {
@@ -438,8 +480,8 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
 #undef VG_ALLOC
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpy(g->d_site, site4.data(), sizeof(float) * 4 * M, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, blocks.data(), sizeof(float) * 4 * nrec, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->d_rel, rel.data(), sizeof(float) * 4 * nrel, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_cells, blocks.get(), sizeof(float) * 4 * nrec, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_rel, rel.get(), sizeof(float) * 4 * nrel, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_perm, g->perm.data(), sizeof(int32_t) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_blk_off, boff.data(), sizeof(int32_t) * boff.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_dens, dens.data(), sizeof(float) * dens.size(), cudaMemcpyHostToDevice);
@@ -450,16 +492,18 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
             brec[4 * q + 0] = brec[4 * q + 1] = brec[4 * q + 2] = fnan;
             put_int(&brec[4 * q + 3], -1);
         }
-        for (size_t b = 0; b < nblk; b++) {
-            for (int64_t q = g->blocks.off[b]; q < g->blocks.off[b + 1]; q++) {
-                const int32_t c = g->blocks.idx[q];
-                float *r = &brec[4 * ((size_t)boff[b] + (size_t)(q - g->blocks.off[b]))];
-                r[0] = (float)Si[3 * (int64_t)c + 0];
-                r[1] = (float)Si[3 * (int64_t)c + 1];
-                r[2] = (float)Si[3 * (int64_t)c + 2];
-                put_int(r + 3, c);
+        vg::parallel_for((int64_t)nblk, o.threads, 1 << 12, [&](int64_t b0, int64_t b1) {
+            for (int64_t b = b0; b < b1; b++) {
+                for (int64_t q = g->blocks.off[b]; q < g->blocks.off[b + 1]; q++) {
+                    const int32_t c = g->blocks.idx[q];
+                    float *r = &brec[4 * ((size_t)boff[b] + (size_t)(q - g->blocks.off[b]))];
+                    r[0] = (float)Si[3 * (int64_t)c + 0];
+                    r[1] = (float)Si[3 * (int64_t)c + 1];
+                    r[2] = (float)Si[3 * (int64_t)c + 2];
+                    put_int(r + 3, c);
+                }
             }
-        }
+        });
         e = cudaMemcpy(g->d_blk_rec, brec.data(), sizeof(float) * brec.size(), cudaMemcpyHostToDevice);
     }
 
@@ -507,6 +551,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         free_grid(g);
         return fail(VGRID_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     }
+    lap(5, t_lap);
     g->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = g;
     return VGRID_OK;
@@ -534,6 +579,7 @@ int vgrid_info(const vgrid_t *g, vgrid_info_t *info) {
         info->box[3 + c] = g->hd.hi[c];
     }
     info->build_seconds = g->build_seconds;
+    for (int k = 0; k < 6; k++) info->phase_seconds[k] = g->phase_seconds[k];
     info->device_bytes = g->device_bytes;
     info->host_fallback_cells = g->host_fallback_cells;
     return VGRID_OK;

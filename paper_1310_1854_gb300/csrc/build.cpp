@@ -519,27 +519,52 @@ static inline uint64_t spread21(uint64_t x) {
     return x;
 }
 
-void morton_order(const double *S, int64_t M, const double *box, std::vector<int32_t> &perm) {
-    std::vector<std::pair<uint64_t, int32_t>> key(M);
-    for (int64_t i = 0; i < M; i++) {
-        uint64_t code = 0;
-        for (int c = 0; c < 3; c++) {
-            double u = (S[3 * i + c] - box[c]) / (box[3 + c] - box[c]);
-            u = std::min(std::max(u, 0.0), 1.0);
-            uint64_t q = (uint64_t)std::min(u * 2097152.0, 2097151.0);
-            code |= spread21(q) << c;
-        }
-        key[i] = {code, (int32_t)i};
+void parallel_for(int64_t n, int threads, int64_t grain, const std::function<void(int64_t, int64_t)> &fn) {
+    if (n <= 0) return;
+    if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    threads = (int)std::max<int64_t>(1, std::min<int64_t>(threads, n / std::max<int64_t>(grain, 1)));
+    if (threads == 1) {
+        fn(0, n);
+        return;
     }
+    std::vector<std::thread> pool;
+    const int64_t step = (n + threads - 1) / threads;
+    for (int t = 1; t < threads; t++) {
+        const int64_t b = t * step, e = std::min(n, b + step);
+        if (b < e) pool.emplace_back(fn, b, e);
+    }
+    fn(0, std::min(n, step));
+    for (auto &th : pool) th.join();
+}
+
+void morton_order(const double *S, int64_t M, const double *box, std::vector<int32_t> &perm,
+                  std::vector<uint64_t> *codes, int threads) {
+    std::vector<std::pair<uint64_t, int32_t>> key(M);
+    parallel_for(M, threads, 1 << 14, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; i++) {
+            uint64_t code = 0;
+            for (int c = 0; c < 3; c++) {
+                double u = (S[3 * i + c] - box[c]) / (box[3 + c] - box[c]);
+                u = std::min(std::max(u, 0.0), 1.0);
+                uint64_t q = (uint64_t)std::min(u * 2097152.0, 2097151.0);
+                code |= spread21(q) << c;
+            }
+            key[i] = {code, (int32_t)i};
+        }
+    });
     std::sort(key.begin(), key.end());
     perm.resize(M);
-    for (int64_t i = 0; i < M; i++) perm[i] = key[i].second;
+    if (codes) codes->resize(M);
+    for (int64_t i = 0; i < M; i++) {
+        perm[i] = key[i].second;
+        if (codes) (*codes)[i] = key[i].first;
+    }
 }
 
 // Regular block grid over the box; each block lists the cells whose bounding
 // box overlaps it (Sect. 2.3).
 void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M, double blocks_per_site,
-                  BlocksOut &out) {
+                  BlocksOut &out, int threads) {
     double ext[3] = {box[3] - box[0], box[4] - box[1], box[5] - box[2]};
     double target = std::max(1.0, blocks_per_site * (double)M);
     double s = std::cbrt(ext[0] * ext[1] * ext[2] / target);
@@ -560,26 +585,44 @@ void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M,
         a = (int32_t)std::max(0.0, std::floor(lo));
         b = (int32_t)std::min((double)out.dim[c] - 1, std::floor(hi));
     };
-    std::vector<int64_t> count(K + 1, 0);
-    for (int64_t m = 0; m < M; m++) {
-        int32_t a[3], b[3];
-        for (int c = 0; c < 3; c++) range(m, c, a[c], b[c]);
-        for (int32_t i = a[0]; i <= b[0]; i++)
-            for (int32_t j = a[1]; j <= b[1]; j++)
-                for (int32_t k = a[2]; k <= b[2]; k++) count[((int64_t)i * out.dim[1] + j) * out.dim[2] + k + 1]++;
-    }
-    for (int64_t q = 0; q < K; q++) count[q + 1] += count[q];
-    out.off.assign(count.begin(), count.end());
-    out.idx.resize(count[K]);
-    std::vector<int64_t> cur(count.begin(), count.end() - 1);
-    for (int64_t m = 0; m < M; m++) {  // ascending m: lists come out sorted
-        int32_t a[3], b[3];
-        for (int c = 0; c < 3; c++) range(m, c, a[c], b[c]);
-        for (int32_t i = a[0]; i <= b[0]; i++)
-            for (int32_t j = a[1]; j <= b[1]; j++)
-                for (int32_t k = a[2]; k <= b[2]; k++)
-                    out.idx[cur[((int64_t)i * out.dim[1] + j) * out.dim[2] + k]++] = (int32_t)m;
-    }
+    // cells per block (parallel over cells, atomic counters), prefix sum,
+    // then every cell into the lists of its blocks and each list sorted by
+    // cell index, so the lists do not depend on the thread schedule
+    std::vector<std::atomic<int64_t>> count(K + 1);
+    parallel_for(K + 1, threads, 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; q++) count[q].store(0, std::memory_order_relaxed);
+    });
+    parallel_for(M, threads, 1 << 12, [&](int64_t b0, int64_t e0) {
+        for (int64_t m = b0; m < e0; m++) {
+            int32_t a[3], b[3];
+            for (int c = 0; c < 3; c++) range(m, c, a[c], b[c]);
+            for (int32_t i = a[0]; i <= b[0]; i++)
+                for (int32_t j = a[1]; j <= b[1]; j++)
+                    for (int32_t k = a[2]; k <= b[2]; k++)
+                        count[((int64_t)i * out.dim[1] + j) * out.dim[2] + k + 1].fetch_add(1, std::memory_order_relaxed);
+        }
+    });
+    out.off.resize(K + 1);
+    out.off[0] = 0;
+    for (int64_t q = 0; q < K; q++) out.off[q + 1] = out.off[q] + count[q + 1].load(std::memory_order_relaxed);
+    out.idx.resize(out.off[K]);
+    parallel_for(K, threads, 1 << 16, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; q++) count[q].store(out.off[q], std::memory_order_relaxed);  // cursors
+    });
+    parallel_for(M, threads, 1 << 12, [&](int64_t b0, int64_t e0) {
+        for (int64_t m = b0; m < e0; m++) {
+            int32_t a[3], b[3];
+            for (int c = 0; c < 3; c++) range(m, c, a[c], b[c]);
+            for (int32_t i = a[0]; i <= b[0]; i++)
+                for (int32_t j = a[1]; j <= b[1]; j++)
+                    for (int32_t k = a[2]; k <= b[2]; k++)
+                        out.idx[count[((int64_t)i * out.dim[1] + j) * out.dim[2] + k].fetch_add(
+                            1, std::memory_order_relaxed)] = (int32_t)m;
+        }
+    });
+    parallel_for(K, threads, 1 << 12, [&](int64_t b, int64_t e) {
+        for (int64_t q = b; q < e; q++) std::sort(out.idx.begin() + out.off[q], out.idx.begin() + out.off[q + 1]);
+    });
 }
 
 }  // namespace vg

@@ -413,22 +413,35 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
         (e = cudaMemcpy(out.bbox.data(), bbox, sizeof(double) * 6 * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return bad(e, "download");
     cleanup();
-    std::vector<std::vector<int32_t>> lists(M);
-    std::vector<int32_t> redo;
-    for (int64_t m = 0; m < M; m++) {
-        if (hfail[m]) {
-            redo.push_back((int32_t)m);
-            continue;
+    // each cell's list sorted and made unique in place (parallel over
+    // cells), the failed cells rebuilt on the host, then one CSR
+    std::vector<int64_t> len(M, 0);
+    parallel_for(M, threads, 1 << 12, [&](int64_t b, int64_t e) {
+        for (int64_t m = b; m < e; m++) {
+            if (hfail[m]) continue;
+            int *row = hnbr.data() + m * kCap;
+            std::sort(row, row + hcnt[m]);
+            len[m] = std::unique(row, row + hcnt[m]) - row;
         }
-        lists[m].assign(hnbr.begin() + m * kCap, hnbr.begin() + m * kCap + hcnt[m]);
-        std::sort(lists[m].begin(), lists[m].end());
-        lists[m].erase(std::unique(lists[m].begin(), lists[m].end()), lists[m].end());
-    }
+    });
+    std::vector<int32_t> redo;
+    for (int64_t m = 0; m < M; m++)
+        if (hfail[m]) redo.push_back((int32_t)m);
     if (host_fallback_cells) *host_fallback_cells = (int64_t)redo.size();
+    std::vector<std::vector<int32_t>> lists(redo.empty() ? 0 : M);
     if (!redo.empty()) {
         if (build_cells_into(S, M, box, threads, &redo, lists, out.vol.data(), out.bbox.data(), err) != 0) return -1;
+        for (int32_t m : redo) len[m] = (int64_t)lists[m].size();
     }
-    cells_to_csr(lists, out);
+    out.off.assign(M + 1, 0);
+    for (int64_t m = 0; m < M; m++) out.off[m + 1] = out.off[m] + len[m];
+    out.idx.resize(out.off[M]);
+    parallel_for(M, threads, 1 << 12, [&](int64_t b, int64_t e) {
+        for (int64_t m = b; m < e; m++) {
+            if (hfail[m]) std::copy(lists[m].begin(), lists[m].end(), out.idx.begin() + out.off[m]);
+            else std::copy(hnbr.begin() + m * kCap, hnbr.begin() + m * kCap + len[m], out.idx.begin() + out.off[m]);
+        }
+    });
     return 0;
 }
 

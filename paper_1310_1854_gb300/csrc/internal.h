@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <functional>
 #include <vector>
 
 namespace vg {
@@ -32,9 +33,16 @@ void cells_to_csr(const std::vector<std::vector<int32_t>> &nbr, CellsOut &out);
 // on the host. Returns 0, or -1 with err set.
 int build_cells_gpu(const double *sites, int64_t M, const double *box, int threads, CellsOut &out, std::string &err,
                     int64_t *host_fallback_cells);
-void morton_order(const double *sites, int64_t M, const double *box, std::vector<int32_t> &perm);
+// cells sorted by the Morton code of their site (21 bits per axis); the
+// sorted codes go to *codes if given
+void morton_order(const double *sites, int64_t M, const double *box, std::vector<int32_t> &perm,
+                  std::vector<uint64_t> *codes = nullptr, int threads = 0);
+// fn(begin, end) over [0, n) split into contiguous ranges on up to `threads`
+// host threads (0: all cores); ranges of fewer than `grain` items stay on
+// one thread
+void parallel_for(int64_t n, int threads, int64_t grain, const std::function<void(int64_t, int64_t)> &fn);
 void build_blocks(const double *box, const std::vector<double> &bbox, int64_t M, double blocks_per_site,
-                  BlocksOut &out);
+                  BlocksOut &out, int threads = 0);
 
 }  // namespace vg
 
