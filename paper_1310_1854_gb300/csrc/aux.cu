@@ -59,7 +59,10 @@ __global__ void __launch_bounds__(256) locate_kernel(const GridDev *grids, const
         const double *o = rs.origin + 3 * li;
         const LocPt P = loc_point(__ldg(o), __ldg(o + 1), __ldg(o + 2));
         RayPrep *out = rs.start + li;
-        int m = locate_point<true>(gp, P, prep == PREP_CELL32 || prep == PREP_FP32, nullptr);
+        // float32 distances with the proven float64 fallback give exactly the
+        // float64 argmin, so both traversal forms start that way; only
+        // vgrid_locate's float64 mode (PREP_CELL64) scans in float64
+        int m = locate_point<true>(gp, P, prep != PREP_CELL64, nullptr);
         if (out_caller) out_caller[w] = m >= 0 ? __ldg(&gp->perm[m]) : -1;
         if (prep == PREP_CELL32 || prep == PREP_CELL64) {
             out->cell = m;
