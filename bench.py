@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--block", type=int, default=int(os.environ.get("VGRID_BLOCK", "0")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=1_000_000)
-    ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6"],
+    ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6", "segments1e5"],
                     help="disk1e5 is the benchmark line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -384,7 +384,8 @@ def main():
 
 # ---------------------------------------------------------------------------
 # other workloads (one GPU): 10^6 clumpy sites, 64 uneven grids in one
-# launch, and the adjoint on the 10^6-site disk
+# launch, the adjoint on the 10^6-site disk, and segment lists on the
+# 10^5-site disk
 # ---------------------------------------------------------------------------
 
 def _events_ms(fn, steps, flush):
@@ -412,6 +413,52 @@ def run_extra(args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
     sampler = ClockSampler(gpu_index(0))
+    if args.workload == "segments1e5":
+        g, _ = gen.config2(n_rays=1)
+        rays = gen.disk_rays(args.rays, gen.SEED_BASE + 2 + 1000)
+        vg = VoronoiGrid(g.sites, g.box)
+        vg.set_density(torch.from_numpy(g.rho).to(dev))
+        info = vg.info()
+        O = torch.from_numpy(rays.origin).to(dev)
+        D = torch.from_numpy(rays.dir).to(dev)
+        N = O.shape[0]
+        res = {}
+        for prec in ("fp32", "fp64"):
+            r = vg.trace(O, D, precision=prec, segments=True, stats=True)
+            cap = int(r.seg_off[N].item())
+            fn = lambda: vg.trace(O, D, precision=prec, segments=True, seg_capacity=cap)
+            for _ in range(args.warmup):
+                fn()
+            steps = args.steps if prec == "fp32" else max(3, args.steps // 4)
+            vg.enable_timing(True)
+            vg.read_timing()
+            sampler.start()
+            n0 = kernel_launches()
+            ms = _events_ms(fn, steps, flush)
+            n_kernels = kernel_launches() - n0
+            clocks = sampler.stop()
+            _, tr_ms, launches = vg.read_timing()
+            vg.enable_timing(False)
+            res[prec] = (cap * steps / (ms / 1e3), ms / steps, n_kernels, clocks, r.stats, tr_ms / max(launches, 1))
+        v32, ms32, nk, clocks, st, kern = res["fp32"]
+        deg = info["nnz"] / info["M"]
+        # the traversal's algorithmic bytes per crossing plus the 8-byte slot
+        # it stores per segment
+        bpc = 28.0 + 20.0 * deg + 8.0
+        achieved = st["crossings"] * bpc / (kern / 1e3) / 1e9
+        line.update({"value": v32, "ms_per_step": ms32,
+                     "config": {"workload": "exp-disk 1e5 sites, 1e6 rays, segment list (cell, length) of every "
+                                            "ray in CSR form plus tau", "sites": info["M"], "rays": N,
+                                "segments": st["crossings"], "l2": "flushed between timed steps"},
+                     "fp64": {"value": res["fp64"][0], "ms_per_step": res["fp64"][1],
+                              "traversal_ms_per_launch": res["fp64"][5]},
+                     "stats_per_step": st, "gpu_launches": nk,
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                                  "frac": achieved / peak, "traffic": None, "kernel_ms_per_launch": kern,
+                                  "algorithmic_bytes_per_crossing": bpc, "peak_source": peak_kind},
+                     "e2e": None, "clocks": clocks})
+        print(json.dumps(line), flush=True)
+        return
     if args.workload in ("clumpy1e6", "grad1e6"):
         t0 = time.time()
         if args.workload == "clumpy1e6":

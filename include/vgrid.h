@@ -219,9 +219,16 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  *                 [seg_capacity]: segment lengths.
  *   ray_status    device int32[N] or NULL: VGRID_RAY_* per ray.
  *   stats         host or NULL: counters of this call (synchronises `stream`).
- * Segment mode traces twice (count, then fill) and reads the total back to
- * the host; if seg_capacity is too small it returns VGRID_ERR_CAPACITY with
- * seg_off filled so the caller can size the buffers and call again.
+ * Segment mode traces once: each ray appends its segments to chunks of 8 in
+ * a work buffer of the library, the counts are scanned into seg_off, the
+ * total is read back to the host, and a copy kernel moves the chunks into
+ * seg_cell / seg_len in ray order. If seg_capacity is too small it returns
+ * VGRID_ERR_CAPACITY with seg_off filled so the caller can size the buffers
+ * and call again (seg_capacity = 0 only counts). The work buffer holds
+ * ceil(seg_capacity/8) + min(N, seg_capacity) + 32 x (warps of the launch)
+ * chunks of 8 slots of 8 (FP32_RECHECK) or 16 (FP64) bytes plus 12 bytes
+ * of records each, and 8 bytes per ray; N is at most 2^31 - 1 in segment
+ * mode.
  * Rays that start outside the domain get tau = 0, no segments and status
  * VGRID_RAY_OUTSIDE (not an error). Whenever the call reads its counters back
  * (stats non-NULL, or segment mode) it returns VGRID_ERR_ARG if some
@@ -231,7 +238,7 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  * The first call with more rays than any earlier call on this grid
  * allocates larger work buffers: a 64-byte start record per ray, and with
  * the ray order (vgrid_launch.order) 5 more bytes per ray; segment mode adds
- * the scan's scratch.
+ * the scan's scratch and the chunk buffer above.
  */
 int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, int output,
                 void *tau, int64_t *seg_off, int32_t *seg_cell, void *seg_len, int64_t seg_capacity,

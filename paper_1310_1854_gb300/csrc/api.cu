@@ -105,6 +105,15 @@ struct vgrid {
     int64_t scan_cap = 0;
     double *d_entry = nullptr;   // entry points of VGRID_ENTER calls
     int64_t entry_cap = 0;
+    // segment mode: chunk slots, each chunk's (ray, position), the cursor
+    int4 *d_slots = nullptr;     // slots of 8 (float32) or 16 (float64) bytes
+    int64_t slot_bytes = 0;
+    int2 *d_chunk_meta = nullptr;
+    int32_t *d_chunk_inv = nullptr;  // destination chunk -> chunk
+    int64_t meta_cap = 0;
+    int64_t *d_coff = nullptr;       // chunks per ray, scanned
+    int64_t coff_cap = 0;
+    unsigned long long *d_cursor = nullptr;
     uint8_t *d_bin = nullptr;    // ray order: bins, counts, permutation
     uint32_t *d_hist = nullptr;
     int32_t *d_order = nullptr;
@@ -201,7 +210,7 @@ static void free_grid(vgrid_t *g) {
     if (g->s_d2h) cudaStreamDestroy(g->s_d2h);
     void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
                     g->d_order, g->d_perm,  g->d_blk_off, g->d_blk_rec, g->d_queue, g->d_stats, g->d_set,
-                    g->d_start, g->d_scan,  g->d_entry};
+                    g->d_start, g->d_scan,  g->d_entry, g->d_slots, g->d_chunk_meta, g->d_chunk_inv, g->d_coff, g->d_cursor};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete g;
@@ -738,6 +747,48 @@ int ensure_scan(vgrid_t *g, int64_t N) {
     return VGRID_OK;
 }
 
+// chunk pool of segment mode: `chunks` chunks of kSegChunk slots of
+// slot_bytes, their (ray, position) records and the inverse map, and the
+// chunk offsets of N rays
+int ensure_chunks(vgrid_t *g, int64_t N, int64_t chunks, int slot_bytes) {
+    if (!g->d_cursor) {
+        int rc = dmalloc(&g->d_cursor, 1, g->device_bytes);
+        if (rc) return rc;
+    }
+    if (N + 1 > g->coff_cap) {
+        if (g->d_coff) cudaFree(g->d_coff);
+        g->device_bytes -= g->coff_cap * (int64_t)sizeof(int64_t);
+        g->d_coff = nullptr;
+        g->coff_cap = 0;
+        int rc = dmalloc(&g->d_coff, (size_t)(N + 1), g->device_bytes);
+        if (rc) return rc;
+        g->coff_cap = N + 1;
+    }
+    const int64_t bytes = chunks * vg::kSegChunk * slot_bytes;  // a multiple of 64
+    if (bytes > g->slot_bytes) {
+        if (g->d_slots) cudaFree(g->d_slots);
+        g->device_bytes -= g->slot_bytes;
+        g->d_slots = nullptr;
+        g->slot_bytes = 0;
+        int rc = dmalloc(&g->d_slots, (size_t)(bytes / 16), g->device_bytes);
+        if (rc) return rc;
+        g->slot_bytes = bytes;
+    }
+    if (chunks > g->meta_cap) {
+        if (g->d_chunk_meta) cudaFree(g->d_chunk_meta);
+        if (g->d_chunk_inv) cudaFree(g->d_chunk_inv);
+        g->device_bytes -= g->meta_cap * (int64_t)(sizeof(int2) + sizeof(int32_t));
+        g->d_chunk_meta = nullptr;
+        g->d_chunk_inv = nullptr;
+        g->meta_cap = 0;
+        int rc = dmalloc(&g->d_chunk_meta, (size_t)chunks, g->device_bytes);
+        if (!rc) rc = dmalloc(&g->d_chunk_inv, (size_t)chunks, g->device_bytes);
+        if (rc) return rc;
+        g->meta_cap = chunks;
+    }
+    return VGRID_OK;
+}
+
 // persistent grid size for a trace kernel
 int persistent_blocks(const void *fn, const vgrid_launch &l, int sms, int64_t work_items) {
     int per_sm = 0;
@@ -870,6 +921,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     if (output == VGRID_TAU && N > 0 && !tau) return fail(VGRID_ERR_ARG, "tau is NULL");
     if (output == VGRID_SEGMENTS && !seg_off) return fail(VGRID_ERR_ARG, "seg_off is NULL");
     if (seg_capacity < 0) return fail(VGRID_ERR_ARG, "negative capacity");
+    if (output == VGRID_SEGMENTS && N > INT32_MAX) return fail(VGRID_ERR_ARG, "segment mode takes at most 2^31-1 rays");
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (N == 0) {
@@ -893,7 +945,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
     {
-        const void *fn = ks.fn[fp64][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_COUNT];
+        const void *fn = ks.fn[fp64][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_SEGS];
         if ((rc = locate_start(g, fn, L, N, &order, s, fp64 != 0))) return rc;
     }
     mark(g, 0, 1, s);
@@ -914,26 +966,45 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
         if (stats) return read_stats(g->d_stats, stats, s);
         return VGRID_OK;
     }
-    // segment lists: count, prefix sum, capacity check, fill
+    // segment lists in one traversal: each ray's segments go to chunks of
+    // the pool, the counts are scanned into seg_off, and the chunks are
+    // copied into the caller's arrays. The pool holds every chunk a ray
+    // fills or starts (at most cap / kSegChunk + min(N, cap) when the total
+    // fits the capacity) plus the page each warp may leave unused, so it
+    // never runs out when the segments fit the caller's buffers.
+    const void *fn = ks.fn[fp64][vg::MODE_SEGS];
+    int64_t chunks = 0;
+    if (seg_capacity > 0) {
+        const int64_t warps = (int64_t)persistent_blocks(fn, L, g->sms, N) * L.block / 32;
+        chunks = (seg_capacity + vg::kSegChunk - 1) / vg::kSegChunk + std::min(N, seg_capacity) +
+                 warps * vg::kSegPage;
+        if (chunks > INT32_MAX - 2 * vg::kSegPage)
+            return fail(VGRID_ERR_ARG, "seg_capacity too large for one call (split the rays)");
+    }
     if ((rc = ensure_scan(g, N))) return rc;
+    if ((rc = ensure_chunks(g, N, chunks, fp64 ? 16 : 8))) return rc;
+    VG_CUDA(cudaMemsetAsync(g->d_cursor, 0, sizeof(unsigned long long), s));
     a.seg_off = seg_off;
+    a.seg_slots = g->d_slots;
+    a.chunk_meta = g->d_chunk_meta;
+    a.chunk_cursor = g->d_cursor;
+    a.chunk_cap = chunks;
     mark(g, 1, 0, s);
-    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_COUNT], L, g->sms, N, a, s))) return rc;
+    if ((rc = launch_trace(fn, L, g->sms, N, a, s))) return rc;
     mark(g, 1, 1, s);
     VG_CUDA(vg::launch_exclusive_scan(seg_off, N, g->d_scan, s));
     int64_t total = 0;
+    unsigned long long taken = 0;
     VG_CUDA(cudaMemcpyAsync(&total, seg_off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    VG_CUDA(cudaMemcpyAsync(&taken, g->d_cursor, sizeof(taken), cudaMemcpyDeviceToHost, s));
     VG_CUDA(cudaStreamSynchronize(s));
     if (total > seg_capacity || (total > 0 && (!seg_cell || !seg_len)))
         return fail(VGRID_ERR_CAPACITY, "segment buffers hold " + std::to_string(seg_capacity) + ", need " +
                                             std::to_string(total));
-    VG_CUDA(vg::launch_prepare(nullptr, set, g->d_queue, g->d_stats, s));
-    a.seg_cell = seg_cell;
-    a.seg_len = seg_len;
-    a.seg_cap = total;
-    mark(g, 1, 0, s);
-    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_FILL], L, g->sms, N, a, s))) return rc;
-    mark(g, 1, 1, s);
+    if ((int64_t)taken > chunks)  // cannot happen when the total fits (see above)
+        return fail(VGRID_ERR_CUDA, "segment chunk pool ran out");
+    VG_CUDA(vg::launch_compact_segments(seg_off, N, (int64_t)taken, g->d_chunk_meta, g->d_slots, fp64 != 0, g->d_coff,
+                                        g->d_scan, g->d_chunk_inv, seg_cell, seg_len, g->sms, s));
     return read_stats(g->d_stats, stats, s);
 }
 

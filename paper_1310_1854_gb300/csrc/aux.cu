@@ -1,6 +1,7 @@
 // Auxiliary kernels of libvgrid: start-cell location (C(r), Sect. 2.3),
 // per-call set-up, density reordering and the prefix sum that turns
 // per-ray segment counts into offsets.
+#include <algorithm>
 #include <atomic>
 
 #include "kernels.h"
@@ -394,6 +395,74 @@ __global__ void __launch_bounds__(kScanThreads) scan_fix_kernel(int64_t *data, i
 #pragma unroll
     for (int i = 0; i < kScanItems; i++)
         if (base + i < n) data[base + i] += add;
+}
+
+// Chunked segments -> CSR, in the order of the destination so that the
+// stores are coalesced: (1) chunks per ray, ceil(n / kSegChunk), scanned into
+// coff; (2) each used chunk c of ray r at position k is entered as
+// inv[coff[r] + k] = c; (3) kSegChunk threads per destination chunk copy its
+// slots to the ray's offset plus kSegChunk * k.
+__global__ void chunk_counts_kernel(const int64_t *off, int64_t N, int64_t *ccount) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x)
+        ccount[r] = (__ldg(off + r + 1) - __ldg(off + r) + kSegChunk - 1) / kSegChunk;
+}
+
+__global__ void chunk_invert_kernel(const int2 *meta, int64_t nchunks, const int64_t *coff, int32_t *inv) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int2 m = __ldg(meta + c);
+        if (m.x >= 0) inv[__ldg(coff + m.x) + m.y] = (int32_t)c;  // -1: handed to a warp, not used
+    }
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(256) compact_segments_kernel(const int64_t *off, const int64_t *coff, int64_t N,
+                                                               const int32_t *inv, const int2 *meta, const void *slots,
+                                                               int32_t *cell, void *len) {
+    const int64_t nd = __ldg(coff + N);  // destination chunks
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nd * kSegChunk; t += stride) {
+        const int32_t c = __ldg(inv + t / kSegChunk);
+        const int2 m = __ldg(meta + c);
+        const int64_t o = __ldg(off + m.x), n = __ldg(off + m.x + 1) - o;
+        const int64_t j = (int64_t)m.y * kSegChunk + (t & (kSegChunk - 1));
+        if (j >= n) continue;
+        const int64_t at = (int64_t)c * kSegChunk + (t & (kSegChunk - 1));
+        if (FP64) {
+            const int4 v = __ldcs(reinterpret_cast<const int4 *>(slots) + at);
+            cell[o + j] = v.x;
+            reinterpret_cast<double *>(len)[o + j] = __hiloint2double(v.w, v.z);
+        } else {
+            const int2 v = __ldcs(reinterpret_cast<const int2 *>(slots) + at);
+            cell[o + j] = v.x;
+            reinterpret_cast<float *>(len)[o + j] = __int_as_float(v.y);
+        }
+    }
+}
+
+static int grid_for(int64_t threads, int sms) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)sms * 8));
+}
+
+cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchunks, const int2 *meta,
+                                    const void *slots, bool fp64, int64_t *coff, int64_t *scan_tmp, int32_t *inv,
+                                    int32_t *cell, void *len, int sms, cudaStream_t s) {
+    if (N <= 0 || nchunks <= 0) return cudaSuccess;
+    chunk_counts_kernel<<<grid_for(N, sms), 256, 0, s>>>(off, N, coff);
+    count_launches(1);
+    cudaError_t e = launch_exclusive_scan(coff, N, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    chunk_invert_kernel<<<grid_for(nchunks, sms), 256, 0, s>>>(meta, nchunks, coff, inv);
+    count_launches(1);
+    // destination chunks: coff[N] (read on the device), at most nchunks
+    if (fp64)
+        compact_segments_kernel<true><<<grid_for(nchunks * kSegChunk, sms), 256, 0, s>>>(off, coff, N, inv, meta,
+                                                                                         slots, cell, len);
+    else
+        compact_segments_kernel<false><<<grid_for(nchunks * kSegChunk, sms), 256, 0, s>>>(off, coff, N, inv, meta,
+                                                                                          slots, cell, len);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }

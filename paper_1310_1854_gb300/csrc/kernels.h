@@ -7,7 +7,18 @@
 
 namespace vg {
 
-enum { MODE_TAU = 0, MODE_COUNT = 1, MODE_FILL = 2, MODE_GRAD = 3, MODE_INTERACT = 4, NUM_MODES = 5 };
+enum { MODE_TAU = 0, MODE_SEGS = 1, MODE_GRAD = 2, MODE_INTERACT = 3, NUM_MODES = 4 };
+
+// Segment lists in one traversal. A ray's segments go, in path order, into
+// chunks of kSegChunk slots of a work buffer; each chunk records its ray and
+// its position in that ray's list, so once the counts have been scanned a
+// compaction kernel can copy every chunk to its place in the CSR arrays
+// independently of the others. Chunks are handed to the lanes of a warp from
+// a page of kSegPage chunks that the warp takes from one global cursor, so
+// the cursor sees one atomic per kSegPage chunks. A slot is int2 (cell,
+// float32 length) or int4 (cell, 0, float64 length as low and high words).
+constexpr int kSegChunk = 8;
+constexpr int kSegPage = 32;  // >= 32: one ballot's requests always fit in what is left plus one page
 
 struct TraceArgs {
     const GridDev *grids;     // one descriptor per grid
@@ -16,10 +27,12 @@ struct TraceArgs {
     int64_t total;            // rays over all sets
     unsigned long long *queue;
     StatsDev *stats;
-    int64_t *seg_off;         // count mode: counts per ray; fill mode: offsets
-    int32_t *seg_cell;
-    void *seg_len;            // float or double
-    int64_t seg_cap;          // entries of seg_cell / seg_len; writes beyond are dropped
+    // segment mode
+    int64_t *seg_off;         // segment count per ray (scanned afterwards)
+    void *seg_slots;          // chunk slots (kSegChunk per chunk)
+    int2 *chunk_meta;         // per chunk: (ray, position in the ray's list); ray -1: unused
+    unsigned long long *chunk_cursor;  // chunks handed out (zeroed by the caller)
+    int64_t chunk_cap;        // chunks in the buffer; segments beyond are counted, not stored
     const float *dL_dtau;
     float *dL_drho;
     // interaction mode
@@ -87,6 +100,12 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
                           int32_t *out_caller, int sms, cudaStream_t s);
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,
                                    float4 *cells, float4 *rel, cudaStream_t s);
+// copy the segments in chunks 0..nchunks-1 (see kSegChunk) of rays 0..N-1
+// into the CSR arrays at the scanned offsets off[0..N]; coff holds N+1 and
+// inv nchunks values of scratch, scan_tmp scan_tmp_elems(N)
+cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchunks, const int2 *meta,
+                                    const void *slots, bool fp64, int64_t *coff, int64_t *scan_tmp, int32_t *inv,
+                                    int32_t *cell, void *len, int sms, cudaStream_t s);
 // exclusive scan of counts[0..n-1] (int64) into off[0..n]; tmp holds
 // scan_tmp_elems(n) int64 values
 int64_t scan_tmp_elems(int64_t n);

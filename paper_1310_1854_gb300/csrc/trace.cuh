@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fsplit.h"
 #include "internal.h"
 #include "kernels.h"
@@ -488,9 +490,79 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     float dLr = 0.f;
     float tint = 0.f, wgt = 1.f, att = 1.f;   // interaction mode: tau_int, weight, exp(-tau)
     int nseg = 0, zrun = 0, steps = 0, status = 0;
-    int64_t seg_base = 0;
+    // segment mode: the segment of the last step waits in registers until
+    // the top of the next iteration, where the warp is converged and takes
+    // chunks for its lanes from a shared page [pg, pe)
+    using SegLen = typename std::conditional<FP64, double, float>::type;
+    bool pend = false;
+    int pend_cell = 0, pend_ray = 0;
+    SegLen pend_len = 0;
+    int cur_chunk = -1;     // chunk of the current ray; -1 none yet, -2 out of chunks
+    // the warp's page of chunks [s_page[w][0], s_page[w][1]), kept in shared
+    // memory (registers are the scarce resource of this kernel)
+    __shared__ int s_page[8][2];
+    const int wib = threadIdx.x >> 5;
+    if (MODE == MODE_SEGS) {
+        if (lane == 0) s_page[wib][0] = s_page[wib][1] = 0;
+        __syncwarp();
+    }
 
     for (;;) {
+        // ---------------- segment mode: store the last step's segment ----------------
+        if (MODE == MODE_SEGS) {
+            if (a.chunk_cap > 0) {
+                // the pending segment is number j of its ray (nseg is reset
+                // only when the next ray starts, further down)
+                const int j = nseg - 1;
+                const bool want = pend && cur_chunk != -2 && (j & (kSegChunk - 1)) == 0;
+                const unsigned wm = __ballot_sync(0xffffffffu, want);
+                if (wm) {
+                    const int k = __popc(wm);
+                    const int rank = __popc(wm & ((1u << lane) - 1u));
+                    const int pg = s_page[wib][0], pe = s_page[wib][1];
+                    const int left = pe - pg;
+                    int base = 0;
+                    if (k > left) {
+                        // a new page; the cursor may run past the buffer, ids
+                        // at or beyond chunk_cap are never stored
+                        unsigned long long b = 0;
+                        if (lane == 0) b = atomicAdd(a.chunk_cursor, (unsigned long long)kSegPage);
+                        b = __shfl_sync(0xffffffffu, b, 0);
+                        base = (int)min(b, (unsigned long long)a.chunk_cap);
+                    }
+                    if (want) {
+                        const int nc = rank < left ? pg + rank : base + (rank - left);
+                        if (nc < a.chunk_cap) {
+                            a.chunk_meta[nc] = make_int2(pend_ray, j / kSegChunk);
+                            cur_chunk = nc;
+                        } else {
+                            cur_chunk = -2;  // the rest of this ray is only counted
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) {
+                        s_page[wib][0] = k > left ? base + (k - left) : pg + k;
+                        if (k > left) s_page[wib][1] = base + kSegPage;
+                    }
+                    __syncwarp();
+                }
+                if (pend && cur_chunk >= 0) {
+                    const int64_t at = (int64_t)cur_chunk * kSegChunk + (j & (kSegChunk - 1));
+                    // streaming stores: the slots are read once, by the
+                    // compaction, and should not push the grid out of L2
+                    if (FP64) {
+                        const double v = (double)pend_len;
+                        __stcs(reinterpret_cast<int4 *>(a.seg_slots) + at,
+                               make_int4(pend_cell, 0, __double2loint(v), __double2hiint(v)));
+                    } else {
+                        __stcs(reinterpret_cast<int2 *>(a.seg_slots) + at,
+                               make_int2(pend_cell, __float_as_int((float)pend_len)));
+                    }
+                }
+            }
+            pend = false;
+        }
+
         // ---------------- fetch new rays (one atomic per warp) ----------------
         const bool need = ray == -1;
         const unsigned needmask = __ballot_sync(0xffffffffu, need && gl == 0);
@@ -529,7 +601,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             tau32 = 0.f;
             tauc = 0.f;
             th = tl = 0.f;
-            if (MODE == MODE_FILL) seg_base = a.seg_off[ray];
+            if (MODE == MODE_SEGS) cur_chunk = -1;
             if (MODE == MODE_GRAD) dLr = __ldg(&a.dL_dtau[ray]);
             if (MODE == MODE_INTERACT) {
                 tint = __ldg(&a.tau_int[ray]);
@@ -582,14 +654,14 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 if (gl == 0) {
                     VG_STAT(S_RAYS, 1);
                     VG_STAT(status == RAY_OUTSIDE ? S_OUT : S_BAD, 1);
-                    if (MODE == MODE_TAU || MODE == MODE_FILL) {
+                    if (MODE == MODE_TAU || MODE == MODE_SEGS) {
                         if (rs->tau) {
                             if (FP64) ((double *)rs->tau)[li] = 0.0;
                             else ((float *)rs->tau)[li] = 0.f;
                         }
                         if (rs->status) rs->status[li] = status;
                     }
-                    if (MODE == MODE_COUNT) a.seg_off[ray] = 0;
+                    if (MODE == MODE_SEGS) a.seg_off[ray] = 0;
                     if (MODE == MODE_INTERACT) {
                         a.int_cell[ray] = -1;
                         a.int_s[ray] = 0.f;
@@ -725,13 +797,12 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         } else {
             const bool positive = FP64 ? (s64 > 0.0) : (len > 0.0f);
             if (positive) {
-                if (MODE == MODE_FILL && gl == 0) {
-                    const int64_t at = seg_base + nseg;
-                    if (at < a.seg_cap) {  // the count pass sized the buffer; never write past it
-                        a.seg_cell[at] = caller;
-                        if (FP64) ((double *)a.seg_len)[at] = s64;
-                        else ((float *)a.seg_len)[at] = len;
-                    }
+                if (MODE == MODE_SEGS && gl == 0) {
+                    pend = true;  // stored at the top of the next iteration
+                    pend_cell = caller;
+                    pend_ray = (int)ray;
+                    if (FP64) pend_len = s64;
+                    else pend_len = len;
                 }
                 if (MODE == MODE_GRAD && gl == 0) atomicAdd(&a.dL_drho[caller], dLr * kappa * len);
                 if (MODE == MODE_INTERACT) {
@@ -827,14 +898,14 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 VG_STAT(S_CROSS, nseg);
                 VG_STAT(S_DEC, steps);
                 const RaySetDev *rs = BATCH ? &a.sets[set] : &a.s1;
-                if (MODE == MODE_TAU || MODE == MODE_FILL) {
+                if (MODE == MODE_TAU || MODE == MODE_SEGS) {
                     if (rs->tau) {
                         if (FP64) ((double *)rs->tau)[li] = tau64;
                         else ((float *)rs->tau)[li] = tau32;
                     }
                     if (rs->status) rs->status[li] = status;
                 }
-                if (MODE == MODE_COUNT) a.seg_off[ray] = nseg;
+                if (MODE == MODE_SEGS) a.seg_off[ray] = nseg;
                 if (MODE == MODE_INTERACT && !interacted) {
                     a.int_cell[ray] = -1;  // escaped (or cut at the step limit)
                     a.int_s[ray] = __fadd_rn(th, tl);
@@ -843,6 +914,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             ray = -1;
         }
     }
+
+    // segment mode: the rest of the warp's page holds no segments
+    if (MODE == MODE_SEGS && a.chunk_cap > 0)
+        for (int c = s_page[wib][0] + lane; c < s_page[wib][1]; c += 32)
+            if (c < a.chunk_cap) a.chunk_meta[c] = make_int2(-1, 0);
 
     // ---------------- statistics: one global atomic per block and counter ----------------
 #undef VG_STAT

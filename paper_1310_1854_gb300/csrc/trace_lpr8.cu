@@ -6,12 +6,10 @@ namespace vg {
 
 void kernel_table_lpr8(KernelSet &k) {
     k.fn[0][MODE_TAU] = (const void *)trace_kernel<8, false, MODE_TAU, false>;
-    k.fn[0][MODE_COUNT] = (const void *)trace_kernel<8, false, MODE_COUNT, false>;
-    k.fn[0][MODE_FILL] = (const void *)trace_kernel<8, false, MODE_FILL, false>;
+    k.fn[0][MODE_SEGS] = (const void *)trace_kernel<8, false, MODE_SEGS, false>;
     k.fn[0][MODE_GRAD] = (const void *)trace_kernel<8, false, MODE_GRAD, false>;
     k.fn[1][MODE_TAU] = (const void *)trace_kernel<8, true, MODE_TAU, false>;
-    k.fn[1][MODE_COUNT] = (const void *)trace_kernel<8, true, MODE_COUNT, false>;
-    k.fn[1][MODE_FILL] = (const void *)trace_kernel<8, true, MODE_FILL, false>;
+    k.fn[1][MODE_SEGS] = (const void *)trace_kernel<8, true, MODE_SEGS, false>;
     k.fn[1][MODE_GRAD] = nullptr;
     k.fn[0][MODE_INTERACT] = (const void *)trace_kernel<8, false, MODE_INTERACT, false>;
     k.fn[1][MODE_INTERACT] = nullptr;

@@ -536,6 +536,89 @@ def test_ray_order_edge_cases():
     vg.set_launch()
 
 
+def test_segment_lists_single_pass():
+    """Segment lists come from one traversal (chunks of 8 per ray, handed out
+    in warp pages, then copied into ray order): the lists are the same for
+    every launch shape and with or without the ray order, whatever the
+    capacity given (exact, generous); a capacity one short, or zero, reports
+    the same offsets; per ray the lengths add up to the path length to the
+    wall and kappa rho l adds up to tau."""
+    from paper_1310_1854_gb300 import VGridError, _lib
+    g, rays = gen.config2(M=20_000, n_rays=30_000)
+    vg = make(g)
+    rng = gen.rng_for(321)
+    # a few rays outside the box among them: no segments
+    o = rays.origin.copy()
+    out = rng.choice(len(o), 100, replace=False)
+    o[out] = g.box[3:] + rng.uniform(0.1, 1.0, (100, 3))
+    O, D = dev(o), dev(rays.dir)
+    N = len(o)
+    lo, hi = g.box[:3], g.box[3:]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tw = np.where(rays.dir > 0, (hi - o) / rays.dir, np.where(rays.dir < 0, (lo - o) / rays.dir, np.inf))
+    tmax = tw.min(axis=1)
+    rho = g.rho.astype(np.float64)
+    inside = np.ones(N, dtype=bool)
+    inside[out] = False
+    for prec in ("fp32", "fp64"):
+        ref = None
+        for lpr in (1, 2, 4, 8):
+            for order in (-1, 1):
+                vg.set_launch(lanes_per_ray=lpr, fp64_lanes_per_ray=lpr, order=order)
+                r = vg.trace(O, D, precision=prec, segments=True, status=True, stats=True)
+                cur = [r.seg_off.cpu().numpy(), r.seg_cell.cpu().numpy(), r.seg_len.cpu().numpy(),
+                       r.tau.cpu().numpy()]
+                if ref is None:
+                    ref = cur
+                    total = int(cur[0][-1])
+                    assert total == r.stats["crossings"] and total > 10 * N
+                    st = r.status.cpu().numpy()
+                    assert np.all(st[out] == _lib.RAY_OUTSIDE) and np.all(st[inside] == _lib.RAY_OK)
+                elif prec == "fp64" and lpr != 1:
+                    # the float64 winner does not depend on the lane split
+                    for a, b in zip(ref, cur):
+                        np.testing.assert_array_equal(a, b)
+                else:
+                    for a, b in zip(ref[:3], cur[:3]):
+                        np.testing.assert_array_equal(a, b)
+        so, cells, lens, tau = ref
+        cnt = np.diff(so)
+        assert np.all(cnt[out] == 0) and np.all(cnt[inside] > 0)
+        ray_of = np.repeat(np.arange(N), cnt)
+        ltot = np.bincount(ray_of, weights=lens.astype(np.float64), minlength=N)
+        ttot = np.bincount(ray_of, weights=float(g.kappa) * rho[cells] * lens.astype(np.float64), minlength=N)
+        if prec == "fp64":
+            # the point moves by rounded steps r += s k; the last step, to
+            # the wall, makes up for their drift only to about n ulp / |k_axis|
+            np.testing.assert_allclose(ltot[inside], tmax[inside], rtol=1e-9)
+            np.testing.assert_allclose(ttot[inside], tau[inside], rtol=1e-11)
+        else:
+            np.testing.assert_allclose(ltot[inside], tmax[inside], rtol=1e-4)
+            np.testing.assert_allclose(ttot[inside], tau[inside], rtol=1e-5)
+        vg.set_launch()
+        for cap in (total, 4 * total + 17):
+            r = vg.trace(O, D, precision=prec, segments=True, seg_capacity=cap)
+            np.testing.assert_array_equal(r.seg_off.cpu().numpy(), so)
+            np.testing.assert_array_equal(r.seg_cell.cpu().numpy(), cells)
+            np.testing.assert_array_equal(r.seg_len.cpu().numpy(), lens)
+        for cap in (total - 1, 0):
+            with pytest.raises(VGridError) as ex:
+                vg.trace(O, D, precision=prec, segments=True, seg_capacity=cap)
+            assert ex.value.code == _lib.ERR_CAPACITY
+        # the offsets of a refused call, read through the C ABI
+        import ctypes
+        lib = _lib.load()
+        off = torch.empty(N + 1, dtype=torch.int64, device="cuda")
+        tdt = torch.float64 if prec == "fp64" else torch.float32
+        tb = torch.empty(N, dtype=tdt, device="cuda")
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        rc = lib.vgrid_trace(vg._h, p(O), p(D), N, _lib.FP64 if prec == "fp64" else _lib.FP32_RECHECK,
+                             _lib.SEGMENTS, p(tb), p(off), None, None, 0, None, None, None)
+        assert rc == _lib.ERR_CAPACITY
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(off.cpu().numpy(), so)
+
+
 def test_rays_entering_from_outside():
     g, _ = gen.config1(10)
     rng = gen.rng_for(310)
