@@ -144,70 +144,93 @@ __device__ __forceinline__ int key64(const Hot &h, int w) {
     return w < 0 ? w : hdr_caller(__ldg(&h.cells[w]));
 }
 
-__device__ __forceinline__ bool better64(const Hot &h, double s, int w, double bs, int bw, bool have) {
+// FRAC: candidates are compared as fractions s = num / den with den > 0,
+// num_a den_b < num_b den_a, two products instead of a division per
+// candidate; only the winner's s is divided out, with the same operations
+// as the oracle's, so its length is bit-identical. The products round where
+// the quotients would, so the choice can differ from a comparison of
+// rounded quotients only between candidates whose quotients agree to about
+// one ulp (near ties, where either exit is correct to that precision). The
+// float64 form uses it; the float32 form's recheck, rare and inlined into a
+// kernel whose occupancy is set by its registers, divides per candidate
+// (n holds s there and d is unused).
+template <bool FRAC>
+__device__ __forceinline__ bool better64(const Hot &h, double n, double d, int w, double bn, double bd, int bw,
+                                         bool have) {
     if (!have) return true;
-    if (s < bs) return true;
-    if (s > bs) return false;
+    const double l = FRAC ? __dmul_rn(n, bd) : n, r = FRAC ? __dmul_rn(bn, d) : bn;
+    if (l < r) return true;
+    if (l > r) return false;
     return key64(h, w) < key64(h, bw);
 }
 
 // One record: bisector of the current site and the record's site (Eq. 1-4),
-// or a wall (Eq. 5). Returns false if it is not a candidate (n.k <= 0).
+// or a wall (Eq. 5), as the fraction num / den (num >= 0, den > 0). Returns
+// false if it is not a candidate (n.k <= 0).
 __device__ __forceinline__ bool plane64(const GridDev *gp, float4 q, double pmx, double pmy, double pmz,
-                                        const double *r, const double *k, double &s) {
+                                        const double *r, const double *k, double &num, double &den) {
     const int w = rec_w(q);
     if (w >= 0) {
         const double px = (double)q.x, py = (double)q.y, pz = (double)q.z;
         const double nx = __dsub_rn(px, pmx), ny = __dsub_rn(py, pmy), nz = __dsub_rn(pz, pmz);
-        const double den = __dadd_rn(__dadd_rn(__dmul_rn(nx, k[0]), __dmul_rn(ny, k[1])), __dmul_rn(nz, k[2]));
+        den = __dadd_rn(__dadd_rn(__dmul_rn(nx, k[0]), __dmul_rn(ny, k[1])), __dmul_rn(nz, k[2]));
         if (!(den > 0.0)) return false;
         const double wx = __dsub_rn(__dmul_rn(__dadd_rn(px, pmx), 0.5), r[0]);
         const double wy = __dsub_rn(__dmul_rn(__dadd_rn(py, pmy), 0.5), r[1]);
         const double wz = __dsub_rn(__dmul_rn(__dadd_rn(pz, pmz), 0.5), r[2]);
-        double num = __dadd_rn(__dadd_rn(__dmul_rn(nx, wx), __dmul_rn(ny, wy)), __dmul_rn(nz, wz));
+        num = __dadd_rn(__dadd_rn(__dmul_rn(nx, wx), __dmul_rn(ny, wy)), __dmul_rn(nz, wz));
         if (num < 0.0) num = 0.0;
-        s = __ddiv_rn(num, den);
         return true;
     }
     if (w < -6) return false;
     const int wi = -w - 1, axis = wi >> 1, hi = wi & 1;
     const double kc = k[axis];
     if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
+    // (bound - r) / k as a fraction with a positive denominator: the
+    // negated difference is the exact negation of the rounded one
     const double bound = hi ? gp->hi[axis] : gp->lo[axis];
-    const double v = __ddiv_rn(__dsub_rn(bound, r[axis]), kc);
-    s = v < 0.0 ? 0.0 : v;
+    const double v = hi ? __dsub_rn(bound, r[axis]) : __dsub_rn(r[axis], bound);
+    num = v < 0.0 ? 0.0 : v;
+    den = fabs(kc);
     return true;
 }
 
 // Exit of the cell whose records are blk[1..cnt] for the group: the
 // lexicographically smallest (s, id); returns the winner's record position
-// (1-based) or 0 if there is no candidate.
-template <int LPR>
+// (1-based) or 0 if there is no candidate, and its s in bs.
+template <int LPR, bool FRAC>
 __device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const float4 *blk, int cnt, double pmx,
                                       double pmy, double pmz, const double *r, const double *k, unsigned gmask,
                                       int gl, double &bs) {
-    bs = 0.0;
+    double bn = 0.0, bd = 1.0;
     int bp = 0, bw = 0;
     for (int p = 1 + gl; p <= cnt; p += LPR) {
         const float4 q = __ldg(blk + p);
-        double s;
-        if (plane64(gp, q, pmx, pmy, pmz, r, k, s) && better64(h, s, rec_w(q), bs, bw, bp != 0)) {
-            bs = s;
-            bp = p;
-            bw = rec_w(q);
+        double n, d;
+        if (plane64(gp, q, pmx, pmy, pmz, r, k, n, d)) {
+            if (!FRAC) n = __ddiv_rn(n, d);
+            if (better64<FRAC>(h, n, d, rec_w(q), bn, bd, bw, bp != 0)) {
+                bn = n;
+                if (FRAC) bd = d;
+                bp = p;
+                bw = rec_w(q);
+            }
         }
     }
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) {
-        const double os = __shfl_xor_sync(gmask, bs, o);
+        const double on = __shfl_xor_sync(gmask, bn, o);
+        const double od = FRAC ? __shfl_xor_sync(gmask, bd, o) : 1.0;
         const int op = __shfl_xor_sync(gmask, bp, o);
         const int ow = __shfl_xor_sync(gmask, bw, o);
-        if (op != 0 && better64(h, os, ow, bs, bw, bp != 0)) {
-            bs = os;
+        if (op != 0 && better64<FRAC>(h, on, od, ow, bn, bd, bw, bp != 0)) {
+            bn = on;
+            if (FRAC) bd = od;
             bp = op;
             bw = ow;
         }
     }
+    bs = bp == 0 ? 0.0 : (FRAC ? __ddiv_rn(bn, bd) : bn);
     return bp;
 }
 
@@ -697,7 +720,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         int nextB = 0;         // block offset of the next cell (same form as B)
         float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);  // float64 form: the winner's record
         if (FP64) {
-            const int win = exit64<LPR>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
+            const int win =
+                exit64<LPR, true>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
             if (win > 0) {
                 qn = __ldg(blk + win);
                 found = true;
@@ -776,8 +800,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 }
                 const float4 *ablk = h.cells + rec_w(hdr1);
                 const int acnt = hdr_count(__ldg(ablk));
-                const int win = exit64<LPR>(h, gp, ablk, acnt, (double)pmx, (double)pmy, (double)pmz, rp, kd, gmask,
-                                            gl, s64);
+                const int win = exit64<LPR, false>(h, gp, ablk, acnt, (double)pmx, (double)pmy, (double)pmz, rp, kd,
+                                                   gmask, gl, s64);
                 if (win > 0) {
                     const float4 qa = __ldg(ablk + win);
                     found = true;
