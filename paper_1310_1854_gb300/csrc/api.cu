@@ -87,6 +87,7 @@ struct vgrid {
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
     float4 *d_cells = nullptr;
+    float4 *d_rec64 = nullptr;       // float64 form: exact differences per entry of d_cells
     float4 *d_rel = nullptr;
     int32_t *d_perm = nullptr;
     int32_t *d_blk_off = nullptr;
@@ -208,7 +209,7 @@ static void free_grid(vgrid_t *g) {
     }
     if (g->s_h2d) cudaStreamDestroy(g->s_h2d);
     if (g->s_d2h) cudaStreamDestroy(g->s_d2h);
-    void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
+    void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rec64, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
                     g->d_order, g->d_perm,  g->d_blk_off, g->d_blk_rec, g->d_queue, g->d_stats, g->d_set,
                     g->d_start, g->d_scan,  g->d_entry, g->d_slots, g->d_chunk_meta, g->d_chunk_inv, g->d_coff, g->d_cursor};
     for (void *p : ptrs)
@@ -477,6 +478,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     }
     VG_ALLOC(g->d_site, M);
     VG_ALLOC(g->d_cells, nrec);
+    VG_ALLOC(g->d_rec64, 2 * (size_t)nrec);
     VG_ALLOC(g->d_rel, nrel);
     VG_ALLOC(g->d_perm, M);
     VG_ALLOC(g->d_blk_off, boff.size());
@@ -516,9 +518,15 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         e = cudaMemcpy(g->d_blk_rec, brec.data(), sizeof(float) * brec.size(), cudaMemcpyHostToDevice);
     }
 
+    if (e == cudaSuccess) {
+        e = vg::launch_build_rec64(g->d_site, g->d_rel, g->d_cells, M, nrec, g->d_rec64, g->sms, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+
     GridDev &hd = g->hd;
     hd.site = g->d_site;
     hd.cells = g->d_cells;
+    hd.rec64 = g->d_rec64;
     hd.rel = g->d_rel;
     hd.perm = g->d_perm;
     hd.blk_off = g->d_blk_off;

@@ -465,6 +465,56 @@ cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchun
     return cudaGetLastError();
 }
 
+// exact float64 sum of two floats? (the TwoSum error term is zero)
+__device__ __forceinline__ bool exact_sum(double a, double b) {
+    const double s = __dadd_rn(a, b), bb = __dsub_rn(s, a);
+    return __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb)) == 0.0;
+}
+
+// One thread per cell: the records of its absolute block get n = p_j - p_m
+// in float64 (site coordinates are floats, so n is exact unless their
+// exponents lie far apart; then the flag sends the kernel back to the float
+// coordinates, as it does for p_j + p_m).
+__global__ void build_rec64_kernel(const float4 *site, const float4 *rel, const float4 *cells, int64_t M,
+                                   float4 *rec64) {
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        const float4 sm = site[m];
+        const int A = __float_as_int(rel[__float_as_int(sm.w) + 1].w);
+        const int cnt = __float_as_int(cells[A].y);
+        rec64[2 * (int64_t)A] = make_float4(0.f, 0.f, 0.f, 0.f);
+        rec64[2 * (int64_t)A + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const double pm[3] = {(double)sm.x, (double)sm.y, (double)sm.z};
+        for (int p = 1; p <= cnt; p++) {
+            const float4 q = cells[A + p];
+            const int w = __float_as_int(q.w);
+            double n[3] = {0.0, 0.0, 0.0};
+            int flag = 0;
+            if (w >= 0) {
+                const double pj[3] = {(double)q.x, (double)q.y, (double)q.z};
+                for (int c = 0; c < 3; c++) {
+                    n[c] = __dsub_rn(pj[c], pm[c]);
+                    if (!exact_sum(pj[c], -pm[c]) || !exact_sum(pj[c], pm[c])) flag = 1;
+                }
+            }
+            const int64_t at = 2 * ((int64_t)A + p);
+            rec64[at] = make_float4(__int_as_float(__double2loint(n[0])), __int_as_float(__double2hiint(n[0])),
+                                    __int_as_float(__double2loint(n[1])), __int_as_float(__double2hiint(n[1])));
+            rec64[at + 1] = make_float4(__int_as_float(__double2loint(n[2])), __int_as_float(__double2hiint(n[2])),
+                                        __int_as_float(w), __int_as_float(flag));
+        }
+    }
+}
+
+cudaError_t launch_build_rec64(const float4 *site, const float4 *rel, const float4 *cells, int64_t M, int64_t nrec,
+                               float4 *rec64, int sms, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    (void)nrec;
+    const int blocks = (int)std::min<int64_t>((M + 127) / 128, (int64_t)sms * 16);
+    build_rec64_kernel<<<blocks, 128, 0, s>>>(site, rel, cells, M, rec64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 cudaError_t launch_exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t s) {

@@ -75,6 +75,11 @@ struct GridDev {
     const int32_t *perm;
     const int32_t *blk_off;
     const float4 *blk_rec;
+    // float64 form: per entry of `cells`, 32 bytes (two float4) holding the
+    // record's n = p_j - p_m as three doubles, its id (neighbour's offset in
+    // `cells`, or wall id) and a flag set where n or p_j + p_m is not exact
+    // in float64 (then the record is evaluated from its float coordinates)
+    const float4 *rec64;
     double lo[3], hi[3];      // domain box
     double bscale[3];         // blocks per unit length along each axis
     int64_t lokey[3], hikey[3];        // order keys of lo and hi (exact box test)

@@ -100,6 +100,10 @@ cudaError_t launch_locate(const GridDev *grids, const RaySetDev *sets, int nsets
                           int32_t *out_caller, int sms, cudaStream_t s);
 cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm, const float4 *site, int64_t M,
                                    float4 *cells, float4 *rel, cudaStream_t s);
+// the float64 form's table of exact differences (GridDev::rec64) for the
+// nrec entries of `cells`
+cudaError_t launch_build_rec64(const float4 *site, const float4 *rel, const float4 *cells, int64_t M, int64_t nrec,
+                               float4 *rec64, int sms, cudaStream_t s);
 // copy the segments in chunks 0..nchunks-1 (see kSegChunk) of rays 0..N-1
 // into the CSR arrays at the scanned offsets off[0..N]; coff holds N+1 and
 // inv nchunks values of scratch, scan_tmp scan_tmp_elems(N)

@@ -164,6 +164,22 @@ __device__ __forceinline__ bool better64(const Hot &h, double n, double d, int w
     return key64(h, w) < key64(h, bw);
 }
 
+// A wall (Eq. 5) as the fraction num / den; false unless the ray faces it.
+__device__ __forceinline__ bool wall64(const GridDev *gp, int w, const double *r, const double *k, double &num,
+                                      double &den) {
+    if (w < -6) return false;
+    const int wi = -w - 1, axis = wi >> 1, hi = wi & 1;
+    const double kc = k[axis];
+    if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
+    // (bound - r) / k as a fraction with a positive denominator: the
+    // negated difference is the exact negation of the rounded one
+    const double bound = hi ? gp->hi[axis] : gp->lo[axis];
+    const double v = hi ? __dsub_rn(bound, r[axis]) : __dsub_rn(r[axis], bound);
+    num = v < 0.0 ? 0.0 : v;
+    den = fabs(kc);
+    return true;
+}
+
 // One record: bisector of the current site and the record's site (Eq. 1-4),
 // or a wall (Eq. 5), as the fraction num / den (num >= 0, den > 0). Returns
 // false if it is not a candidate (n.k <= 0).
@@ -182,38 +198,67 @@ __device__ __forceinline__ bool plane64(const GridDev *gp, float4 q, double pmx,
         if (num < 0.0) num = 0.0;
         return true;
     }
-    if (w < -6) return false;
-    const int wi = -w - 1, axis = wi >> 1, hi = wi & 1;
-    const double kc = k[axis];
-    if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
-    // (bound - r) / k as a fraction with a positive denominator: the
-    // negated difference is the exact negation of the rounded one
-    const double bound = hi ? gp->hi[axis] : gp->lo[axis];
-    const double v = hi ? __dsub_rn(bound, r[axis]) : __dsub_rn(r[axis], bound);
-    num = v < 0.0 ? 0.0 : v;
-    den = fabs(kc);
+    return wall64(gp, w, r, k, num, den);
+}
+
+// float64 form, one record of the table of exact differences (see
+// GridDev::rec64): the same num and den as plane64 on the float record, with
+// fewer float64 operations. n = p_j - p_m is stored, and fma(0.5, n, p_m)
+// is (p_j + p_m) / 2 exactly, the value plane64 gets by rounding the sum and
+// halving it, because the table holds only records whose sum and difference
+// are exact; the flagged others go through plane64.
+__device__ __forceinline__ bool plane64x(const GridDev *gp, const float4 *crec, float4 xa, float4 xb, double pmx,
+                                         double pmy, double pmz, const double *r, const double *k, double &num,
+                                         double &den) {
+    const int w = __float_as_int(xb.z);
+    if (w < 0) return wall64(gp, w, r, k, num, den);
+    if (__float_as_int(xb.w) != 0) return plane64(gp, __ldg(crec), pmx, pmy, pmz, r, k, num, den);
+    const double nx = __hiloint2double(__float_as_int(xa.y), __float_as_int(xa.x));
+    const double ny = __hiloint2double(__float_as_int(xa.w), __float_as_int(xa.z));
+    const double nz = __hiloint2double(__float_as_int(xb.y), __float_as_int(xb.x));
+    den = __dadd_rn(__dadd_rn(__dmul_rn(nx, k[0]), __dmul_rn(ny, k[1])), __dmul_rn(nz, k[2]));
+    if (!(den > 0.0)) return false;
+    const double wx = __dsub_rn(__fma_rn(0.5, nx, pmx), r[0]);
+    const double wy = __dsub_rn(__fma_rn(0.5, ny, pmy), r[1]);
+    const double wz = __dsub_rn(__fma_rn(0.5, nz, pmz), r[2]);
+    num = __dadd_rn(__dadd_rn(__dmul_rn(nx, wx), __dmul_rn(ny, wy)), __dmul_rn(nz, wz));
+    if (num < 0.0) num = 0.0;
     return true;
 }
 
 // Exit of the cell whose records are blk[1..cnt] for the group: the
 // lexicographically smallest (s, id); returns the winner's record position
 // (1-based) or 0 if there is no candidate, and its s in bs.
+// FRAC (the float64 form) reads the records from x64, the block's entries
+// of the table of exact differences (two float4 per entry), and blk only for
+// flagged records; otherwise it reads the float records of blk.
 template <int LPR, bool FRAC>
-__device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const float4 *blk, int cnt, double pmx,
-                                      double pmy, double pmz, const double *r, const double *k, unsigned gmask,
-                                      int gl, double &bs) {
+__device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const float4 *blk, const float4 *x64, int cnt,
+                                      double pmx, double pmy, double pmz, const double *r, const double *k,
+                                      unsigned gmask, int gl, double &bs) {
     double bn = 0.0, bd = 1.0;
     int bp = 0, bw = 0;
     for (int p = 1 + gl; p <= cnt; p += LPR) {
-        const float4 q = __ldg(blk + p);
         double n, d;
-        if (plane64(gp, q, pmx, pmy, pmz, r, k, n, d)) {
+        int w;
+        bool cand;
+        if (FRAC) {
+            float4 xa, xb;
+            ldg_pair(x64 + 2 * p, xa, xb);  // 32-byte entries
+            w = __float_as_int(xb.z);
+            cand = plane64x(gp, blk + p, xa, xb, pmx, pmy, pmz, r, k, n, d);
+        } else {
+            const float4 q = __ldg(blk + p);
+            w = rec_w(q);
+            cand = plane64(gp, q, pmx, pmy, pmz, r, k, n, d);
+        }
+        if (cand) {
             if (!FRAC) n = __ddiv_rn(n, d);
-            if (better64<FRAC>(h, n, d, rec_w(q), bn, bd, bw, bp != 0)) {
+            if (better64<FRAC>(h, n, d, w, bn, bd, bw, bp != 0)) {
                 bn = n;
                 if (FRAC) bd = d;
                 bp = p;
-                bw = rec_w(q);
+                bw = w;
             }
         }
     }
@@ -720,8 +765,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         int nextB = 0;         // block offset of the next cell (same form as B)
         float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);  // float64 form: the winner's record
         if (FP64) {
-            const int win =
-                exit64<LPR, true>(h, gp, blk, cnt, (double)pmx, (double)pmy, (double)pmz, r64, k64, gmask, gl, s64);
+            const int win = exit64<LPR, true>(h, gp, blk, a.g1.rec64 + 2 * (int64_t)B, cnt, (double)pmx, (double)pmy,
+                                              (double)pmz, r64, k64, gmask, gl, s64);
             if (win > 0) {
                 qn = __ldg(blk + win);
                 found = true;
@@ -800,8 +845,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 }
                 const float4 *ablk = h.cells + rec_w(hdr1);
                 const int acnt = hdr_count(__ldg(ablk));
-                const int win = exit64<LPR, false>(h, gp, ablk, acnt, (double)pmx, (double)pmy, (double)pmz, rp, kd,
-                                                   gmask, gl, s64);
+                const int win = exit64<LPR, false>(h, gp, ablk, nullptr, acnt, (double)pmx, (double)pmy, (double)pmz,
+                                                   rp, kd, gmask, gl, s64);
                 if (win > 0) {
                     const float4 qa = __ldg(ablk + win);
                     found = true;

@@ -118,6 +118,24 @@ def test_cubic_lattice_parity():
     run_case(g, rays, ref)
 
 
+def test_tiny_coordinates_parity():
+    """Sites with tiny nonzero coordinates next to ordinary ones: their float
+    differences and sums round in float64, so the float64 form takes those
+    records from the float coordinates instead of its table of exact
+    differences; it must still match the oracle bit for bit."""
+    rng = gen.rng_for(107)
+    S = rng.uniform(-1.0, 1.0, (1500, 3))
+    pick = rng.choice(len(S), 200, replace=False)
+    axis = rng.integers(0, 3, 200)
+    S[pick, axis] = rng.choice([-1.0, 1.0], 200) * 10.0 ** rng.uniform(-30, -9, 200)
+    S = S.astype(np.float32).astype(np.float64)
+    S = np.unique(S, axis=0)
+    g = gen.Grid(S, gen.CUBE_BOX.copy(), rng.uniform(0.5, 1.5, len(S)).astype(np.float32))
+    rays = gen.uniform_rays(3000, 108)
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref)
+
+
 def test_locate_parity():
     g = gen.make_disk_grid(20_000, 107)
     vg = make(g)
