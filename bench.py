@@ -213,7 +213,7 @@ def main():
     ap.add_argument("--block", type=int, default=int(os.environ.get("VGRID_BLOCK", "0")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rays", type=int, default=1_000_000)
-    ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6", "segments1e5"],
+    ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6", "segments1e5", "next"],
                     help="disk1e5 is the benchmark line; the others measure the remaining workloads")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -413,6 +413,8 @@ def run_extra(args):
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
     sampler = ClockSampler(gpu_index(0))
+    if args.workload == "next":
+        return run_next(args, line, flush, sampler)
     if args.workload == "segments1e5":
         g, _ = gen.config2(n_rays=1)
         rays = gen.disk_rays(args.rays, gen.SEED_BASE + 2 + 1000)
@@ -550,6 +552,84 @@ def run_extra(args):
                                 "host_build_s": round(build_s, 2), "l2": "flushed between timed steps"},
                      "stats_per_step": st, "rays_per_s": st["rays"] * args.steps / (ms / 1e3),
                      "gpu_launches": n_kernels, "roofline": None, "e2e": None, "clocks": clocks})
+    print(json.dumps(line), flush=True)
+
+
+def run_next(args, base, flush, sampler):
+    """One line per row built after the hot path: Monte Carlo interaction
+    sampling along the path, rays entering from outside the box, and C(r)
+    at uniform points for the grid-quality measure (Table 1)."""
+    import torch
+
+    import gen
+    from paper_1310_1854_gb300 import VoronoiGrid
+    from paper_1310_1854_gb300.quality import grid_quality, sample_points
+    dev = torch.device("cuda", 0)
+    g, _ = gen.config2(n_rays=1)
+    vg = VoronoiGrid(g.sites, g.box)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    N = args.rays
+    rays = gen.disk_rays(N, gen.SEED_BASE + 2 + 1000)
+    O = torch.from_numpy(rays.origin).to(dev)
+    D = torch.from_numpy(rays.dir).to(dev)
+    rng = gen.rng_for(gen.SEED_BASE + 77)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        sampler.start()
+        n0 = kernel_launches()
+        ms = _events_ms(fn, steps, flush)
+        return ms / steps, kernel_launches() - n0, sampler.stop()
+
+    # f1: tau_int = -ln(xi) per package; the package stops in the cell where
+    # the running tau reaches it, and the absorbed weight is booked per cell
+    tau_int = torch.from_numpy(-np.log(rng.random(N))).to(dev, torch.float32)
+    absorbed = torch.zeros(g.sites.shape[0], dtype=torch.float32, device=dev)
+    cell, _, _ = vg.interact(O, D, tau_int, absorbed=absorbed)
+    interacted = int((cell >= 0).sum().item())
+    ms, nk, clocks = timed(lambda: vg.interact(O, D, tau_int, absorbed=absorbed), args.steps)
+    line = dict(base, metric="Monte Carlo photon packages/sec (interaction point sampled along the path)",
+                unit="packages/s", value=N / (ms / 1e3), ms_per_step=ms, gpu_launches=nk, clocks=clocks,
+                config={"workload": "exp-disk 1e5 sites, 1e6 packages from the disk sampler, tau_int = -ln xi, "
+                                    "absorbed weight booked per cell", "sites": g.sites.shape[0], "packages": N,
+                        "interacting": interacted, "l2": "flushed between timed steps"},
+                roofline=None, e2e=None)
+    print(json.dumps(line), flush=True)
+
+    # f2: rays from a sphere around the box aimed at uniform points inside it
+    c = 0.5 * (g.box[:3] + g.box[3:])
+    R = 0.6 * float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    u = rng.standard_normal((N, 3))
+    org = c + R * u / np.linalg.norm(u, axis=1, keepdims=True)
+    tgt = sample_points(g.box, N, gen.SEED_BASE + 78)
+    dirs = tgt - org
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    Oe = torch.from_numpy(org).to(dev)
+    De = torch.from_numpy(dirs).to(dev)
+    st = vg.trace(Oe, De, precision="fp32", stats=True, enter=True).stats
+    tau = torch.empty(N, dtype=torch.float32, device=dev)
+    ms, nk, clocks = timed(lambda: vg.trace(Oe, De, precision="fp32", out_tau=tau, enter=True), args.steps)
+    line = dict(base, value=st["crossings"] / (ms / 1e3), ms_per_step=ms, gpu_launches=nk, clocks=clocks,
+                config={"workload": "exp-disk 1e5 sites, 1e6 rays from a sphere around the box aimed at uniform "
+                                    "points inside it (entry point by the slab test, then the same traversal)",
+                        "sites": g.sites.shape[0], "rays": N, "l2": "flushed between timed steps"},
+                stats_per_step=st, roofline=None, e2e=None)
+    print(json.dumps(line), flush=True)
+
+    # f3: C(r) at 1e7 uniform points of the 1e6-site disk (Table 1's measure)
+    g5, _, _, _ = gen.config5(npix=1, n_interior=1)
+    v5 = VoronoiGrid(g5.sites, g5.box)
+    P = torch.from_numpy(sample_points(g5.box, 10_000_000, gen.SEED_BASE + 79)).to(dev)
+    ms, nk, clocks = timed(lambda: v5.locate(P), args.steps)
+    q = grid_quality(v5, g5.rho, gen.disk_density, n_points=10_000_000)
+    line = dict(base, metric="C(r) point locations/sec (grid-quality sampling, Table 1)", unit="points/s",
+                value=P.shape[0] / (ms / 1e3), ms_per_step=ms, gpu_launches=nk, clocks=clocks,
+                config={"workload": "exp-disk 1e6 sites, 1e7 uniform points of the box, float32 distances with "
+                                    "float64 recheck", "sites": g5.sites.shape[0], "points": P.shape[0],
+                        "l2": "flushed between timed steps"},
+                quality={"std_rho_t_minus_rho_g": q["std"], "mean": q["mean"], "points": q["points"]},
+                roofline=None, e2e=None)
     print(json.dumps(line), flush=True)
 
 
