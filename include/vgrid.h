@@ -249,11 +249,14 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
  * output), with the copies overlapped with the traversal. Each chunk of
  * rays goes through one of two device slots that alternate across chunks and
  * calls: its origins and directions are copied in on a copy stream as soon
- * as the slot's previous traversal is done, it is traced on `stream`, and its
- * tau (and status) are copied out on a second copy stream. Consecutive calls
- * therefore overlap: the next call's rays go in while this call's traversal
- * runs. Host buffers should be page-locked (cudaHostAlloc, pinned tensors)
- * for the copies to overlap; pageable buffers work, serialised.
+ * as the slot's previous traversal is done, and it is traced on `stream`.
+ * If tau (and ray_status, when given) are page-locked host memory mapped
+ * into the device's address space (cudaHostAlloc and pinned tensors are,
+ * with unified addressing), the traversal writes them directly; otherwise
+ * they are copied out from the slot on a second copy stream. Consecutive
+ * calls therefore overlap: the next call's rays go in while this call's
+ * traversal runs. Host buffers should be page-locked for the copies to
+ * overlap; pageable buffers work, serialised.
  *   origin, dir   host float64[N*3], unit directions as for vgrid_trace
  *   precision     VGRID_FP64 or VGRID_FP32_RECHECK
  *   tau           host float64[N] (FP64) or float32[N] (FP32_RECHECK)

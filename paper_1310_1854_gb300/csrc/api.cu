@@ -1059,6 +1059,27 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
             VG_CUDA(cudaEventCreateWithFlags(&g->ev_out[k], cudaEventDisableTiming));
         }
     }
+    // Results go straight into the caller's memory when the device can
+    // write it (pinned host memory is mapped into the device's address
+    // space): no copy out, and the next call's traversal need not wait for
+    // one. Otherwise they go through the slots and a copy out.
+    char *tau_dev = nullptr;
+    int32_t *st_dev = nullptr;
+    {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, tau) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer)
+            tau_dev = static_cast<char *>(at.devicePointer);
+        if (tau_dev && ray_status) {
+            cudaPointerAttributes as{};
+            if (cudaPointerGetAttributes(&as, ray_status) == cudaSuccess && as.type == cudaMemoryTypeHost &&
+                as.devicePointer)
+                st_dev = static_cast<int32_t *>(as.devicePointer);
+            else
+                tau_dev = nullptr;
+        }
+        cudaGetLastError();  // a pointer the runtime does not know is not an error here
+    }
+    const bool direct = tau_dev != nullptr;
     // slots alternate across chunks and calls; a slot's events order its
     // reuse after the traversal and the copy out that last used it
     const int64_t nchunks = (N + chunk - 1) / chunk;
@@ -1074,9 +1095,13 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
         // trace once the rays are in and the slot's previous results are out
         VG_CUDA(cudaStreamWaitEvent(s, g->ev_in[k], 0));
         VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k], 0));
-        int rc = trace_tau_chunk(g, dO, dD, n, fp64, g->d_hout[k], ray_status ? g->d_hst[k] : nullptr, c == 0, s);
+        int rc = direct ? trace_tau_chunk(g, dO, dD, n, fp64, tau_dev + tau_sz * first,
+                                          st_dev ? st_dev + first : nullptr, c == 0, s)
+                        : trace_tau_chunk(g, dO, dD, n, fp64, g->d_hout[k], ray_status ? g->d_hst[k] : nullptr,
+                                          c == 0, s);
         if (rc) return rc;
         VG_CUDA(cudaEventRecord(g->ev_k[k], s));
+        if (direct) continue;
         // results out
         VG_CUDA(cudaStreamWaitEvent(g->s_d2h, g->ev_k[k], 0));
         VG_CUDA(cudaMemcpyAsync(static_cast<char *>(tau) + tau_sz * first, g->d_hout[k], tau_sz * n,
@@ -1087,8 +1112,9 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
         VG_CUDA(cudaEventRecord(g->ev_out[k], g->s_d2h));
     }
     g->host_slot = k;
-    // `stream` continues after the last copy out
-    VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k ^ 1], 0));
+    // `stream` continues after the last copy out (direct writes are done
+    // when the traversal on `stream` is)
+    if (!direct) VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k ^ 1], 0));
     if (stats) return read_stats(g->d_stats, stats, s);  // synchronises
     return VGRID_OK;
 }

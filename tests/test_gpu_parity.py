@@ -485,7 +485,8 @@ def test_host_pipelined_trace_matches_device_trace():
     """vgrid_trace_host (rays and results in host memory, copies overlapped
     with the traversal) gives the tau, status and counters of vgrid_trace on
     the same rays: one chunk, several with a ragged last one, pageable
-    buffers, the float64 form, and calls queued back to back."""
+    buffers, pinned rays with a pageable result, the float64 form, and calls
+    queued back to back."""
     g, rays = gen.config2(n_rays=300_000)
     vg = make(g)
     N = len(rays.origin)
@@ -504,6 +505,10 @@ def test_host_pipelined_trace_matches_device_trace():
                 assert r.stats[key] == ref.stats[key], (prec, chunk, key)
     r = vg.trace_host(torch.from_numpy(rays.origin), torch.from_numpy(rays.dir), chunk=123_457)
     t32 = vg.trace(O, D).tau.cpu().numpy()
+    np.testing.assert_array_equal(r.tau.numpy(), t32)
+    # pinned rays, pageable tau: results through the slots and a copy out
+    # (pinned tau is written by the traversal directly)
+    r = vg.trace_host(Oh, Dh, out_tau=torch.empty(N, dtype=torch.float32), chunk=100_000)
     np.testing.assert_array_equal(r.tau.numpy(), t32)
     assert vg.trace_host(Oh[:0], Dh[:0]).tau.numel() == 0
     # queued calls back to back (the next call's copies overlap this traversal)
