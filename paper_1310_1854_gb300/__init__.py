@@ -96,6 +96,7 @@ class VoronoiGrid:
         self.M = S.shape[0]
         self.box = B.copy()
         self.kappa = 1.0
+        self._seg_per_ray = None  # segments per ray of the last segment-list call
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -185,7 +186,17 @@ class VoronoiGrid:
                                   _ptr(st), sref, _stream(stream)))
             return TraceResult(tau, status=st, stats=cs.as_dict() if cs is not None else None)
         seg_off = torch.empty(N + 1, dtype=torch.int64, device=self.device)
-        cap = int(seg_capacity) if seg_capacity is not None else 0
+        if seg_capacity is not None:
+            cap = int(seg_capacity)
+        elif self._seg_per_ray is not None:
+            # a guess from the last call (one traversal when it is enough;
+            # otherwise the call reports the total and runs again); large
+            # calls count first rather than size buffers on a guess
+            cap = int(N * self._seg_per_ray * 1.25) + 1024
+            if cap > (1 << 27):
+                cap = 0
+        else:
+            cap = 0  # the first call counts, then traces again with the total
         cells = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
         lens = torch.empty(max(cap, 1), dtype=tdt, device=self.device)
         rc = lib.vgrid_trace(self._h, _ptr(O), _ptr(D), N, prec, _lib.SEGMENTS | flag, _ptr(tau), _ptr(seg_off),
@@ -198,6 +209,8 @@ class VoronoiGrid:
                                  _ptr(cells), _ptr(lens), total, _ptr(st), sref, _stream(stream))
         check(rc)
         total = int(seg_off[N].item())
+        if N > 0:
+            self._seg_per_ray = total / N
         return TraceResult(tau, seg_off, cells[:total], lens[:total], st, cs.as_dict())
 
     def trace_host(self, origin, direction, precision="fp32", out_tau=None, status=False, stats=False, chunk=0,
