@@ -255,14 +255,18 @@ __device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, d
     return nf2 >= 4 ? 1 : -1;
 }
 
+// Persistent threads: each takes its next cell from a global counter as soon
+// as it has finished one, so a thread whose cell needed few cuts does not
+// wait for the slowest cell of its block.
 __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, BucketGrid bg, const int64_t *boff,
                                                     const int *bsites, double box0, double box1, double box2,
                                                     double box3, double box4, double box5, double eps, int *out_cnt,
-                                                    int *out_nbr, double *out_vol, double *out_bbox, int *out_fail) {
+                                                    int *out_nbr, double *out_vol, double *out_bbox, int *out_fail,
+                                                    unsigned long long *next) {
     DPoly P;
     Scratch W;
     const double box[6] = {box0, box1, box2, box3, box4, box5};
-    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t m = (int64_t)atomicAdd(next, 1ull); m < M; m = (int64_t)atomicAdd(next, 1ull)) {
         const double px = S[3 * m], py = S[3 * m + 1], pz = S[3 * m + 2];
         poly_box(P, box);
         double rmax = sqrt(poly_rmax2(P, px, py, pz));
@@ -398,9 +402,15 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
         return bad(e, "copy");
     bucket_fill_kernel<<<blocks, 256>>>(bidx, M, cursor, bsites);
     bucket_sort_kernel<<<(int)std::min<int64_t>((K + 255) / 256, 65535), 256>>>(boff, K, bsites);
-    const int cblocks = (int)std::min<int64_t>((M + 127) / 128, 1 << 20);
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cells_kernel, 128, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((M + 127) / 128, (int64_t)per_sm * sms));
+    if ((e = cudaMemset(cursor, 0, sizeof(unsigned long long))) != cudaSuccess) return bad(e, "memset");
     cells_kernel<<<cblocks, 128>>>(dS, M, bg, boff, bsites, box[0], box[1], box[2], box[3], box[4], box[5], eps, cnt,
-                                   nbr, vol, bbox, fail);
+                                   nbr, vol, bbox, fail, reinterpret_cast<unsigned long long *>(cursor));
     count_launches(4);  // bucket count, fill, sort, cells (the scan counts its own)
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cells kernel");
     std::vector<int> hcnt(M), hfail(M), hnbr((size_t)kCap * M);
