@@ -249,7 +249,9 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
  * output), with the copies overlapped with the traversal. Each chunk of
  * rays goes through one of two device slots that alternate across chunks and
  * calls: its origins and directions are copied in on a copy stream as soon
- * as the slot's previous traversal is done, and it is traced on `stream`.
+ * as the slot's previous traversal is done, its start records (and ray
+ * order) are prepared on a third stream once they are in, so that this runs
+ * beside the previous chunk's traversal, and it is traced on `stream`.
  * If tau (and ray_status, when given) are page-locked host memory mapped
  * into the device's address space (cudaHostAlloc and pinned tensors are,
  * with unified addressing), the traversal writes them directly; otherwise
@@ -269,8 +271,10 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
  * Without stats the call returns once everything is queued: the results are
  * in host memory when `stream` has been synchronised, and the host buffers
  * must stay untouched until then. The first call with a larger chunk than
- * before synchronises the device and allocates two device slots (56 bytes
- * per ray each); the first call creates two copy streams.
+ * before synchronises the device and allocates two device slots (125 bytes
+ * per ray each: rays, result, status, start record, order); the first call
+ * creates three streams. A call with stats prepares its start records on
+ * `stream`, after the previous traversal.
  */
 int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,
                      int32_t *ray_status, int64_t chunk, vgrid_stats *stats, vgrid_stream_t stream);

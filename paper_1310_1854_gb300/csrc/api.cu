@@ -124,10 +124,20 @@ struct vgrid {
     double *d_hin[2] = {nullptr, nullptr};  // chunk origins then directions
     void *d_hout[2] = {nullptr, nullptr};   // chunk tau (8 bytes per ray)
     int32_t *d_hst[2] = {nullptr, nullptr}; // chunk status
+    // per slot also the start records, ray order, work counter and set
+    // descriptor, so that a chunk's start records can be prepared on s_loc
+    // while the previous chunk is traced (the start-cell pass then fills the
+    // SMs that the traversal frees in its tail)
+    RayPrep *d_hstart[2] = {nullptr, nullptr};
+    uint8_t *d_hbin[2] = {nullptr, nullptr};
+    int32_t *d_horder[2] = {nullptr, nullptr};
+    uint32_t *d_hhist = nullptr;             // per slot 2 kOrderBins
+    unsigned long long *d_hqueue = nullptr;  // per slot
+    RaySetDev *d_hset = nullptr;             // per slot
     int64_t host_cap = 0;
     int host_slot = 0;
-    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
-    cudaEvent_t ev_in[2] = {}, ev_k[2] = {}, ev_out[2] = {};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr, s_loc = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_k[2] = {}, ev_out[2] = {}, ev_prep[2] = {};
     double build_seconds = 0;
     double phase_seconds[6] = {0, 0, 0, 0, 0, 0};
     int64_t device_bytes = 0;
@@ -185,16 +195,24 @@ static void free_events(vgrid_t *g) {
     g->n_loc = g->n_trace = 0;
 }
 
+// bytes per ray of one host-pipe slot: rays, result, status, start record,
+// order bin and permutation
+constexpr int64_t kSlotBytesPerRay =
+    6 * sizeof(double) + sizeof(double) + sizeof(int32_t) + sizeof(RayPrep) + sizeof(uint8_t) + sizeof(int32_t);
+
 static void free_pipe(vgrid_t *g) {
     for (int k = 0; k < 2; k++) {
-        if (g->d_hin[k]) cudaFree(g->d_hin[k]);
-        if (g->d_hout[k]) cudaFree(g->d_hout[k]);
-        if (g->d_hst[k]) cudaFree(g->d_hst[k]);
+        void *ptrs[] = {g->d_hin[k], g->d_hout[k], g->d_hst[k], g->d_hstart[k], g->d_hbin[k], g->d_horder[k]};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
         g->d_hin[k] = nullptr;
         g->d_hout[k] = nullptr;
         g->d_hst[k] = nullptr;
+        g->d_hstart[k] = nullptr;
+        g->d_hbin[k] = nullptr;
+        g->d_horder[k] = nullptr;
     }
-    g->device_bytes -= g->host_cap * (int64_t)(2 * (6 * sizeof(double) + sizeof(double) + sizeof(int32_t)));
+    g->device_bytes -= g->host_cap * 2 * kSlotBytesPerRay;
     g->host_cap = 0;
 }
 
@@ -207,8 +225,14 @@ static void free_grid(vgrid_t *g) {
         if (g->ev_k[k]) cudaEventDestroy(g->ev_k[k]);
         if (g->ev_out[k]) cudaEventDestroy(g->ev_out[k]);
     }
+    for (int k = 0; k < 2; k++)
+        if (g->ev_prep[k]) cudaEventDestroy(g->ev_prep[k]);
     if (g->s_h2d) cudaStreamDestroy(g->s_h2d);
     if (g->s_d2h) cudaStreamDestroy(g->s_d2h);
+    if (g->s_loc) cudaStreamDestroy(g->s_loc);
+    if (g->d_hhist) cudaFree(g->d_hhist);
+    if (g->d_hqueue) cudaFree(g->d_hqueue);
+    if (g->d_hset) cudaFree(g->d_hset);
     void *ptrs[] = {g->d_desc,  g->d_site,  g->d_cells, g->d_rec64, g->d_rel,   g->d_dens,  g->d_bin,   g->d_hist,
                     g->d_order, g->d_perm,  g->d_blk_off, g->d_blk_rec, g->d_queue, g->d_stats, g->d_set,
                     g->d_start, g->d_scan,  g->d_entry, g->d_slots, g->d_chunk_meta, g->d_chunk_inv, g->d_coff, g->d_cursor};
@@ -875,6 +899,49 @@ int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t
     return VGRID_OK;
 }
 
+// tau (and status) of one chunk of host-resident rays in slot k: its start
+// records (and ray order) are prepared on s_loc once its rays are in and the
+// slot's previous traversal is done, then it is traced on s. The start-cell
+// pass of one chunk can thus run while the previous chunk is traced, in the
+// SMs that traversal frees in its tail. The counters are not reset (calls
+// that read them take trace_tau_chunk instead).
+int trace_chunk_slot(vgrid_t *g, int k, const double *origin, const double *dir, int64_t n, int fp64, void *tau,
+                     int32_t *status, cudaStream_t s) {
+    vgrid_launch L = g->launch;
+    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+    const void *fn = kernels(L.lanes_per_ray).fn[fp64][vg::MODE_TAU];
+    cudaStream_t t = g->s_loc;
+    VG_CUDA(cudaStreamWaitEvent(t, g->ev_in[k], 0));
+    VG_CUDA(cudaStreamWaitEvent(t, g->ev_k[k], 0));
+    RaySetDev set{origin, dir, tau, status, g->d_hstart[k], n, 0, 0, 0};
+    VG_CUDA(vg::launch_prepare(g->d_hset + k, set, g->d_hqueue + k, nullptr, t));
+    const int prep = fp64 ? vg::PREP_FP64 : vg::PREP_FP32;
+    const bool want = n <= INT32_MAX && (L.order == 1 || (L.order == 0 && n >= 2 * resident_lanes(g, fn, L)));
+    const int32_t *order = nullptr;
+    if (want) {
+        const vg::RayOrder ord{g->d_hbin[k], g->d_hhist + 2 * vg::kOrderBins * k, g->d_horder[k]};
+        VG_CUDA(cudaMemsetAsync(ord.hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), t));
+        VG_CUDA(vg::launch_locate_ordered(g->d_desc, g->d_hset + k, 1, n, ord, prep, g->sms, t));
+        VG_CUDA(vg::launch_order(ord, n, g->sms, t));
+        order = ord.order;
+    } else {
+        VG_CUDA(vg::launch_locate(g->d_desc, g->d_hset + k, 1, n, prep, nullptr, g->sms, t));
+    }
+    VG_CUDA(cudaEventRecord(g->ev_prep[k], t));
+    VG_CUDA(cudaStreamWaitEvent(s, g->ev_prep[k], 0));
+    vg::TraceArgs a{};
+    a.grids = g->d_desc;
+    a.sets = g->d_hset + k;
+    a.nsets = 1;
+    a.total = n;
+    a.queue = g->d_hqueue + k;
+    a.stats = g->d_stats;
+    a.g1 = g->hd;
+    a.s1 = set;
+    a.order = order;
+    return launch_trace(fn, L, g->sms, n, a, s);
+}
+
 int read_stats(StatsDev *d, vgrid_stats *out, cudaStream_t s, StatsDev *host_copy = nullptr) {
     StatsDev h{};
     VG_CUDA(cudaMemcpyAsync(&h, d, sizeof(StatsDev), cudaMemcpyDeviceToHost, s));
@@ -1043,6 +1110,9 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
             int rc = dmalloc(&g->d_hin[k], (size_t)(6 * chunk), g->device_bytes);
             if (!rc) rc = dmalloc(reinterpret_cast<double **>(&g->d_hout[k]), (size_t)chunk, g->device_bytes);
             if (!rc) rc = dmalloc(&g->d_hst[k], (size_t)chunk, g->device_bytes);
+            if (!rc) rc = dmalloc(&g->d_hstart[k], (size_t)chunk, g->device_bytes);
+            if (!rc) rc = dmalloc(&g->d_hbin[k], (size_t)chunk, g->device_bytes);
+            if (!rc) rc = dmalloc(&g->d_horder[k], (size_t)chunk, g->device_bytes);
             if (rc) {
                 free_pipe(g);
                 return rc;
@@ -1051,12 +1121,18 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
         g->host_cap = chunk;
     }
     if (!g->s_h2d) {
+        int rc = dmalloc(&g->d_hhist, 2 * 2 * vg::kOrderBins, g->device_bytes);
+        if (!rc) rc = dmalloc(&g->d_hqueue, 2, g->device_bytes);
+        if (!rc) rc = dmalloc(&g->d_hset, 2, g->device_bytes);
+        if (rc) return rc;
         VG_CUDA(cudaStreamCreateWithFlags(&g->s_h2d, cudaStreamNonBlocking));
         VG_CUDA(cudaStreamCreateWithFlags(&g->s_d2h, cudaStreamNonBlocking));
+        VG_CUDA(cudaStreamCreateWithFlags(&g->s_loc, cudaStreamNonBlocking));
         for (int k = 0; k < 2; k++) {
             VG_CUDA(cudaEventCreateWithFlags(&g->ev_in[k], cudaEventDisableTiming));
             VG_CUDA(cudaEventCreateWithFlags(&g->ev_k[k], cudaEventDisableTiming));
             VG_CUDA(cudaEventCreateWithFlags(&g->ev_out[k], cudaEventDisableTiming));
+            VG_CUDA(cudaEventCreateWithFlags(&g->ev_prep[k], cudaEventDisableTiming));
         }
     }
     // Results go straight into the caller's memory when the device can
@@ -1095,10 +1171,12 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
         // trace once the rays are in and the slot's previous results are out
         VG_CUDA(cudaStreamWaitEvent(s, g->ev_in[k], 0));
         VG_CUDA(cudaStreamWaitEvent(s, g->ev_out[k], 0));
-        int rc = direct ? trace_tau_chunk(g, dO, dD, n, fp64, tau_dev + tau_sz * first,
-                                          st_dev ? st_dev + first : nullptr, c == 0, s)
-                        : trace_tau_chunk(g, dO, dD, n, fp64, g->d_hout[k], ray_status ? g->d_hst[k] : nullptr,
-                                          c == 0, s);
+        void *out_tau = direct ? static_cast<void *>(tau_dev + tau_sz * first) : g->d_hout[k];
+        int32_t *out_st = direct ? (st_dev ? st_dev + first : nullptr) : (ray_status ? g->d_hst[k] : nullptr);
+        // without counters to read, the chunk's start records are prepared
+        // beside the previous chunk's traversal (trace_chunk_slot)
+        int rc = stats ? trace_tau_chunk(g, dO, dD, n, fp64, out_tau, out_st, c == 0, s)
+                       : trace_chunk_slot(g, k, dO, dD, n, fp64, out_tau, out_st, s);
         if (rc) return rc;
         VG_CUDA(cudaEventRecord(g->ev_k[k], s));
         if (direct) continue;
