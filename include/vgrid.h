@@ -129,7 +129,7 @@ typedef struct {
     int32_t lanes_per_ray;      /* 1, 2, 4 or 8 lanes cooperate on one ray (default 1) */
     int32_t block;              /* threads per block (multiple of 32, 32..256; default 128) */
     int32_t blocks_per_sm;      /* persistent blocks per SM; 0 = as many as fit */
-    int32_t fp64_lanes_per_ray; /* lanes per ray of the float64 form; 0 = lanes_per_ray (default 4) */
+    int32_t fp64_lanes_per_ray; /* lanes per ray of the float64 form; 0 = lanes_per_ray (default 1) */
     int32_t order;              /* order in which the traversal takes the rays:
                                    1 = longest estimated path first (crossings estimated
                                    from a coarse site-density grid along each ray),

@@ -132,7 +132,7 @@ class VoronoiGrid:
         return vol, bb
 
     # -------------------------------------------------------------- launch
-    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, fp64_lanes_per_ray=4, order=0):
+    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, fp64_lanes_per_ray=1, order=0):
         """Launch shape of the traversal kernels; order: 1 = longest estimated
         path first, -1 = the caller's order, 0 = automatic (see vgrid.h)."""
         l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), int(fp64_lanes_per_ray), int(order))

@@ -82,7 +82,7 @@ struct vgrid {
     int sms = 1;
     int64_t M = 0;
     vgrid_opts opts{};
-    vgrid_launch launch{1, 128, 0, 4, 0};
+    vgrid_launch launch{1, 128, 0, 1, 0};
     GridDev hd{};
     GridDev *d_desc = nullptr;
     float4 *d_site = nullptr;
@@ -153,7 +153,7 @@ struct vgrid_batch {
     int sms = 1;
     int32_t G = 0;
     int64_t total = 0;
-    vgrid_launch launch{1, 128, 0, 4, 0};
+    vgrid_launch launch{1, 128, 0, 1, 0};
     GridDev *d_grids = nullptr;
     RaySetDev *d_sets = nullptr;
     RayPrep *d_start = nullptr;
@@ -675,7 +675,7 @@ int vgrid_set_density(vgrid_t *g, const float *rho, float kappa, vgrid_stream_t 
 int vgrid_set_launch(vgrid_t *g, const vgrid_launch *l) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (!l) {
-        g->launch = vgrid_launch{1, 128, 0, 4, 0};
+        g->launch = vgrid_launch{1, 128, 0, 1, 0};
         return VGRID_OK;
     }
     if (!valid_lpr(l->lanes_per_ray)) return fail(VGRID_ERR_ARG, "lanes_per_ray must be 1, 2, 4 or 8");

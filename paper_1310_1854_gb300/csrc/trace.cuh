@@ -229,36 +229,83 @@ __device__ __forceinline__ bool plane64x(const GridDev *gp, const float4 *crec, 
 // Exit of the cell whose records are blk[1..cnt] for the group: the
 // lexicographically smallest (s, id); returns the winner's record position
 // (1-based) or 0 if there is no candidate, and its s in bs.
+// The float64 form's pre-test: false only for a record whose plane
+// certainly faces away (n.k <= 0), so that the float64 test can skip it; the
+// results are the same bits. The stored n's high words are truncated to
+// float32 with integer operations only (21 significant bits, relative error
+// below 2^-20; components below 2^-126 become 0) and dotted with k in
+// float32. The error against the exact n.k is at most ||n~||_1 (2^-20 +
+// 4.1 2^-24) + 3 2^-126; the bound b below is more than three times that,
+// so d <= -b leaves n.k < 0 by a margin far above float64's rounding. Walls
+// and flagged records always pass.
+__device__ __forceinline__ float hi_to_float(int h) {
+    const int e = (h >> 20) & 0x7ff;
+    const int bits = (h & (int)0x80000000) | ((e - 896) << 23) | ((h & 0xfffff) << 3);
+    return e > 896 ? __int_as_float(bits) : 0.0f;
+}
+
+__device__ __forceinline__ bool may_face64(float4 xa, float4 xb, const float *kf) {
+    if (__float_as_int(xb.z) < 0 || __float_as_int(xb.w) != 0) return true;
+    const float nx = hi_to_float(__float_as_int(xa.y));
+    const float ny = hi_to_float(__float_as_int(xa.w));
+    const float nz = hi_to_float(__float_as_int(xb.y));
+    const float d = __fmaf_rn(nz, kf[2], __fmaf_rn(ny, kf[1], __fmul_rn(nx, kf[0])));
+    const float b = __fmaf_rn(__fadd_rn(__fadd_rn(fabsf(nx), fabsf(ny)), fabsf(nz)), 0x1p-18f, 0x1p-120f);
+    return d > -b;
+}
+
 // FRAC (the float64 form) reads the records from x64, the block's entries
 // of the table of exact differences (two float4 per entry), and blk only for
 // flagged records; otherwise it reads the float records of blk.
 template <int LPR, bool FRAC>
 __device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const float4 *blk, const float4 *x64, int cnt,
                                       double pmx, double pmy, double pmz, const double *r, const double *k,
-                                      unsigned gmask, int gl, double &bs) {
+                                      const float *kf, unsigned gmask, int gl, double &bs) {
     double bn = 0.0, bd = 1.0;
     int bp = 0, bw = 0;
-    for (int p = 1 + gl; p <= cnt; p += LPR) {
-        double n, d;
-        int w;
-        bool cand;
-        if (FRAC) {
-            float4 xa, xb;
-            ldg_pair(x64 + 2 * p, xa, xb);  // 32-byte entries
-            w = __float_as_int(xb.z);
-            cand = plane64x(gp, blk + p, xa, xb, pmx, pmy, pmz, r, k, n, d);
-        } else {
-            const float4 q = __ldg(blk + p);
-            w = rec_w(q);
-            cand = plane64(gp, q, pmx, pmy, pmz, r, k, n, d);
+    if (FRAC) {
+        // A warp issues a float64 instruction for all its lanes if any needs
+        // it, so a lane first marks which of its records may face ahead
+        // (float32 pre-test, up to 32 at a time) and then runs the float64
+        // test over those alone: the warp's float64 work follows the lane
+        // with the most candidates, not the one with the most records.
+        for (int base = 1 + gl; base <= cnt; base += 32 * LPR) {
+            unsigned m = 0;
+            for (int i = 0; i < 32; i++) {
+                const int p = base + i * LPR;
+                if (p > cnt) break;
+                float4 xa, xb;
+                ldg_pair(x64 + 2 * p, xa, xb);  // 32-byte entries
+                if (may_face64(xa, xb, kf)) m |= 1u << i;
+            }
+            while (m) {
+                const int p = base + (__ffs(m) - 1) * LPR;
+                m &= m - 1;
+                float4 xa, xb;
+                ldg_pair(x64 + 2 * p, xa, xb);
+                double n, d;
+                if (plane64x(gp, blk + p, xa, xb, pmx, pmy, pmz, r, k, n, d)) {
+                    const int w = __float_as_int(xb.z);
+                    if (better64<true>(h, n, d, w, bn, bd, bw, bp != 0)) {
+                        bn = n;
+                        bd = d;
+                        bp = p;
+                        bw = w;
+                    }
+                }
+            }
         }
-        if (cand) {
-            if (!FRAC) n = __ddiv_rn(n, d);
-            if (better64<FRAC>(h, n, d, w, bn, bd, bw, bp != 0)) {
+    }
+    // the float32 form's recheck: every record of blk, s divided out
+    for (int p = 1 + gl; !FRAC && p <= cnt; p += LPR) {
+        const float4 q = __ldg(blk + p);
+        double n, d;
+        if (plane64(gp, q, pmx, pmy, pmz, r, k, n, d)) {
+            n = __ddiv_rn(n, d);
+            if (better64<false>(h, n, d, rec_w(q), bn, bd, bw, bp != 0)) {
                 bn = n;
-                if (FRAC) bd = d;
                 bp = p;
-                bw = w;
+                bw = rec_w(q);
             }
         }
     }
@@ -545,8 +592,10 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     Hot h{a.g1.cells, a.g1.rel, a.g1.site};
     float kappa = a.g1.kappa;
     int max_steps = (int)min(a.g1.max_steps, (int64_t)0x7fffffff);
-    // float64 form: current point and direction
+    // float64 form: current point and direction (and the direction in
+    // float32 for the pre-test of the planes)
     double r64[3] = {0, 0, 0}, k64[3] = {0, 0, 0};
+    float kf64[3] = {0.f, 0.f, 0.f};
     // float32 form: origin and direction as float pairs, ray parameter t, wall exit
     float R0h[3], R0l[3], Kh[3], Kl[3];
     float th = 0.f, tl = 0.f, tmh = 0.f, tml = 0.f, er = 0.f, ewall = 0.f;
@@ -687,6 +736,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     for (int c = 0; c < 3; c++) {
                         r64[c] = __ldg(o + c);
                         k64[c] = __ldg(d + c);
+                        kf64[c] = __double2float_rn(k64[c]);
                     }
                 }
             } else {
@@ -766,7 +816,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
         float4 qn = make_float4(0.f, 0.f, 0.f, 0.f);  // float64 form: the winner's record
         if (FP64) {
             const int win = exit64<LPR, true>(h, gp, blk, a.g1.rec64 + 2 * (int64_t)B, cnt, (double)pmx, (double)pmy,
-                                              (double)pmz, r64, k64, gmask, gl, s64);
+                                              (double)pmz, r64, k64, kf64, gmask, gl, s64);
             if (win > 0) {
                 qn = __ldg(blk + win);
                 found = true;
@@ -846,7 +896,7 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 const float4 *ablk = h.cells + rec_w(hdr1);
                 const int acnt = hdr_count(__ldg(ablk));
                 const int win = exit64<LPR, false>(h, gp, ablk, nullptr, acnt, (double)pmx, (double)pmy, (double)pmz,
-                                                   rp, kd, gmask, gl, s64);
+                                                   rp, kd, nullptr, gmask, gl, s64);
                 if (win > 0) {
                     const float4 qa = __ldg(ablk + win);
                     found = true;

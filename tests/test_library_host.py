@@ -163,7 +163,7 @@ def test_launch_shape_validation(libvgrid):
     """vgrid_set_launch checks every field (host-only grid: no GPU needed)."""
     from paper_1310_1854_gb300 import _lib
     vg = _grid(gen.cubic_lattice(2), gen.CUBE_BOX)
-    assert vg.get_launch() == {"lanes_per_ray": 1, "block": 128, "blocks_per_sm": 0, "fp64_lanes_per_ray": 4,
+    assert vg.get_launch() == {"lanes_per_ray": 1, "block": 128, "blocks_per_sm": 0, "fp64_lanes_per_ray": 1,
                                "order": 0}
     vg.set_launch(lanes_per_ray=2, block=256, blocks_per_sm=3, fp64_lanes_per_ray=8, order=1)
     assert vg.get_launch() == {"lanes_per_ray": 2, "block": 256, "blocks_per_sm": 3, "fp64_lanes_per_ray": 8,
