@@ -118,6 +118,40 @@ def test_cubic_lattice_parity():
     run_case(g, rays, ref)
 
 
+def test_near_perpendicular_planes_parity():
+    """Rays along the axes of a cubic lattice, exactly and tilted by 1e-9 to
+    1e-3: many planes are perpendicular to the ray or nearly so (n.k = 0 or
+    tiny), where the float64 form's float32 pre-test must never drop a plane
+    that faces ahead. Both forms against the oracle."""
+    S = gen.cubic_lattice(8)
+    rng = gen.rng_for(109)
+    g = gen.Grid(S, gen.CUBE_BOX.copy(), rng.uniform(0.5, 1.5, len(S)).astype(np.float32))
+    n = 1500
+    o = rng.uniform(-0.95, 0.95, (n, 3))
+    axis = rng.integers(0, 3, n)
+    d = np.zeros((n, 3))
+    d[np.arange(n), axis] = rng.choice([-1.0, 1.0], n)
+    tilt = 10.0 ** rng.uniform(-9, -3, (n, 3)) * rng.choice([-1.0, 0.0, 1.0], (n, 3))
+    tilt[: n // 4] = 0.0  # exactly along an axis
+    d = d + tilt
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rays = gen.Rays(o, d)
+    ref = oracle_full(g, rays)
+    vg = make(g)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    ok = np.nonzero(ref.near_tie == 0)[0]
+    assert ok.size >= n // 3
+    O, D = dev(o), dev(d)
+    for lpr in (1, 4):
+        vg.set_launch(fp64_lanes_per_ray=lpr)
+        r64 = vg.trace(O, D, precision="fp64", segments=True)
+        check_segments(ref, ok, r64.seg_off, r64.seg_cell, r64.seg_len, diag, LEN64_REL)
+        np.testing.assert_allclose(r64.tau.cpu().numpy()[ok], ref.tau[ok], rtol=1e-12, atol=1e-300)
+    r32 = vg.trace(O, D, precision="fp32", segments=True)
+    check_segments(ref, ok, r32.seg_off, r32.seg_cell, r32.seg_len, diag, None)
+    vg.set_launch()
+
+
 def test_tiny_coordinates_parity():
     """Sites with tiny nonzero coordinates next to ordinary ones: their float
     differences and sums round in float64, so the float64 form takes those
