@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                                                     const int *bsites, double box0, double box1, double box2,
                                                     double box3, double box4, double box5, double eps, int *out_cnt,
                                                     int *out_nbr, double *out_vol, double *out_bbox, int *out_fail,
-                                                    unsigned long long *next) {
+                                                    unsigned long long *next, const float4 *Sf, int prefilter) {
     DPoly P;
     Scratch W;
     const double box[6] = {box0, box1, box2, box3, box4, box5};
@@ -270,6 +270,20 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
         const double px = S[3 * m], py = S[3 * m + 1], pz = S[3 * m + 2];
         poly_box(P, box);
         double rmax = sqrt(poly_rmax2(P, px, py, pz));
+        // Float32 prefilter of the security radius. A warp issues a float64
+        // instruction for all its lanes, so the float64 distance of every
+        // candidate site costs the whole warp; most candidates lie far out
+        // of reach. Site coordinates are float32 values, so their float
+        // copies are exact and the float32 squared distance is within 2^-21
+        // (relative) of the exact one; a site is dropped only when it
+        // exceeds reach^2 (1 + 2^-17), rounded up, where the float64 test
+        // drops it as well. Zero or underflowed distances never pass it.
+        const float4 pf = Sf[m];
+        auto reach2f = [&](double r) {
+            const double reach = 2.0 * r + 4.0 * eps;
+            return __double2float_ru(reach * reach * (1.0 + 0x1p-17));
+        };
+        float R2f = reach2f(rmax);
         const int bi = bucket_coord(px, bg.lo[0], bg.inv[0], bg.dim[0]);
         const int bj = bucket_coord(py, bg.lo[1], bg.inv[1], bg.dim[1]);
         const int bk = bucket_coord(pz, bg.lo[2], bg.inv[2], bg.dim[2]);
@@ -290,6 +304,10 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                         for (int64_t q = boff[b]; q < boff[b + 1]; q++) {
                             const int jj = bsites[q];
                             if (jj == (int)m) continue;
+                            const float4 qf = Sf[jj];
+                            const float fx = __fsub_rn(qf.x, pf.x), fy = __fsub_rn(qf.y, pf.y),
+                                        fz = __fsub_rn(qf.z, pf.z);
+                            if (prefilter && __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx))) > R2f) continue;
                             const double qx = S[3 * (int64_t)jj], qy = S[3 * (int64_t)jj + 1], qz = S[3 * (int64_t)jj + 2];
                             const double dx = qx - px, dy = qy - py, dz = qz - pz;
                             const double dist = sqrt(dx * dx + dy * dy + dz * dz);
@@ -298,7 +316,10 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                             const double d = nx * 0.5 * (qx + px) + ny * 0.5 * (qy + py) + nz * 0.5 * (qz + pz);
                             const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps);
                             if (rc < 0) { fail = 1; break; }
-                            if (rc > 0) rmax = sqrt(poly_rmax2(P, px, py, pz));
+                            if (rc > 0) {
+                                rmax = sqrt(poly_rmax2(P, px, py, pz));
+                                R2f = reach2f(rmax);
+                            }
                         }
                     }
                 }
@@ -368,11 +389,13 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
         K *= bg.dim[c];
     }
     double *dS = nullptr;
+    float4 *dSf = nullptr;
+    int prefilter = 1;
     int *bidx = nullptr, *bsites = nullptr, *cnt = nullptr, *nbr = nullptr, *fail = nullptr;
     int64_t *boff = nullptr, *cursor = nullptr, *tmp = nullptr;
     double *vol = nullptr, *bbox = nullptr;
     auto cleanup = [&]() {
-        void *ptrs[] = {dS, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
+        void *ptrs[] = {dS, dSf, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     };
@@ -394,6 +417,19 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     if ((e = cudaMalloc(&vol, sizeof(double) * M)) != cudaSuccess) return bad(e, "alloc");
     if ((e = cudaMalloc(&bbox, sizeof(double) * 6 * M)) != cudaSuccess) return bad(e, "alloc");
     if ((e = cudaMemcpy(dS, S, sizeof(double) * 3 * M, cudaMemcpyHostToDevice)) != cudaSuccess) return bad(e, "upload");
+    {
+        // float copies of the sites; the prefilter's bound needs them exact
+        // (sites are float32 values; it is off otherwise)
+        std::vector<float4> sf((size_t)M);
+        for (int64_t m = 0; m < M; m++) {
+            sf[m] = make_float4((float)S[3 * m], (float)S[3 * m + 1], (float)S[3 * m + 2], 0.f);
+            if ((double)sf[m].x != S[3 * m] || (double)sf[m].y != S[3 * m + 1] || (double)sf[m].z != S[3 * m + 2])
+                prefilter = 0;
+        }
+        if ((e = cudaMalloc(&dSf, sizeof(float4) * M)) != cudaSuccess) return bad(e, "alloc");
+        if ((e = cudaMemcpy(dSf, sf.data(), sizeof(float4) * M, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bad(e, "upload");
+    }
     if ((e = cudaMemset(boff, 0, sizeof(int64_t) * (K + 1))) != cudaSuccess) return bad(e, "memset");
     const int blocks = (int)std::min<int64_t>((M + 255) / 256, 65535);
     bucket_count_kernel<<<blocks, 256>>>(dS, M, bg, bidx, boff);
@@ -410,7 +446,7 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     const int cblocks = (int)std::max<int64_t>(1, std::min<int64_t>((M + 127) / 128, (int64_t)per_sm * sms));
     if ((e = cudaMemset(cursor, 0, sizeof(unsigned long long))) != cudaSuccess) return bad(e, "memset");
     cells_kernel<<<cblocks, 128>>>(dS, M, bg, boff, bsites, box[0], box[1], box[2], box[3], box[4], box[5], eps, cnt,
-                                   nbr, vol, bbox, fail, reinterpret_cast<unsigned long long *>(cursor));
+                                   nbr, vol, bbox, fail, reinterpret_cast<unsigned long long *>(cursor), dSf, prefilter);
     count_launches(4);  // bucket count, fill, sort, cells (the scan counts its own)
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cells kernel");
     std::vector<int> hcnt(M), hfail(M), hnbr((size_t)kCap * M);
