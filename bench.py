@@ -511,11 +511,34 @@ def run_extra(args):
         passes = 1 if args.workload == "clumpy1e6" else 2
         segs = st["crossings"] * passes
         kern = tr_ms / max(launches, 1)
+        via_segments = None
+        if args.workload == "grad1e6":
+            # the same step through the segment lists: one traversal that
+            # keeps them, then the adjoint from the lists (no second traversal)
+            cap = st["crossings"]
+
+            def fn_seg():
+                r = vg.trace(O, D, precision="fp32", segments=True, seg_capacity=cap)
+                e = torch.exp(-r.tau)
+                dL = -2.0 * (e - target) * e
+                grad.zero_()
+                vg.segments_grad(r, dL, out=grad)
+
+            g_two = grad.clone()
+            fn_seg()
+            torch.cuda.synchronize()
+            rel = float(((grad - g_two).abs().max() / g_two.abs().max()).item())
+            for _ in range(args.warmup):
+                fn_seg()
+            ms_seg = _events_ms(fn_seg, args.steps, flush)
+            via_segments = {"value": segs * args.steps / (ms_seg / 1e3), "ms_per_step": ms_seg / args.steps,
+                            "max_rel_diff_vs_two_traversals": rel}
         line.update({"value": segs * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
                      "config": {"workload": desc, "sites": info["M"], "rays": N, "mean_degree": round(deg, 3),
                                 "traversals_per_step": passes, "host_build_s": round(build_s, 2),
                                 "device_bytes": info["device_bytes"], "l2": "flushed between timed steps"},
                      "stats_per_traversal": st, "rays_per_s": N * passes * args.steps / (ms / 1e3),
+                     "via_segment_lists": via_segments,
                      "gpu_launches": n_kernels,
                      "roofline": {"bound": "hbm", "achieved": st["crossings"] * bpc / (kern / 1e3) / 1e9, "peak": peak,
                                   "unit": "GB/s", "frac": st["crossings"] * bpc / (kern / 1e3) / 1e9 / peak,

@@ -290,6 +290,22 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
                      float *dL_drho, vgrid_stream_t stream);
 
 /*
+ * The same adjoint from the segment lists that vgrid_trace returned
+ * (VGRID_SEGMENTS with VGRID_FP32_RECHECK), without tracing again: for every
+ * ray r and every k in [seg_off[r], seg_off[r+1]),
+ * dL_drho[seg_cell[k]] += dL_dtau[r] * kappa * seg_len[k], kappa the grid's.
+ * Each term is the product vgrid_trace_grad adds; the order of the float32
+ * atomic sums differs.
+ *   seg_off  device int64[N+1]; seg_cell device int32 and seg_len device
+ *            float32, seg_off[N] entries each (caller ids, as returned).
+ *   dL_dtau  device float32[N]; dL_drho device float32[M], accumulated into.
+ * One pass over the lists (about 8 bytes read and one atomic per segment).
+ * Errors: VGRID_ERR_ARG.
+ */
+int vgrid_segments_grad(vgrid_t *g, const int64_t *seg_off, const int32_t *seg_cell, const float *seg_len, int64_t N,
+                        const float *dL_dtau, float *dL_drho, vgrid_stream_t stream);
+
+/*
  * Interaction sampling along the path: the Monte Carlo step that consumes
  * the traversal in the paper's radiative-transfer code (Sect. 3.1, 3.4:
  * photon packages are shot through the grid and their absorption is booked

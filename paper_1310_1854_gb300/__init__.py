@@ -262,6 +262,22 @@ class VoronoiGrid:
                                     _stream(stream)))
         return cell, s, ab
 
+    def segments_grad(self, res: TraceResult, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """dL/drho (float32[M]) from the float32 segment lists of a trace
+        (``trace(..., segments=True)``) without tracing again; accumulates
+        into ``out``."""
+        if res.seg_off is None or res.seg_len.dtype != torch.float32:
+            raise TypeError("needs the float32 segment lists of trace(..., precision='fp32', segments=True)")
+        N = res.seg_off.shape[0] - 1
+        g = dL_dtau.detach().to(torch.float32).contiguous()
+        if g.numel() != N:
+            raise ValueError("dL_dtau needs one value per ray of the trace")
+        if out is None:
+            out = torch.zeros(self.M, dtype=torch.float32, device=self.device)
+        check(load().vgrid_segments_grad(self._h, _ptr(res.seg_off), _ptr(res.seg_cell), _ptr(res.seg_len), N, _ptr(g),
+                                         _ptr(out), _stream(stream)))
+        return out
+
     def trace_grad(self, origin, direction, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         """dL/drho (float32[M]) for dL/dtau per ray; accumulates into ``out``."""
         O = _rays(origin, "origin", self.device)
@@ -319,24 +335,33 @@ class Batch:
 
 
 class _OpticalDepth(torch.autograd.Function):
-    """tau(rho) for fixed rays; backward is the library's adjoint traversal."""
+    """tau(rho) for fixed rays. Backward is the adjoint from the segment lists
+    kept by forward (keep_segments), else the library's adjoint traversal."""
 
     @staticmethod
-    def forward(ctx, rho, grid, origin, direction, kappa):
+    def forward(ctx, rho, grid, origin, direction, kappa, keep_segments):
         grid.set_density(rho.detach().to(torch.float32).contiguous(), kappa)
-        res = grid.trace(origin, direction, precision="fp32")
+        res = grid.trace(origin, direction, precision="fp32", segments=keep_segments)
         ctx.grid = grid
+        ctx.res = res if keep_segments else None
         ctx.save_for_backward(origin, direction)
         return res.tau
 
     @staticmethod
     def backward(ctx, g):
-        origin, direction = ctx.saved_tensors
-        d = ctx.grid.trace_grad(origin, direction, g.contiguous())
-        return d, None, None, None, None
+        if ctx.res is not None:
+            d = ctx.grid.segments_grad(ctx.res, g.contiguous())
+        else:
+            origin, direction = ctx.saved_tensors
+            d = ctx.grid.trace_grad(origin, direction, g.contiguous())
+        return d, None, None, None, None, None
 
 
 def optical_depth(grid: VoronoiGrid, rho: torch.Tensor, origin: torch.Tensor, direction: torch.Tensor,
-                  kappa: float = 1.0) -> torch.Tensor:
-    """Differentiable tau per ray with respect to the per-cell densities rho."""
-    return _OpticalDepth.apply(rho, grid, origin, direction, kappa)
+                  kappa: float = 1.0, keep_segments: bool = True) -> torch.Tensor:
+    """Differentiable tau per ray with respect to the per-cell densities rho.
+
+    With keep_segments (default) forward keeps the segment lists (8 bytes per
+    segment on the device until backward) and backward reads them instead of
+    tracing the rays again; without, backward traces again."""
+    return _OpticalDepth.apply(rho, grid, origin, direction, kappa, bool(keep_segments))

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("vgrid_trace_host", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64,
                                    c_void_p, c_void_p]),
     ("vgrid_trace_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    ("vgrid_segments_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     ("vgrid_set_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_get_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_batch_create", c_int32, [ctypes.POINTER(Rayset), c_int32, ctypes.POINTER(Launch),

@@ -1197,6 +1197,19 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
     return VGRID_OK;
 }
 
+int vgrid_segments_grad(vgrid_t *g, const int64_t *seg_off, const int32_t *seg_cell, const float *seg_len, int64_t N,
+                        const float *dL_dtau, float *dL_drho, vgrid_stream_t stream) {
+    if (!g) return fail(VGRID_ERR_ARG, "null grid");
+    if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
+    if (N < 0 || (N > 0 && (!seg_off || !seg_cell || !seg_len || !dL_dtau || !dL_drho)))
+        return fail(VGRID_ERR_ARG, "bad arguments");
+    if (N == 0) return VGRID_OK;
+    DeviceGuard dg(g->device);
+    VG_CUDA(vg::launch_segments_grad(seg_off, seg_cell, seg_len, N, dL_dtau, g->hd.kappa, dL_drho, g->sms,
+                                     (cudaStream_t)stream));
+    return VGRID_OK;
+}
+
 int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_t N, const float *dL_dtau,
                      float *dL_drho, vgrid_stream_t stream) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");

@@ -515,6 +515,28 @@ cudaError_t launch_build_rec64(const float4 *site, const float4 *rel, const floa
     return cudaGetLastError();
 }
 
+// 8 lanes per ray striding over its segments (coalesced reads of the
+// lists); the term is (dL/dtau_r kappa) l, as the traversal's adjoint forms it
+__global__ void segments_grad_kernel(const int64_t *off, const int32_t *cell, const float *len, int64_t N,
+                                     const float *g, float kappa, float *out) {
+    const int i = threadIdx.x & 7;
+    const int64_t groups = (int64_t)gridDim.x * blockDim.x / 8;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8; r < N; r += groups) {
+        const float gk = __ldg(g + r) * kappa;
+        const int64_t a = __ldg(off + r), b = __ldg(off + r + 1);
+        for (int64_t k = a + i; k < b; k += 8) atomicAdd(out + __ldg(cell + k), gk * __ldg(len + k));
+    }
+}
+
+cudaError_t launch_segments_grad(const int64_t *off, const int32_t *cell, const float *len, int64_t N, const float *g,
+                                 float kappa, float *out, int sms, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((N * 8 + 255) / 256, (int64_t)sms * 8));
+    segments_grad_kernel<<<blocks, 256, 0, s>>>(off, cell, len, N, g, kappa, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 int64_t scan_tmp_elems(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 cudaError_t launch_exclusive_scan(int64_t *data, int64_t n, int64_t *tmp, cudaStream_t s) {

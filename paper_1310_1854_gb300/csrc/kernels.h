@@ -110,6 +110,10 @@ cudaError_t launch_build_rec64(const float4 *site, const float4 *rel, const floa
 cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchunks, const int2 *meta,
                                     const void *slots, bool fp64, int64_t *coff, int64_t *scan_tmp, int32_t *inv,
                                     int32_t *cell, void *len, int sms, cudaStream_t s);
+// adjoint from segment lists: out[cell[k]] += g[r] * kappa * len[k] for the
+// segments k of every ray r (CSR offsets off[0..N])
+cudaError_t launch_segments_grad(const int64_t *off, const int32_t *cell, const float *len, int64_t N, const float *g,
+                                 float kappa, float *out, int sms, cudaStream_t s);
 // exclusive scan of counts[0..n-1] (int64) into off[0..n]; tmp holds
 // scan_tmp_elems(n) int64 values
 int64_t scan_tmp_elems(int64_t n);

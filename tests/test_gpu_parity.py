@@ -320,6 +320,15 @@ def test_gradient_matches_oracle():
     assert ok or ref.near_tie.sum() < 5
     assert np.all(np.abs(got - want) <= GRAD32_REL * wabs + 1e-30)
     assert np.all(got[wabs == 0] == 0)
+    # the same adjoint from the segment lists of a float32 trace (no second
+    # traversal): same terms, other summation order
+    seg = vg.trace(O, D, precision="fp32", segments=True)
+    got2 = vg.segments_grad(seg, dev(dL.astype(np.float32))).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got2 - want) <= GRAD32_REL * wabs + 1e-30)
+    assert np.all(got2[wabs == 0] == 0)
+    assert np.all(np.abs(got2 - got) <= 2 * GRAD32_REL * wabs + 1e-30)
+    acc = vg.segments_grad(seg, dev(dL.astype(np.float32)), out=torch.from_numpy(got2.astype(np.float32)).cuda())
+    np.testing.assert_allclose(acc.cpu().numpy(), 2 * got2, rtol=1e-5, atol=1e-30 + 1e-6 * np.abs(got2).max())
     # autograd wrapper gives the same gradient
     from paper_1310_1854_gb300 import optical_depth
     rho = dev(g.rho).requires_grad_(True)
@@ -331,6 +340,13 @@ def test_gradient_matches_oracle():
     # torch evaluates the loss in float32 from float32 tau; dL/dtau carries
     # that rounding (about 1e-7 relative to exp(-tau))
     assert np.all(np.abs(gg - want) <= 1e-3 * wabs + 1e-30)
+    # backward by a second traversal instead of the kept segment lists
+    rho2 = dev(g.rho).requires_grad_(True)
+    tau2 = optical_depth(vg, rho2, O, D, float(g.kappa), keep_segments=False)
+    np.testing.assert_array_equal(tau2.detach().cpu().numpy(), tau.detach().cpu().numpy())
+    ((torch.exp(-tau2) - t) ** 2).sum().backward()
+    gg2 = rho2.grad.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(gg2 - want) <= 1e-3 * wabs + 1e-30)
 
 
 def test_batched_matches_single():

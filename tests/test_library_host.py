@@ -156,6 +156,7 @@ def test_host_only_grid_refuses_device_calls(libvgrid):
     assert b"host_only" in lib.vgrid_last_error()
     assert lib.vgrid_locate(vg._h, dummy, 1, 0, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_trace_grad(vg._h, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
+    assert lib.vgrid_segments_grad(vg._h, dummy, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_enable_timing(vg._h, 1) == _lib.ERR_ARG
 
 
