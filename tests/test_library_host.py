@@ -160,6 +160,25 @@ def test_host_only_grid_refuses_device_calls(libvgrid):
     assert lib.vgrid_enable_timing(vg._h, 1) == _lib.ERR_ARG
 
 
+def test_segments_grad_argument_checks(libvgrid):
+    """VoronoiGrid.segments_grad wants the float32 segment lists of a trace
+    and one dL/dtau per ray; the C call refuses a host-only grid."""
+    import torch
+    from paper_1310_1854_gb300 import TraceResult, _lib
+    vg = _grid(gen.cubic_lattice(2), gen.CUBE_BOX)
+    off = torch.tensor([0, 2, 3], dtype=torch.int64)
+    cells = torch.tensor([0, 1, 1], dtype=torch.int32)
+    tau = torch.zeros(2)
+    with pytest.raises(TypeError):
+        vg.segments_grad(TraceResult(tau), torch.ones(2))
+    with pytest.raises(TypeError):
+        vg.segments_grad(TraceResult(tau, off, cells, torch.ones(3, dtype=torch.float64)), torch.ones(2))
+    with pytest.raises(ValueError):
+        vg.segments_grad(TraceResult(tau, off, cells, torch.ones(3)), torch.ones(3))
+    with pytest.raises(_lib.VGridError):
+        vg.segments_grad(TraceResult(tau, off, cells, torch.ones(3)), torch.ones(2), out=torch.zeros(8))
+
+
 def test_launch_shape_validation(libvgrid):
     """vgrid_set_launch checks every field (host-only grid: no GPU needed)."""
     from paper_1310_1854_gb300 import _lib
