@@ -128,9 +128,37 @@ __device__ double poly_rmax2(const DPoly &P, double px, double py, double pz) {
     return r2;
 }
 
+// A double truncated to float32 with integer operations only (its high word:
+// 21 significant bits, relative error below 2^-20; |x| < 2^-126 gives 0).
+__device__ __forceinline__ float trunc_float(double x) {
+    const int h = __double2hiint(x);
+    const int e = (h >> 20) & 0x7ff;
+    const int bits = (h & (int)0x80000000) | ((e - 896) << 23) | ((h & 0xfffff) << 3);
+    return e > 896 ? __int_as_float(bits) : 0.0f;
+}
+
 // Cut P by {x : n.x <= d}. 1: changed, 0: untouched, -1: capacity exceeded
 // or topology broken (the caller rebuilds the cell on the host).
-__device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, double d, int id, double eps) {
+// B bounds the error of the float32 screen below: with |n| = 1, every vertex
+// and the midpoint inside the box (|coordinate| <= X), truncation and
+// float32 rounding leave n.v - d within about 0.76 2^-17 X of its float32
+// value, and B = 2^-16 X; the screen returns 0 only where the float64 test
+// below would (no vertex above the plane by more than eps << B).
+__device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, double d, int id, double eps,
+                        float B) {
+    {
+        // most planes that pass the security radius still miss the cell:
+        // tell them apart without the float64 pipe, which a warp pays for
+        // all its lanes whenever one of them uses it
+        const float fx = trunc_float(nx), fy = trunc_float(ny), fz = trunc_float(nz), fd = trunc_float(d);
+        bool maybe = false;
+        for (int i = 0; i < P.nv; i++) {
+            const float v = __fmaf_rn(fz, trunc_float(P.z[i]), __fmaf_rn(fy, trunc_float(P.y[i]),
+                                                                         __fmul_rn(fx, trunc_float(P.x[i]))));
+            maybe |= __fsub_rn(v, fd) > -B;
+        }
+        if (!maybe) return 0;
+    }
     bool any_out = false;
     for (int i = 0; i < P.nv; i++) {
         W.fv[i] = nx * P.x[i] + ny * P.y[i] + nz * P.z[i] - d;
@@ -266,6 +294,9 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
     DPoly P;
     Scratch W;
     const double box[6] = {box0, box1, box2, box3, box4, box5};
+    double X = 0.0;
+    for (int c = 0; c < 6; c++) X = fmax(X, fabs(box[c]));
+    const float Bscreen = __fmaf_rn((float)X, 0x1p-16f, 0x1p-120f);  // see poly_cut
     for (int64_t m = (int64_t)atomicAdd(next, 1ull); m < M; m = (int64_t)atomicAdd(next, 1ull)) {
         const double px = S[3 * m], py = S[3 * m + 1], pz = S[3 * m + 2];
         poly_box(P, box);
@@ -314,7 +345,7 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                             if (dist > 2.0 * rmax + 4.0 * eps) continue;
                             const double nx = dx / dist, ny = dy / dist, nz = dz / dist;
                             const double d = nx * 0.5 * (qx + px) + ny * 0.5 * (qy + py) + nz * 0.5 * (qz + pz);
-                            const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps);
+                            const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps, Bscreen);
                             if (rc < 0) { fail = 1; break; }
                             if (rc > 0) {
                                 rmax = sqrt(poly_rmax2(P, px, py, pz));
