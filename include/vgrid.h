@@ -280,8 +280,9 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
                      int32_t *ray_status, int64_t chunk, vgrid_stats *stats, vgrid_stream_t stream);
 
 /*
- * Adjoint of tau = sum kappa rho l with respect to rho: for every ray r and
- * every segment (c, l) of its path, dL_drho[c] += dL_dtau[r] * kappa * l.
+ * Adjoint of tau = sum kappa rho l (the optical depth along the path of
+ * Sect. 2.2, linear in the cell densities) with respect to rho: for every ray
+ * r and every segment (c, l) of its path, dL_drho[c] += dL_dtau[r] * kappa * l.
  * The path is the one vgrid_trace finds with VGRID_FP32_RECHECK.
  *   dL_dtau  device float32[N]; dL_drho device float32[M], accumulated into
  *   (caller ids; zero it first for a plain gradient).
@@ -290,8 +291,9 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
                      float *dL_drho, vgrid_stream_t stream);
 
 /*
- * The same adjoint from the segment lists that vgrid_trace returned
- * (VGRID_SEGMENTS with VGRID_FP32_RECHECK), without tracing again: for every
+ * The same adjoint (tau = sum kappa rho l over the path of Sect. 2.2) from
+ * the segment lists that vgrid_trace returned (VGRID_SEGMENTS with
+ * VGRID_FP32_RECHECK), without tracing again: for every
  * ray r and every k in [seg_off[r], seg_off[r+1]),
  * dL_drho[seg_cell[k]] += dL_dtau[r] * kappa * seg_len[k], kappa the grid's.
  * Each term is the product vgrid_trace_grad adds; the order of the float32
@@ -334,7 +336,9 @@ int vgrid_set_launch(vgrid_t *g, const vgrid_launch *launch);
 int vgrid_get_launch(const vgrid_t *g, vgrid_launch *launch);
 
 /*
- * Many grids in one launch (uneven sizes and ray counts). Each set names a
+ * Many grids in one launch (uneven sizes and ray counts): the traversal of
+ * Sect. 2.2 for every set, as vgrid_trace computes it in its float32 form,
+ * with one work queue over all sets. Each set names a
  * grid and its rays; tau (device float32[n]) and status (device int32[n],
  * nullable) receive the results of VGRID_FP32_RECHECK tracing.
  */
