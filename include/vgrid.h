@@ -97,6 +97,14 @@ typedef struct {
     int32_t gpu_build;         /* 1: construct the cells on the current GPU (one
                                   thread per cell; cells that exceed its fixed
                                   capacities are rebuilt on the host) */
+    int32_t zero_run_max;      /* zero-length steps in a row that a path may take
+                                  (a ray through an edge or vertex of several
+                                  cells); one more moves the point on by epsilon
+                                  and locates its cell again, as a decision without
+                                  any exit does (Sect. 2.2). Default 4; 0 nudges
+                                  after every zero-length step. Epsilon is
+                                  1e-12 |Dmax - Dmin| in the float64 form and
+                                  1e-6 |Dmax - Dmin| in the float32 form. */
 } vgrid_opts;
 
 typedef struct {

@@ -36,6 +36,7 @@ _lib = None
 
 WALL_IDS = (-1, -2, -3, -4, -5, -6)   # x=xmin, x=xmax, y=ymin, y=ymax, z=zmin, z=zmax
 TIE_REL = 1e-9                        # near-tie threshold on the decision margin
+ZERO_RUN_MAX = 4                      # zero-length steps in a row before the epsilon nudge (R6)
 STATUS = {0: "ok", 1: "outside", 2: "step_limit", 3: "capacity"}
 
 
@@ -65,7 +66,7 @@ def _load():
         lib.oracle_locate.argtypes = [P, i64, P, P, i64, P, ctypes.c_int]
         lib.oracle_locate.restype = None
         lib.oracle_trace.argtypes = [P, i64, P, P, P, P, ctypes.c_double, P, P, i64, i64, P, P, P, P, P, P,
-                                     P, P, P, i64, ctypes.c_double, ctypes.c_int]
+                                     P, P, P, i64, ctypes.c_int, ctypes.c_double, ctypes.c_int]
         lib.oracle_trace.restype = None
         _lib = lib
         return lib
@@ -164,9 +165,11 @@ class Trace:
 
 
 def trace(sites, box, rho, origin, direction, off=None, idx=None, kappa=1.0, cap=1024, max_steps=1_000_000,
-          tie_rel=TIE_REL, threads=None) -> Trace:
+          tie_rel=TIE_REL, zero_run_max=ZERO_RUN_MAX, threads=None) -> Trace:
     """Trace rays with the paper's loop. With off/idx None every site and all
-    walls are candidates (the plain definition of the exit)."""
+    walls are candidates (the plain definition of the exit). More than
+    ``zero_run_max`` zero-length steps in a row nudge the point by
+    epsilon = 1e-12 |Dmax - Dmin| and locate it again (Sect. 2.2)."""
     lib = _load()
     S = _f64c(sites)
     box = _f64c(box)
@@ -186,7 +189,7 @@ def trace(sites, box, rho, origin, direction, off=None, idx=None, kappa=1.0, cap
     lib.oracle_trace(_p(S), S.shape[0], _p(box), _p(off), _p(idx), _p(rho), float(kappa), _p(O), _p(D), N, cap,
                      _p(seg_cell), _p(seg_len), _p(out["nseg"]), _p(out["tau"]), _p(out["length"]),
                      _p(out["min_margin"]), _p(out["near_tie"]), _p(out["nfallback"]), _p(out["status"]),
-                     int(max_steps), float(tie_rel), _threads(threads))
+                     int(max_steps), int(zero_run_max), float(tie_rel), _threads(threads))
     return Trace(out["nseg"], seg_cell, seg_len, out["tau"], out["length"], out["min_margin"], out["near_tie"],
                  out["nfallback"], out["status"])
 
@@ -275,14 +278,3 @@ def exp_loss(tau, target):
     e = np.exp(-np.asarray(tau, np.float64))
     t = np.asarray(target, np.float64)
     return float(np.sum((e - t) ** 2)), -2.0 * (e - t) * e
-
-
-def in_domain_length(box, origin, direction) -> np.ndarray:
-    """Distance from each origin to the box boundary along its direction
-    (the smallest positive wall parameter of Eq. 5 over the three axes)."""
-    box = np.asarray(box, np.float64)
-    O = np.asarray(origin, np.float64).reshape(-1, 3)
-    D = np.asarray(direction, np.float64).reshape(-1, 3)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        tmax = np.where(D > 0, (box[3:] - O) / D, np.where(D < 0, (box[:3] - O) / D, np.inf))
-    return tmax.min(axis=1)

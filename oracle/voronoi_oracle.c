@@ -16,6 +16,11 @@
  *                  loop stops once a candidate is farther than twice the
  *                  largest vertex radius (its bisector plane then lies
  *                  entirely outside the cell), or never stops (brute = 1).
+ *                  The sites within a shell of radii are found through a
+ *                  uniform bucket grid (every site of every bucket that meets
+ *                  the shell's bounding cube is tested against the radii), so
+ *                  the candidate set and its order are those of a loop over
+ *                  all sites.
  *                  Gives the neighbour list (faces of positive area, walls as
  *                  -1..-6), the cell volume and bounding box (Sect. 2.3).
  *   oracle_locate  C(r): nearest site by brute force over all sites,
@@ -35,8 +40,9 @@
  *   R4 ties are broken by the lexicographic order of (s, id); walls carry
  *      negative ids and so win exact ties;
  *   R5 zero-length steps emit no segment;
- *   R6 epsilon = 1e-12 * |Dmax - Dmin|; more than Z = 4 consecutive
- *      zero-length steps also trigger the nudge;
+ *   R6 epsilon = 1e-12 * |Dmax - Dmin|; more than Z consecutive
+ *      zero-length steps also trigger the nudge (Z = 4 by default; a test
+ *      may lower it, Z = 0 nudging after every zero-length step);
  *   R9 the current point is updated literally, r <- r + s k.
  * Floating-point contraction is disabled at compile time so that results do
  * not depend on the host's FMA support.
@@ -50,7 +56,6 @@
 
 #define OR_MAXF 256
 #define OR_MAXV 96
-#define OR_ZMAX 4
 
 /* ------------------------------------------------------------------------ */
 /* threads: a plain parallel-for over independent items                      */
@@ -304,10 +309,72 @@ static double poly_rmax(const or_poly *P, const double *c)
 /* cells                                                                    */
 /* ------------------------------------------------------------------------ */
 
+/* Uniform bucket grid over the box: bucket b holds the sites
+ * ids[start[b] .. start[b+1]-1]; a site's bucket along an axis is
+ * floor((x - lo) / h) clamped to [0, n - 1], a non-decreasing function of x,
+ * so every site within distance r of a point lies in a bucket between those
+ * of the point's coordinates minus and plus r. */
+typedef struct {
+    int n[3];
+    double lo[3], h[3];
+    int64_t *start;
+    int64_t *ids;
+} or_buckets;
+
+static int bucket_coord(const or_buckets *B, int c, double x)
+{
+    double f = floor((x - B->lo[c]) / B->h[c]);
+    if (!(f >= 0.0)) return 0;
+    if (f >= (double)(B->n[c] - 1)) return B->n[c] - 1;
+    return (int)f;
+}
+
+static int buckets_build(or_buckets *B, const double *S, int64_t M, const double *box)
+{
+    double ext[3], vol = 1.0;
+    for (int c = 0; c < 3; c++) {
+        ext[c] = box[3 + c] - box[c];
+        vol *= ext[c];
+    }
+    double side = cbrt(2.0 * vol / (double)(M > 0 ? M : 1)); /* about two sites per bucket */
+    int64_t nb = 1;
+    for (int c = 0; c < 3; c++) {
+        double k = floor(ext[c] / side);
+        B->n[c] = k < 1.0 ? 1 : (k > 1024.0 ? 1024 : (int)k);
+        B->lo[c] = box[c];
+        B->h[c] = ext[c] / B->n[c];
+        nb *= B->n[c];
+    }
+    B->start = (int64_t *)calloc((size_t)nb + 1, sizeof(int64_t));
+    B->ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M > 0 ? M : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nb);
+    if (!B->start || !B->ids || !fill) {
+        free(fill);
+        return -1;
+    }
+    for (int64_t j = 0; j < M; j++) {
+        const double *p = S + 3 * j;
+        int64_t b = ((int64_t)bucket_coord(B, 0, p[0]) * B->n[1] + bucket_coord(B, 1, p[1])) * B->n[2] +
+                    bucket_coord(B, 2, p[2]);
+        B->start[b + 1]++;
+    }
+    for (int64_t b = 0; b < nb; b++) B->start[b + 1] += B->start[b];
+    memcpy(fill, B->start, sizeof(int64_t) * (size_t)nb);
+    for (int64_t j = 0; j < M; j++) {
+        const double *p = S + 3 * j;
+        int64_t b = ((int64_t)bucket_coord(B, 0, p[0]) * B->n[1] + bucket_coord(B, 1, p[1])) * B->n[2] +
+                    bucket_coord(B, 2, p[2]);
+        B->ids[fill[b]++] = j;
+    }
+    free(fill);
+    return 0;
+}
+
 typedef struct {
     const double *S;
     int64_t M;
     const double *box;
+    const or_buckets *B;
     const int64_t *cells;
     int brute;
     int maxdeg;
@@ -355,22 +422,66 @@ static void cell_item(void *vctx, int64_t ci, void *scratch)
     double lo[3] = {X->box[0], X->box[1], X->box[2]}, hi[3] = {X->box[3], X->box[4], X->box[5]};
     double vbox = (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
     double r_c = 3.0 * cbrt(vbox / (double)X->M);
+    if (!X->brute) {
+        /* first shell: three site spacings at the density of the site's own
+         * bucket. Where the shells are cut does not change the result: the
+         * candidates are still clipped in increasing (distance, index) order
+         * up to the first one beyond twice the largest vertex radius. */
+        const or_buckets *B = X->B;
+        int64_t b = ((int64_t)bucket_coord(B, 0, pm[0]) * B->n[1] + bucket_coord(B, 1, pm[1])) * B->n[2] +
+                    bucket_coord(B, 2, pm[2]);
+        double nloc = (double)(B->start[b + 1] - B->start[b]);
+        r_c = 3.0 * cbrt(B->h[0] * B->h[1] * B->h[2] / (nloc > 1.0 ? nloc : 1.0));
+    }
     double r_prev = -1.0;
     int done = 0;
     while (!done) {
         int64_t nc = 0;
-        for (int64_t j = 0; j < X->M; j++) {
-            if (j == m) continue;
-            const double *pj = X->S + 3 * j;
-            double dx = pj[0] - pm[0], dy = pj[1] - pm[1], dz = pj[2] - pm[2];
-            double d2 = dx * dx + dy * dy + dz * dz;
-            if (!X->brute) {
-                if (r_prev >= 0.0 && d2 <= r_prev * r_prev) continue; /* earlier shell */
-                if (d2 > r_c * r_c) continue;                         /* later shell */
+        /* the sites with r_prev < d <= r_c (all sites with brute), from the
+         * buckets meeting the cube of half side r_c around the site, or from
+         * a loop over all sites when that cube spans more buckets than there
+         * are sites */
+        const or_buckets *B = X->B;
+        int b0[3] = {0, 0, 0}, b1[3] = {0, 0, 0};
+        double span = 1.0;
+        if (!X->brute)
+            for (int c = 0; c < 3; c++) {
+                b0[c] = bucket_coord(B, c, pm[c] - r_c);
+                b1[c] = bucket_coord(B, c, pm[c] + r_c);
+                span *= (double)(b1[c] - b0[c] + 1);
             }
-            cand[nc].d2 = d2;
-            cand[nc].j = j;
-            nc++;
+        if (X->brute || span > (double)X->M) {
+            for (int64_t j = 0; j < X->M; j++) {
+                if (j == m) continue;
+                const double *pj = X->S + 3 * j;
+                double dx = pj[0] - pm[0], dy = pj[1] - pm[1], dz = pj[2] - pm[2];
+                double d2 = dx * dx + dy * dy + dz * dz;
+                if (!X->brute) {
+                    if (r_prev >= 0.0 && d2 <= r_prev * r_prev) continue; /* earlier shell */
+                    if (d2 > r_c * r_c) continue;                         /* later shell */
+                }
+                cand[nc].d2 = d2;
+                cand[nc].j = j;
+                nc++;
+            }
+        } else {
+            for (int ix = b0[0]; ix <= b1[0]; ix++)
+                for (int iy = b0[1]; iy <= b1[1]; iy++)
+                    for (int iz = b0[2]; iz <= b1[2]; iz++) {
+                        int64_t b = ((int64_t)ix * B->n[1] + iy) * B->n[2] + iz;
+                        for (int64_t q = B->start[b]; q < B->start[b + 1]; q++) {
+                            int64_t j = B->ids[q];
+                            if (j == m) continue;
+                            const double *pj = X->S + 3 * j;
+                            double dx = pj[0] - pm[0], dy = pj[1] - pm[1], dz = pj[2] - pm[2];
+                            double d2 = dx * dx + dy * dy + dz * dz;
+                            if (r_prev >= 0.0 && d2 <= r_prev * r_prev) continue; /* earlier shell */
+                            if (d2 > r_c * r_c) continue;                         /* later shell */
+                            cand[nc].d2 = d2;
+                            cand[nc].j = j;
+                            nc++;
+                        }
+                    }
         }
         qsort(cand, (size_t)nc, sizeof(or_cand), cand_cmp);
         double rmax = poly_rmax(P, pm);
@@ -391,7 +502,7 @@ static void cell_item(void *vctx, int64_t ci, void *scratch)
             if (2.0 * rmax + 4.0 * X->eps < r_c) done = 1;
             else {
                 r_prev = r_c;
-                r_c = fmax(2.0 * r_c, 2.0 * rmax + 8.0 * X->eps);
+                r_c = 2.0 * r_c; /* the next shell; any radius gives the same order */
                 int64_t remaining = 0;
                 for (int64_t j = 0; j < X->M && !remaining; j++) {
                     if (j == m) continue;
@@ -450,10 +561,19 @@ int oracle_cells(const double *sites, int64_t M, const double *box, const int64_
                  int brute, int maxdeg, double eps, double area_tol, int32_t *nbr, int32_t *deg, double *area,
                  double *vol, double *bbox, int32_t *err, int nthreads)
 {
-    cells_ctx X = {sites, M, box, cells, brute, maxdeg, eps, area_tol, nbr, deg, area, vol, bbox, err};
+    or_buckets B = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, NULL, NULL};
     memset(err, 0, sizeof(int32_t) * (size_t)ncells);
+    if (!brute && buckets_build(&B, sites, M, box) != 0) {
+        free(B.start);
+        free(B.ids);
+        return -1;
+    }
+    cells_ctx X = {sites, M, box, &B, cells, brute, maxdeg, eps, area_tol, nbr, deg, area, vol, bbox, err};
     size_t scratch = sizeof(or_poly) + sizeof(or_cand) * (size_t)(M > 0 ? M : 1);
-    if (or_parallel_for(ncells, cell_item, &X, scratch, nthreads) != 0) return -1;
+    int rc = or_parallel_for(ncells, cell_item, &X, scratch, nthreads);
+    free(B.start);
+    free(B.ids);
+    if (rc != 0) return -1;
     for (int64_t i = 0; i < ncells; i++)
         if (err[i]) return -1;
     return 0;
@@ -527,6 +647,7 @@ typedef struct {
     double *tau, *length, *min_margin;
     int32_t *near_tie, *nfallback, *status;
     int64_t max_steps;
+    int zmax;            /* zero-length steps in a row tolerated before the nudge */
     double eps_nudge, tie_rel;
 } trace_ctx;
 
@@ -642,7 +763,7 @@ static void trace_item(void *vctx, int64_t i, void *scratch)
         for (int c = 0; c < 3; c++) r[c] = r[c] + best * k[c];  /* R9 */
         if (best_id < 0) break;
         m = best_id;
-        if (zrun > OR_ZMAX) {
+        if (zrun > X->zmax) {
             nfb++;
             for (int c = 0; c < 3; c++) r[c] = r[c] + X->eps_nudge * k[c];
             m = locate1(X->S, X->M, X->box, r);
@@ -664,12 +785,14 @@ out:
  * candidates are all other sites plus the six walls; otherwise the CSR
  * neighbour lists off/idx (walls as -1..-6). Per ray: segments (cell, length)
  * up to cap, the count, tau = sum kappa rho l, the summed length, the
- * smallest decision margin, a near-tie flag, fallback count, status. */
+ * smallest decision margin, a near-tie flag, fallback count, status. More
+ * than zmax zero-length steps in a row nudge the point by epsilon and locate
+ * it again, as a decision without any exit does (Sect. 2.2). */
 void oracle_trace(const double *sites, int64_t M, const double *box, const int64_t *off, const int32_t *idx,
                   const double *rho, double kappa, const double *org, const double *dir, int64_t N, int64_t cap,
                   int32_t *seg_cell, double *seg_len, int32_t *nseg, double *tau, double *length,
                   double *min_margin, int32_t *near_tie, int32_t *nfallback, int32_t *status, int64_t max_steps,
-                  double tie_rel, int nthreads)
+                  int zmax, double tie_rel, int nthreads)
 {
     double dx = box[3] - box[0], dy = box[4] - box[1], dz = box[5] - box[2];
     trace_ctx X;
@@ -693,6 +816,7 @@ void oracle_trace(const double *sites, int64_t M, const double *box, const int64
     X.nfallback = nfallback;
     X.status = status;
     X.max_steps = max_steps;
+    X.zmax = zmax < 0 ? 0 : zmax;
     X.eps_nudge = 1e-12 * sqrt(dx * dx + dy * dy + dz * dz); /* R6 */
     X.tie_rel = tie_rel;
     or_parallel_for(N, trace_item, &X, 0, nthreads);

@@ -68,7 +68,7 @@ class VoronoiGrid:
     """
 
     def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=4.0,
-                 max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False):
+                 max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False, zero_run_max=4):
         lib = load()
         S = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 3))
         B = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(6))
@@ -81,6 +81,7 @@ class VoronoiGrid:
         opts.max_steps = int(max_steps)
         opts.host_only = int(bool(host_only))
         opts.gpu_build = int(bool(gpu_build))
+        opts.zero_run_max = int(zero_run_max)
         h = ctypes.c_void_p()
         args = (S.ctypes.data_as(ctypes.c_void_p), S.shape[0], B.ctypes.data_as(ctypes.c_void_p),
                 ctypes.byref(opts), ctypes.byref(h))

@@ -182,6 +182,7 @@ void vgrid_default_opts(vgrid_opts *o) {
     o->max_steps = 100000;
     o->host_only = 0;
     o->gpu_build = 0;
+    o->zero_run_max = 4;
 }
 
 static void free_events(vgrid_t *g) {
@@ -256,6 +257,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (opts) o = *opts;
     if (!(o.blocks_per_site > 0)) o.blocks_per_site = 4.0;
     if (o.max_steps <= 0) o.max_steps = 100000;
+    if (o.zero_run_max < 0) return fail(VGRID_ERR_ARG, "zero_run_max must be >= 0");
     const auto t0 = std::chrono::steady_clock::now();
 
     // sites as float32 values (the device stores float4)
@@ -587,6 +589,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     hd.eps32 = 1e-6 * diag;
     hd.scale = dmax + diag;
     hd.max_steps = o.max_steps;
+    hd.zmax = o.zero_run_max;
     if (e == cudaSuccess) e = cudaMemcpy(g->d_desc, &hd, sizeof(GridDev), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_grid(g);

@@ -92,7 +92,7 @@ struct GridDev {
     int32_t bdim[3];
     int32_t M;
     float kappa;
-    float pad0;
+    int32_t zmax;             // zero-length steps in a row before the epsilon nudge
     double eps64;             // epsilon nudge, float64 path
     double eps32;             // epsilon nudge, float32 path
     double scale;             // max |coordinate| of the box + diagonal

@@ -46,7 +46,6 @@ namespace vg {
 
 enum { RAY_OK = 0, RAY_OUTSIDE = 1, RAY_STEP_LIMIT = 2, RAY_BAD_DIR = 3 };
 
-constexpr int kZeroRunMax = 4;                      // consecutive zero-length steps before a nudge
 constexpr int kNone = 0x7fffffff;                   // "no candidate"
 constexpr float kU = 5.9604644775390625e-8f;        // 2^-24, unit roundoff of float32
 constexpr float kU2 = 3.552713678800501e-15f;       // 2^-48
@@ -978,7 +977,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                     pmz = qn.z;
                 }
                 B = nextB;
-                relocate = zrun > kZeroRunMax;
+                // more zero-length steps in a row than the grid allows: nudge
+                relocate = zrun > 0 && zrun > (BATCH ? gp->zmax : a.g1.zmax);
             }
         }
         if (relocate) {

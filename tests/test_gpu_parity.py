@@ -152,6 +152,98 @@ def test_near_perpendicular_planes_parity():
     vg.set_launch()
 
 
+def lattice_plane_starts(n, m, seed):
+    """m rays of a cubic lattice of n^3 cells in [-1,1]^3 whose start lies on
+    one, two or three lattice planes (a face, an edge or a vertex of several
+    cells), the other coordinates at least 1e-4 from any plane, isotropic
+    directions. The plane coordinates and the sites are dyadic, so a plane
+    through the start has a numerator of exactly zero in every form."""
+    rng = gen.rng_for(seed)
+    h = 2.0 / n
+    P = rng.uniform(-1 + h, 1 - h, (m, 3))
+    frac = (P + 1) / h - np.round((P + 1) / h)
+    P = np.where(np.abs(frac) * h < 1e-4, P + 2e-4, P)
+    planes = np.arange(1, n) * h - 1.0
+    for i in range(m):
+        for a in rng.choice(3, 1 + i % 3, replace=False):
+            P[i, a] = rng.choice(planes)
+    return gen.Rays(P, gen.isotropic_dirs(m, rng))
+
+
+def test_epsilon_fallback_matches_oracle():
+    """The epsilon nudge of Sect. 2.2 (zero_run_max = 0: every zero-length step
+    nudges the point by epsilon and locates it again) on rays that start on
+    lattice faces, edges and vertices, against the oracle with the same limit.
+    float64 form: the same nudges, cells and lengths as the oracle (same
+    epsilon, 1e-12 |D|). float32 form: the same cells and the same number of
+    nudges; it nudges by 1e-6 |D| (reading R6), so its path misses up to that
+    much more per nudge than the oracle's, and tau may differ by
+    kappa rho_max 1e-6 |D| per nudge beyond the usual 1e-5 relative."""
+    n = 8
+    S = gen.cubic_lattice(n)
+    rng = gen.rng_for(410)
+    g = gen.Grid(S, gen.CUBE_BOX.copy(), rng.uniform(0.5, 1.5, len(S)).astype(np.float32))
+    rays = lattice_plane_starts(n, 3000, 411)
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    rho = g.rho.astype(np.float64)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    O, D = dev(rays.origin), dev(rays.dir)
+    from paper_1310_1854_gb300 import Batch, VoronoiGrid
+    for zmax in (0, 4):
+        ref = oracle.trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, zero_run_max=zmax)
+        assert np.all(ref.status == 0)
+        nfb = int(ref.nfallback.sum())
+        if zmax == 0:
+            # a start on a plane gives a zero-length step unless the ray heads
+            # into the cell that holds the start (lowest index of the tie)
+            assert nfb >= 1500
+        else:
+            assert nfb == 0
+        vg = VoronoiGrid(g.sites, g.box, zero_run_max=zmax)
+        vg.set_density(dev(g.rho), 1.0)
+        for lpr in (1, 4):
+            vg.set_launch(lanes_per_ray=lpr, fp64_lanes_per_ray=lpr)
+            r64 = vg.trace(O, D, precision="fp64", segments=True, stats=True)
+            r32 = vg.trace(O, D, precision="fp32", segments=True, stats=True)
+            assert r64.stats["fallbacks"] == nfb and r32.stats["fallbacks"] == nfb, (zmax, r64.stats, r32.stats)
+            check_segments(ref, range(rays.origin.shape[0]), r64.seg_off, r64.seg_cell, r64.seg_len,
+                           diag, LEN64_REL)
+            check_segments(ref, range(rays.origin.shape[0]), r32.seg_off, r32.seg_cell, r32.seg_len, diag, None)
+            np.testing.assert_allclose(r64.tau.cpu().numpy(), ref.tau, rtol=1e-12, atol=0)
+            t32 = r32.tau.cpu().numpy().astype(np.float64)
+            bound = 1e-5 * ref.tau + ref.nfallback * float(g.kappa) * rho.max() * 1e-6 * diag
+            assert np.all(np.abs(t32 - ref.tau) <= bound), np.max(np.abs(t32 - ref.tau) - bound)
+            # tau mode and the batch launch take the same decisions
+            t = vg.trace(O, D, precision="fp32", stats=True)
+            np.testing.assert_array_equal(t.tau.cpu().numpy(), r32.tau.cpu().numpy())
+            assert t.stats["fallbacks"] == nfb
+        vg.set_launch()
+        b = Batch([(vg, O, D)])
+        st = b.run(stats=True)
+        np.testing.assert_array_equal(b.tau[0].cpu().numpy(), vg.trace(O, D, precision="fp32").tau.cpu().numpy())
+        assert st["fallbacks"] == nfb
+
+
+def test_zero_run_limit_does_not_touch_generic_rays():
+    """On a random grid with random rays no step has length zero, so the
+    zero-run limit changes nothing: tau is the same bits with limit 0 and 4,
+    and no ray is nudged."""
+    from paper_1310_1854_gb300 import VoronoiGrid
+    g, rays = gen.config1(5000)
+    O, D = dev(rays.origin), dev(rays.dir)
+    out = []
+    for zmax in (0, 4):
+        vg = VoronoiGrid(g.sites, g.box, zero_run_max=zmax)
+        vg.set_density(dev(g.rho), 1.0)
+        for prec in ("fp32", "fp64"):
+            r = vg.trace(O, D, precision=prec, stats=True)
+            assert r.stats["fallbacks"] == 0 and r.stats["zero_steps"] == 0
+            out.append(r.tau.cpu().numpy())
+    np.testing.assert_array_equal(out[0], out[2])
+    np.testing.assert_array_equal(out[1], out[3])
+
+
 def test_tiny_coordinates_parity():
     """Sites with tiny nonzero coordinates next to ordinary ones: their float
     differences and sums round in float64, so the float64 form takes those

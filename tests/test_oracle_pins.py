@@ -54,6 +54,101 @@ def test_worked_examples(case, mode):
     assert oracle.STATUS[int(tr.status[0])] == case.get("status", "ok")
 
 
+@pytest.mark.parametrize("case", _load("fallback_examples.json")["cases"], ids=lambda c: c["name"])
+def test_fallback_examples(case):
+    """The epsilon nudge of Sect. 2.2, on hand-worked paths: a start on a
+    face or at a lattice vertex whose zero-length steps exceed the limit Z,
+    and a list without an exit (the branch that finds no candidate)."""
+    box = np.array(case["box"], np.float64)
+    if "lattice" in case:
+        S = gen.cubic_lattice(case["lattice"], box)
+        rho = np.full(len(S), case["rho_all"])
+    else:
+        S = np.array(case["sites"], np.float64)
+        rho = np.array(case["rho"], np.float64)
+    if "lists" in case:
+        lists = case["lists"]
+        off = np.concatenate([[0], np.cumsum([len(a) for a in lists])]).astype(np.int64)
+        idx = np.concatenate([np.array(a, np.int32) for a in lists])
+    else:
+        _, off, idx = _full(S, box)
+    O = np.array([case["origin"]], np.float64)
+    D = np.array([case["dir"]], np.float64)
+    tr = oracle.trace(S, box, rho, O, D, off=off, idx=idx, kappa=case["kappa"], zero_run_max=case["zero_run_max"])
+    assert tr.status[0] == 0
+    assert int(tr.nfallback[0]) == case["nfallback"]
+    cells, lens = tr.segments(0)
+    assert [int(c) for c in cells] == [e[0] for e in case["segments"]]
+    np.testing.assert_allclose(lens, [e[1] for e in case["segments"]], rtol=0, atol=case["len_atol"])
+    assert abs(tr.tau[0] - case["tau"]) <= case["len_atol"] * max(1.0, float(rho.max()))
+    np.testing.assert_allclose(tr.length[0], sum(e[1] for e in case["segments"]), rtol=0, atol=4 * case["len_atol"])
+
+
+def test_fallback_all_sites_definition_agrees():
+    """The nudge cases through lattice vertices give the same path with every
+    site as a candidate (the plain definition of the exit)."""
+    for case in _load("fallback_examples.json")["cases"]:
+        if "lattice" not in case:
+            continue
+        box = np.array(case["box"], np.float64)
+        S = gen.cubic_lattice(case["lattice"], box)
+        rho = np.full(len(S), case["rho_all"])
+        O = np.array([case["origin"]], np.float64)
+        D = np.array([case["dir"]], np.float64)
+        tr = oracle.trace(S, box, rho, O, D, zero_run_max=case["zero_run_max"])
+        assert int(tr.nfallback[0]) == case["nfallback"]
+        assert [int(c) for c in tr.segments(0)[0]] == [e[0] for e in case["segments"]]
+        np.testing.assert_allclose(tr.segments(0)[1], [e[1] for e in case["segments"]], rtol=0,
+                                   atol=case["len_atol"])
+
+
+def test_fallback_lengths_lose_epsilon_per_nudge():
+    """Rays that start on lattice faces, edges and vertices (zero-length
+    steps) traced with Z = 4 and Z = 0: with Z = 0 every nudge skips exactly
+    epsilon of the path, so the summed length is the slab length minus
+    epsilon times the nudges, to rounding; with Z = 4 it is the slab length."""
+    n = 8
+    S = gen.cubic_lattice(n)
+    _, off, idx = _full(S, gen.CUBE_BOX)
+    rng = gen.rng_for(401)
+    m = 300
+    # points on lattice planes: one, two or three coordinates on a plane
+    P = rng.uniform(-0.95, 0.95, (m, 3))
+    planes = np.arange(1, n) * 0.25 - 1.0
+    for i in range(m):
+        k = 1 + i % 3
+        for a in rng.choice(3, k, replace=False):
+            P[i, a] = rng.choice(planes)
+    D = gen.isotropic_dirs(m, rng)
+    L = slab_length(gen.CUBE_BOX, P, D)
+    eps = oracle.default_eps(gen.CUBE_BOX)
+    t4 = oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), P, D, off=off, idx=idx, zero_run_max=4)
+    t0 = oracle.trace(S, gen.CUBE_BOX, np.ones(len(S)), P, D, off=off, idx=idx, zero_run_max=0)
+    assert np.all(t4.nfallback == 0) and np.all(t0.status == 0)
+    assert t0.nfallback.sum() >= m // 2
+    np.testing.assert_allclose(t4.length, L, rtol=1e-12)
+    err = np.abs(t0.length - (L - eps * t0.nfallback))
+    assert np.all(err <= 1e-14 + 1e-15 * t0.nseg), err.max()
+    # the cells crossed after each nudge are those of Z = 4 (the nudge is far
+    # smaller than the lattice spacing)
+    for i in range(m):
+        assert np.array_equal(t0.segments(i)[0], t4.segments(i)[0]), i
+
+
+def test_shell_search_equals_brute_force_disk():
+    """The shell-by-shell candidate search (buckets, first shell from the local
+    density) against clipping by every site, on a grid whose density spans
+    orders of magnitude."""
+    g = gen.make_disk_grid(3000, 402)
+    ids = np.concatenate([np.arange(0, 3000, 7)])
+    a = oracle.cells(g.sites, g.box, ids=ids)
+    b = oracle.cells(g.sites, g.box, ids=ids, brute=True)
+    for k in range(ids.size):
+        assert np.array_equal(a.nbr[k], b.nbr[k]), ids[k]
+    np.testing.assert_allclose(a.vol, b.vol, rtol=1e-11)
+    np.testing.assert_allclose(a.bbox, b.bbox, rtol=0, atol=1e-12)
+
+
 # --------------------------------------------------------------------------
 # cells: lattices with known cells, Delaunay adjacency, Monte Carlo volumes
 # --------------------------------------------------------------------------
