@@ -7,9 +7,18 @@ One step = start-cell location plus the traversal of every ray to the domain
 boundary, computing tau per ray, float32 plane tests with float64 rechecks.
 The float64 form runs on the same rays for comparison.
 
+The line also carries: the roofline of the traversal kernel against read
+ceilings of L2 measured in this process (the grid's cell blocks stay in L2),
+the CPU oracle timed on the host with the accuracy of both forms against it,
+and summaries of the other workloads (10^6 clumpy sites with 10^7 rays, 64
+uneven grids in one autotuned batch launch, the adjoint on the 10^6-site
+disk).
+
 With torchrun (N > 1) every rank traces its own 10^6 rays through a copy of
 the grid (weak scaling, no collective on the data path); the time is the
-maximum over ranks.
+maximum over ranks. `--gpus N` without torchrun starts N ranks under
+torch.distributed.run itself. `--dry-run` runs the rank bookkeeping of that
+path on the CPU with the gloo backend (no GPU, no timing).
 
 --impl reference times the CPU oracle (plain float64 C, the paper's loop over
 neighbour lists) on a bounded sample of the same workload.
@@ -21,6 +30,7 @@ import hashlib
 import json
 import os
 import re
+import socket
 import statistics
 import subprocess
 import sys
@@ -35,6 +45,7 @@ METRIC = "Voronoi path segments/sec on 1 GB300 (FP32+recheck vs FP64) at ≤1e-5
 UNIT = "segments/s"
 WORKLOAD = "exp-disk 1e5 sites, 1e6 rays/GPU, tau per ray, fp32 plane tests + fp64 recheck"
 L2_BYTES = 129 * 2 ** 20
+TAU32_REL = 1e-5
 
 
 def dist_info():
@@ -61,15 +72,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per traversal launch from the committed ncu summary, if it
-    was taken from the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "trace_kernel_disk1e5.md")
+def profiled(name, key):
+    """A per-launch figure from a committed ncu summary, if it was taken from
+    the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     txt = open(p).read()
     m = re.search(r"kernel source hash:\s*([0-9a-f]+)", txt)
-    t = re.search(r"dram bytes per full launch:\s*([0-9.eE+]+)", txt)
+    t = re.search(re.escape(key) + r":\s*([0-9.eE+]+)", txt)
     if m and t and m.group(1) == kernel_source_hash():
         return float(t.group(1))
     return None
@@ -131,6 +142,70 @@ def gpu_index(local_rank):
     return local_rank
 
 
+def rank_rays_seed(rank):
+    """Seed of one rank's rays: every rank traces its own 10^6 rays."""
+    import gen
+    return gen.SEED_BASE + 2 + 1000 + 7919 * rank
+
+
+# ---------------------------------------------------------------------------
+# several ranks: start them under torch.distributed.run when not started so
+# ---------------------------------------------------------------------------
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def relaunch(n, argv):
+    """Run this script as n ranks under torch.distributed.run (one node,
+    rendezvous on 127.0.0.1) with the same arguments; rank 0 prints the line.
+    Returns the launcher's exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """The multi-rank path without a GPU: gloo process group, each rank's own
+    rays, a barrier, and the reductions that form the line (max of the times,
+    sums of rays and crossings) -- the bookkeeping of the GPU leg with the
+    traversal left out."""
+    import torch
+    import torch.distributed as tdist
+
+    import gen
+    ws, rank, _ = dist_info()
+    if ws > 1:
+        tdist.init_process_group("gloo")
+    rays = gen.disk_rays(args.rays, rank_rays_seed(rank))
+    if ws > 1:
+        tdist.barrier()
+    t0 = time.perf_counter()
+    checksum = float(np.abs(rays.origin).sum())
+    dt = time.perf_counter() - t0
+
+    def red(x, op):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        tdist.all_reduce(t, op=op)
+        return float(t.item())
+
+    seconds_max = red(dt, tdist.ReduceOp.MAX if ws > 1 else None)
+    rays_all = red(float(len(rays.origin)), tdist.ReduceOp.SUM if ws > 1 else None)
+    checks = red(checksum, tdist.ReduceOp.SUM if ws > 1 else None)
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": ws, "gpus_requested": args.gpus, "rays_per_rank": args.rays,
+                          "rays_all": rays_all, "seconds_max": seconds_max, "origin_abs_sum": checks,
+                          "scaling": "weak"}), flush=True)
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle leg (rank 0, N = 1; and the --impl reference arm)
 # ---------------------------------------------------------------------------
@@ -139,7 +214,7 @@ def oracle_setup(g):
     import oracle
     oracle.build()
     t = time.time()
-    c = oracle.cells(g.sites, g.box)
+    c = oracle.cells(g.sites, g.box, maxdeg=96)
     off, idx = oracle.csr(c, len(g.sites))
     return off, idx, time.time() - t
 
@@ -151,7 +226,7 @@ def oracle_sample(g, rays, off, idx, n, seed):
     tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin[sel], rays.dir[sel], off=off, idx=idx,
                       cap=1)
     dt = time.time() - t
-    return int(tr.nseg.sum()), dt
+    return tr, sel, dt
 
 
 def oracle_threads():
@@ -159,17 +234,40 @@ def oracle_threads():
     return n if n > 0 else (os.cpu_count() or 1)
 
 
-def cpu_baseline(g, rays, target_s=10.0):
+def _rel_stats(x):
+    if x.size == 0:
+        return None
+    return {"max": float(x.max()), "p99": float(np.quantile(x, 0.99)), "mean": float(x.mean())}
+
+
+def cpu_baseline(g, rays, tau32, tau64, target_s=10.0):
+    """The oracle timed on a bounded seeded sample of the workload's rays
+    (about target_s of CPU time, all rays if they fit), and the tau of both
+    GPU forms on those rays against the oracle's."""
     off, idx, setup_s = oracle_setup(g)
     n = 2000
-    segs, dt = oracle_sample(g, rays, off, idx, n, 1)
+    tr, sel, dt = oracle_sample(g, rays, off, idx, n, 1)
     if dt < target_s:
         n = int(min(len(rays.origin), max(n, n * target_s / max(dt, 1e-3))))
-        segs, dt = oracle_sample(g, rays, off, idx, n, 2)
-    return {"value": segs / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+        tr, sel, dt = oracle_sample(g, rays, off, idx, n, 2)
+    segs = int(tr.nseg.sum())
+    base = {"value": segs / dt, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
             "sample": f"{n} of the {len(rays.origin)} rays (seeded), neighbour-list traversal with "
                       f"brute-force C(r0), float64; cell construction ({setup_s:.1f} s) not timed",
             "seconds": dt, "segments": segs}
+    ok = (tr.near_tie == 0) & (tr.status == 0) & (tr.tau > 0)
+    t32 = tau32[sel].astype(np.float64)
+    t64 = tau64[sel]
+    rel32 = np.abs(t32 - tr.tau) / np.maximum(tr.tau, 1e-300)
+    rel64 = np.abs(t64 - tr.tau) / np.maximum(tr.tau, 1e-300)
+    pos = tr.tau > 0
+    acc = {"reference": "CPU oracle, float64, neighbour lists from its own bisector clipping",
+           "rays_compared": int(n), "near_tie_fraction": float(1.0 - ok.mean()),
+           "fp32_tau_rel_err": _rel_stats(rel32[ok]), "fp64_tau_rel_err": _rel_stats(rel64[ok]),
+           "fp32_tau_rel_err_incl_near_ties": _rel_stats(rel32[pos]),
+           "fp32_rays_over_1e-5": int((rel32[ok] > TAU32_REL).sum()),
+           "oracle_fallbacks": int(tr.nfallback.sum())}
+    return base, acc
 
 
 def run_reference(args):
@@ -184,8 +282,8 @@ def run_reference(args):
         oracle_sample(g, rays, off, idx, 2000, 0)
     segs_total, secs = 0, 0.0
     for k in range(args.steps):
-        s, dt = oracle_sample(g, rays, off, idx, n, 100 + k)
-        segs_total += s
+        tr, _, dt = oracle_sample(g, rays, off, idx, n, 100 + k)
+        segs_total += int(tr.nseg.sum())
         secs += dt
     v = segs_total / secs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -197,6 +295,42 @@ def run_reference(args):
                                        f"by the oracle before timing ({setup_s:.1f} s)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# roofline
+# ---------------------------------------------------------------------------
+
+def l2_ceilings(nbytes):
+    """Read ceilings of L2 for a buffer the size of the grid's cell blocks:
+    256-bit streaming reads and the dependent chase over 288-byte blocks."""
+    from paper_1310_1854_gb300 import probe_l2
+    nbytes = int(max(nbytes, 1 << 20))
+    return {"stream_gbs": probe_l2(nbytes, "stream"), "chase_gbs": probe_l2(nbytes, "chase"), "bytes": nbytes}
+
+
+def roofline(crossings, bytes_per_crossing, kernel_ms, rel_bytes, ceil, traffic=None, kernel="trace_kernel"):
+    """Roofline entry of a traversal launch: algorithmic bytes per launch over
+    its CUDA-event time, against the level that serves its cell blocks (L2
+    when they fit in half of it, else HBM), with the other ceilings beside."""
+    hbm, hbm_kind = measured_peaks()
+    achieved = crossings * bytes_per_crossing / (kernel_ms / 1e3) / 1e9
+    r = {"achieved": achieved, "unit": "GB/s", "traffic": traffic, "kernel": kernel,
+         "algorithmic_bytes_per_crossing": bytes_per_crossing, "crossings_per_launch": crossings,
+         "kernel_ms_per_launch": kernel_ms, "cell_block_bytes": rel_bytes,
+         "hbm_peak": hbm, "frac_of_hbm": achieved / hbm,
+         "hbm_peak_source": f"{hbm_kind} hbm_gbs (MEASURED_PEAKS.json)"}
+    if ceil is not None:
+        r.update({"l2_stream_peak": ceil["stream_gbs"], "frac_of_l2_stream": achieved / ceil["stream_gbs"],
+                  "l2_chase_ceiling": ceil["chase_gbs"], "frac_of_l2_chase": achieved / ceil["chase_gbs"],
+                  "l2_source": f"measured in this process (vgrid_probe_l2) on a {ceil['bytes'] / 1e6:.0f} MB "
+                               "buffer held in L2: 256-bit streaming reads (stream) and a dependent chase over "
+                               "288-byte blocks at random positions (chase)"})
+    if rel_bytes <= 0.5 * L2_BYTES and ceil is not None:
+        r.update({"bound": "l2", "peak": ceil["stream_gbs"], "frac": achieved / ceil["stream_gbs"]})
+    else:
+        r.update({"bound": "hbm", "peak": hbm, "frac": achieved / hbm})
+    return r
 
 
 # ---------------------------------------------------------------------------
@@ -212,14 +346,29 @@ def main():
     ap.add_argument("--lanes", type=int, default=int(os.environ.get("VGRID_LANES", "0")))
     ap.add_argument("--block", type=int, default=int(os.environ.get("VGRID_BLOCK", "0")))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="leave out the summaries of the other workloads")
+    ap.add_argument("--dry-run", action="store_true", help="multi-rank bookkeeping on the CPU (gloo), no GPU")
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--workload", default="disk1e5", choices=["disk1e5", "clumpy1e6", "batched64", "grad1e6", "segments1e5", "next"],
                     help="disk1e5 is the benchmark line; the others measure the remaining workloads")
     args = ap.parse_args()
+    if args.gpus < 1:
+        ap.error("--gpus must be at least 1")
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # one process per GPU: start them, each reads its rank from the env
+        sys.exit(relaunch(args.gpus, sys.argv[1:]))
+    ws, rank, _ = dist_info()
+    if ws != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws}")
+    if args.dry_run:
+        return run_dry(args)
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
     if args.workload != "disk1e5":
+        if ws > 1:
+            sys.exit("bench.py: --workload other than disk1e5 runs on one GPU")
         return run_extra(args)
 
     import torch
@@ -235,7 +384,7 @@ def main():
     dev = torch.device("cuda", local)
 
     g, _ = gen.config2(n_rays=1)
-    rays = gen.disk_rays(args.rays, gen.SEED_BASE + 2 + 1000 + 7919 * rank)
+    rays = gen.disk_rays(args.rays, rank_rays_seed(rank))
     vg = VoronoiGrid(g.sites, g.box)
     vg.set_density(torch.from_numpy(g.rho).to(dev))
     if args.lanes or args.block:
@@ -255,6 +404,7 @@ def main():
     assert st64["crossings"] == crossings or abs(st64["crossings"] - crossings) <= 1e-6 * crossings
 
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    ceil = l2_ceilings(info["rel_bytes"])
 
     def timed(precision, out, steps, warm):
         for _ in range(warm):
@@ -297,7 +447,9 @@ def main():
     # end to end through the public call for host-resident rays
     # (vgrid_trace_host): pinned host origins and directions in, tau out to
     # pinned host memory, every step; consecutive calls overlap the next
-    # step's copy in with this step's traversal
+    # step's copy in with this step's traversal. L2 is flushed between the
+    # calls as between the device-resident steps (the flush is queued on the
+    # traversal's stream; the copies in run on the library's copy stream).
     Oh = torch.from_numpy(rays.origin).pin_memory()
     Dh = torch.from_numpy(rays.dir).pin_memory()
     Th = torch.empty(N, dtype=torch.float32).pin_memory()
@@ -310,6 +462,7 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(args.steps):
+        flush.zero_()
         vg.trace_host(Oh, Dh, precision="fp32", out_tau=Th, wait=False)
     e1.record()
     torch.cuda.synchronize()
@@ -341,11 +494,11 @@ def main():
     # roofline of the traversal kernel: algorithmic bytes per crossing
     deg = info["nnz"] / info["M"]
     bytes_per_crossing = 28.0 + 20.0 * deg
-    per_launch_bytes = crossings * bytes_per_crossing
     trace_launch_ms = tr_ms / max(launches, 1)
-    achieved = per_launch_bytes / (trace_launch_ms / 1e3) / 1e9
-    peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic()
+    traffic = profiled("trace_kernel_disk1e5.md", "dram bytes per full launch")
+    roof = roofline(crossings, bytes_per_crossing, trace_launch_ms, info["rel_bytes"], ceil, traffic,
+                    "trace_kernel<1,false,TAU,false>")
+    roof["locate_ms_per_step"] = loc_ms / max(launches, 1)
 
     if rank != 0:
         if ws > 1:
@@ -356,7 +509,7 @@ def main():
         "ms_per_step": step_ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sites": info["M"], "rays_per_gpu": N, "mean_degree": round(deg, 3),
-                   "l2": "flushed between timed steps (2x L2 buffer written)",
+                   "l2": "flushed between timed steps (2x L2 buffer written), also between the e2e calls",
                    "launch": launch, "parallelism": f"rays sharded over {ws} GPU(s)"},
         "rays_per_s": rays_all * args.steps / (step_ms_max / 1e3),
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": step64_max / k64,
@@ -366,17 +519,32 @@ def main():
         "stats_per_step": st32,
         "recheck_rate": st32["rechecks"] / max(st32["decisions"], 1),
         "gpu_launches": gpu_launches,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "trace_kernel<LPR,false,TAU>",
-                     "algorithmic_bytes_per_crossing": bytes_per_crossing, "crossings_per_launch": crossings,
-                     "kernel_ms_per_launch": trace_launch_ms, "locate_ms_per_step": loc_ms / max(launches, 1),
-                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)"},
+        "roofline": roof,
         "e2e": {"value": seg_all * args.steps / (e2e_max / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(O.numel() * 8 + D.numel() * 8), "d2h_bytes_per_step": int(N * 4)},
         "clocks": clocks,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, rays)
+        base, acc = cpu_baseline(g, rays, tau.cpu().numpy(), tau64.cpu().numpy())
+        acc.update({"gpu_recheck_rate": st32["rechecks"] / max(st32["decisions"], 1),
+                    "gpu_fallbacks_fp32": st32["fallbacks"], "gpu_fallbacks_fp64": st64["fallbacks"]})
+        line["cpu_baseline"] = base
+        line["accuracy"] = acc
+    if ws == 1 and not args.no_other_configs:
+        del O, D, tau, tau64, Oh, Dh, Th
+        del vg
+        torch.cuda.empty_cache()
+        other = {}
+        for name, fn in (("clumpy1e6", measure_clumpy1e6), ("batched64", measure_batched64),
+                         ("grad1e6", measure_grad1e6)):
+            r = fn(steps=5, warmup=3, flush=flush, sampler=ClockSampler(gpu_index(local)))
+            other[name] = {k: r[k] for k in ("value", "unit", "ms_per_step", "steps", "config", "clocks",
+                                             "gpu_launches", "roofline") if k in r}
+            for k in ("launch", "tuned", "via_segment_lists", "fd_check"):
+                if k in r:
+                    other[name][k] = r[k]
+            torch.cuda.empty_cache()
+        line["other_configs"] = other
     print(json.dumps(line), flush=True)
     if ws > 1:
         tdist.destroy_process_group()
@@ -401,181 +569,247 @@ def _events_ms(fn, steps, flush):
     return sum(a.elapsed_time(b) for a, b in ev)
 
 
-def run_extra(args):
+def _base_line():
+    return {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
+
+
+def measure_clumpy1e6(steps, warmup, flush, sampler):
+    """10^6 clumpy sites (2,000 Gaussian clumps), 10^7 uniform rays, tau."""
     import torch
 
     import gen
-    from paper_1310_1854_gb300 import Batch, VoronoiGrid
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
-    peak, peak_kind = measured_peaks()
-    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic"}
-    sampler = ClockSampler(gpu_index(0))
-    if args.workload == "next":
-        return run_next(args, line, flush, sampler)
-    if args.workload == "segments1e5":
-        g, _ = gen.config2(n_rays=1)
-        rays = gen.disk_rays(args.rays, gen.SEED_BASE + 2 + 1000)
+    from paper_1310_1854_gb300 import VoronoiGrid
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    g, rays = gen.config3()
+    vg = VoronoiGrid(g.sites, g.box)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    build_s = time.time() - t0
+    info = vg.info()
+    O = torch.from_numpy(rays.origin).to(dev)
+    D = torch.from_numpy(rays.dir).to(dev)
+    N = O.shape[0]
+    tau = torch.empty(N, dtype=torch.float32, device=dev)
+    st = vg.trace(O, D, precision="fp32", stats=True).stats
+    fn = lambda: vg.trace(O, D, precision="fp32", out_tau=tau)
+    for _ in range(warmup):
+        fn()
+    vg.enable_timing(True)
+    vg.read_timing()
+    sampler.start()
+    n0 = kernel_launches()
+    ms = _events_ms(fn, steps, flush)
+    n_kernels = kernel_launches() - n0
+    clocks = sampler.stop()
+    loc_ms, tr_ms, launches = vg.read_timing()
+    vg.enable_timing(False)
+    deg = info["nnz"] / info["M"]
+    kern = tr_ms / max(launches, 1)
+    line = dict(_base_line(), value=st["crossings"] * steps / (ms / 1e3), ms_per_step=ms / steps, steps=steps,
+                warmup=warmup,
+                config={"workload": "clumpy 1e6 sites (2,000 clumps), 1e7 uniform rays, tau per ray",
+                        "sites": info["M"], "rays": N, "mean_degree": round(deg, 3), "host_build_s": round(build_s, 2),
+                        "device_bytes": info["device_bytes"], "l2": "flushed between timed steps"},
+                stats_per_step=st, rays_per_s=N * steps / (ms / 1e3), gpu_launches=n_kernels, clocks=clocks,
+                launch=vg.get_launch(),
+                roofline=roofline(st["crossings"], 28.0 + 20.0 * deg, kern, info["rel_bytes"], None,
+                                  profiled("trace_kernel_clumpy1e6.md", "dram bytes per full launch")),
+                e2e=None)
+    line["roofline"]["locate_ms_per_step"] = loc_ms / max(launches, 1)
+    return line
+
+
+def measure_grad1e6(steps, warmup, flush, sampler):
+    """10^6-site disk, 512^2 detector + 10^6 interior rays: tau, the loss
+    sum (exp(-tau) - target)^2 and its gradient with respect to all cell
+    densities; by a second (adjoint) traversal, and from the segment lists
+    kept by the forward traversal."""
+    import torch
+
+    import gen
+    from paper_1310_1854_gb300 import VoronoiGrid
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    g, det, inner, rho_t = gen.config5()
+    rays = gen.concat_rays(det, inner)
+    vg = VoronoiGrid(g.sites, g.box)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    build_s = time.time() - t0
+    info = vg.info()
+    O = torch.from_numpy(rays.origin).to(dev)
+    D = torch.from_numpy(rays.dir).to(dev)
+    N = O.shape[0]
+    tau = torch.empty(N, dtype=torch.float32, device=dev)
+    st = vg.trace(O, D, precision="fp32", stats=True).stats
+    vg.set_density(torch.from_numpy(rho_t).to(dev))
+    target = torch.exp(-vg.trace(O, D, precision="fp32").tau)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    grad = torch.zeros(g.sites.shape[0], dtype=torch.float32, device=dev)
+
+    def fn():
+        t = vg.trace(O, D, precision="fp32", out_tau=tau).tau
+        e = torch.exp(-t)
+        dL = -2.0 * (e - target) * e
+        grad.zero_()
+        vg.trace_grad(O, D, dL, out=grad)
+
+    for _ in range(warmup):
+        fn()
+    vg.enable_timing(True)
+    vg.read_timing()
+    sampler.start()
+    n0 = kernel_launches()
+    ms = _events_ms(fn, steps, flush)
+    n_kernels = kernel_launches() - n0
+    clocks = sampler.stop()
+    loc_ms, tr_ms, launches = vg.read_timing()
+    vg.enable_timing(False)
+    segs = st["crossings"] * 2
+    kern = tr_ms / max(launches, 1)
+    cap = st["crossings"]
+
+    def fn_seg():
+        r = vg.trace(O, D, precision="fp32", segments=True, seg_capacity=cap)
+        e = torch.exp(-r.tau)
+        dL = -2.0 * (e - target) * e
+        grad.zero_()
+        vg.segments_grad(r, dL, out=grad)
+
+    g_two = grad.clone()
+    fn_seg()
+    torch.cuda.synchronize()
+    rel = float(((grad - g_two).abs().max() / g_two.abs().max()).item())
+    for _ in range(warmup):
+        fn_seg()
+    ms_seg = _events_ms(fn_seg, steps, flush)
+    deg = info["nnz"] / info["M"]
+    return dict(_base_line(), value=segs * steps / (ms / 1e3), ms_per_step=ms / steps, steps=steps, warmup=warmup,
+                config={"workload": "exp-disk 1e6 sites, 512^2 detector + 1e6 interior rays, tau and adjoint "
+                                    "d loss / d rho (two traversals per step)",
+                        "sites": info["M"], "rays": N, "mean_degree": round(deg, 3), "traversals_per_step": 2,
+                        "host_build_s": round(build_s, 2), "device_bytes": info["device_bytes"],
+                        "l2": "flushed between timed steps"},
+                stats_per_traversal=st, rays_per_s=N * 2 * steps / (ms / 1e3), gpu_launches=n_kernels,
+                clocks=clocks, launch=vg.get_launch(),
+                via_segment_lists={"value": segs * steps / (ms_seg / 1e3), "ms_per_step": ms_seg / steps,
+                                   "max_rel_diff_vs_two_traversals": rel},
+                roofline=roofline(st["crossings"], 28.0 + 20.0 * deg, kern, info["rel_bytes"], None),
+                e2e=None)
+
+
+def measure_batched64(steps, warmup, flush, sampler):
+    """64 grids (sites log-uniform in 2e3..2e5, rays log-uniform in
+    1e4..1e6) in one persistent launch replayed from a CUDA graph, with the
+    launch shape chosen by the autotuner."""
+    import torch
+
+    import gen
+    from paper_1310_1854_gb300 import Batch, VoronoiGrid, tune
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.time()
+    sets = gen.config4()
+    grids = []
+    total_sites = 0
+    for g, r in sets:
         vg = VoronoiGrid(g.sites, g.box)
         vg.set_density(torch.from_numpy(g.rho).to(dev))
-        info = vg.info()
-        O = torch.from_numpy(rays.origin).to(dev)
-        D = torch.from_numpy(rays.dir).to(dev)
-        N = O.shape[0]
-        res = {}
-        for prec in ("fp32", "fp64"):
-            r = vg.trace(O, D, precision=prec, segments=True, stats=True)
-            cap = int(r.seg_off[N].item())
-            fn = lambda: vg.trace(O, D, precision=prec, segments=True, seg_capacity=cap)
-            for _ in range(args.warmup):
-                fn()
-            steps = args.steps if prec == "fp32" else max(3, args.steps // 4)
-            vg.enable_timing(True)
-            vg.read_timing()
-            sampler.start()
-            n0 = kernel_launches()
-            ms = _events_ms(fn, steps, flush)
-            n_kernels = kernel_launches() - n0
-            clocks = sampler.stop()
-            _, tr_ms, launches = vg.read_timing()
-            vg.enable_timing(False)
-            res[prec] = (cap * steps / (ms / 1e3), ms / steps, n_kernels, clocks, r.stats, tr_ms / max(launches, 1))
-        v32, ms32, nk, clocks, st, kern = res["fp32"]
-        deg = info["nnz"] / info["M"]
-        # the traversal's algorithmic bytes per crossing plus the 8-byte slot
-        # it stores per segment
-        bpc = 28.0 + 20.0 * deg + 8.0
-        achieved = st["crossings"] * bpc / (kern / 1e3) / 1e9
-        line.update({"value": v32, "ms_per_step": ms32,
-                     "config": {"workload": "exp-disk 1e5 sites, 1e6 rays, segment list (cell, length) of every "
-                                            "ray in CSR form plus tau", "sites": info["M"], "rays": N,
-                                "segments": st["crossings"], "l2": "flushed between timed steps"},
-                     "fp64": {"value": res["fp64"][0], "ms_per_step": res["fp64"][1],
-                              "traversal_ms_per_launch": res["fp64"][5]},
-                     "stats_per_step": st, "gpu_launches": nk,
-                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                                  "frac": achieved / peak, "traffic": None, "kernel_ms_per_launch": kern,
-                                  "algorithmic_bytes_per_crossing": bpc, "peak_source": peak_kind},
-                     "e2e": None, "clocks": clocks})
-        print(json.dumps(line), flush=True)
-        return
-    if args.workload in ("clumpy1e6", "grad1e6"):
-        t0 = time.time()
-        if args.workload == "clumpy1e6":
-            g, rays = gen.config3()
-            rho = g.rho
-            desc = "clumpy 1e6 sites (2,000 clumps), 1e7 uniform rays, tau per ray"
-        else:
-            g, det, inner, rho_t = gen.config5()
-            rays = gen.concat_rays(det, inner)
-            rho = g.rho
-            desc = "exp-disk 1e6 sites, 512^2 detector + 1e6 interior rays, tau and adjoint d loss / d rho"
-        vg = VoronoiGrid(g.sites, g.box)
-        vg.set_density(torch.from_numpy(rho).to(dev))
-        build_s = time.time() - t0
-        info = vg.info()
-        O = torch.from_numpy(rays.origin).to(dev)
-        D = torch.from_numpy(rays.dir).to(dev)
-        N = O.shape[0]
-        tau = torch.empty(N, dtype=torch.float32, device=dev)
-        st = vg.trace(O, D, precision="fp32", stats=True).stats
-        deg = info["nnz"] / info["M"]
-        bpc = 28.0 + 20.0 * deg
-        if args.workload == "clumpy1e6":
-            fn = lambda: vg.trace(O, D, precision="fp32", out_tau=tau)
-        else:
-            vg.set_density(torch.from_numpy(rho_t).to(dev))
-            target = torch.exp(-vg.trace(O, D, precision="fp32").tau)
-            vg.set_density(torch.from_numpy(rho).to(dev))
-            grad = torch.zeros(g.sites.shape[0], dtype=torch.float32, device=dev)
+        grids.append((vg, torch.from_numpy(r.origin).to(dev), torch.from_numpy(r.dir).to(dev)))
+        total_sites += g.sites.shape[0]
+    build_s = time.time() - t0
+    b = Batch(grids)
+    t0 = time.time()
+    tuned = tune.autotune_batch(b)
+    tune_s = time.time() - t0
+    st = b.run(stats=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            b.run(graph=True, stream=s)
+        s.synchronize()
+        sampler.start()
+        n0 = kernel_launches()
+        ms = _events_ms(lambda: b.run(graph=True, stream=s), steps, flush)
+        n_kernels = kernel_launches() - n0
+        clocks = sampler.stop()
+    rel = sum(vg.info()["rel_bytes"] for vg, _, _ in grids)
+    return dict(_base_line(), value=st["crossings"] * steps / (ms / 1e3), ms_per_step=ms / steps, steps=steps,
+                warmup=warmup,
+                config={"workload": "64 grids, sites log-uniform 2e3..2e5, rays log-uniform 1e4..1e6, one "
+                                    "persistent launch replayed from a CUDA graph, autotuned launch shape",
+                        "grids": len(sets), "sites": total_sites, "rays": st["rays"],
+                        "host_build_s": round(build_s, 2), "l2": "flushed between timed steps"},
+                stats_per_step=st, rays_per_s=st["rays"] * steps / (ms / 1e3), gpu_launches=n_kernels,
+                clocks=clocks, launch=b.get_launch(),
+                tuned={k: tuned[k] for k in ("lanes_per_ray", "block", "blocks_per_sm", "order", "cached",
+                                             "sample_rays", "key")} | {"tune_s": round(tune_s, 2)},
+                roofline={"bound": None, "note": "the batch's grids are traced one after another (each grid's "
+                                                 "cell blocks fit in L2); no per-kernel timing in a graph",
+                          "cell_block_bytes_all_grids": rel},
+                e2e=None)
 
-            def fn():
-                t = vg.trace(O, D, precision="fp32", out_tau=tau).tau
-                e = torch.exp(-t)
-                dL = -2.0 * (e - target) * e
-                grad.zero_()
-                vg.trace_grad(O, D, dL, out=grad)
-        for _ in range(args.warmup):
+
+def measure_segments1e5(steps, warmup, flush, sampler, n_rays=1_000_000):
+    """The disk workload with segment lists (CSR cell + length) and tau."""
+    import torch
+
+    import gen
+    from paper_1310_1854_gb300 import VoronoiGrid
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g, _ = gen.config2(n_rays=1)
+    rays = gen.disk_rays(n_rays, gen.SEED_BASE + 2 + 1000)
+    vg = VoronoiGrid(g.sites, g.box)
+    vg.set_density(torch.from_numpy(g.rho).to(dev))
+    info = vg.info()
+    O = torch.from_numpy(rays.origin).to(dev)
+    D = torch.from_numpy(rays.dir).to(dev)
+    N = O.shape[0]
+    ceil = l2_ceilings(info["rel_bytes"])
+    res = {}
+    for prec in ("fp32", "fp64"):
+        r = vg.trace(O, D, precision=prec, segments=True, stats=True)
+        cap = int(r.seg_off[N].item())
+        fn = lambda: vg.trace(O, D, precision=prec, segments=True, seg_capacity=cap)
+        for _ in range(warmup):
             fn()
+        k = steps if prec == "fp32" else max(3, steps // 4)
         vg.enable_timing(True)
         vg.read_timing()
         sampler.start()
         n0 = kernel_launches()
-        ms = _events_ms(fn, args.steps, flush)
+        ms = _events_ms(fn, k, flush)
         n_kernels = kernel_launches() - n0
         clocks = sampler.stop()
-        loc_ms, tr_ms, launches = vg.read_timing()
+        _, tr_ms, launches = vg.read_timing()
         vg.enable_timing(False)
-        passes = 1 if args.workload == "clumpy1e6" else 2
-        segs = st["crossings"] * passes
-        kern = tr_ms / max(launches, 1)
-        via_segments = None
-        if args.workload == "grad1e6":
-            # the same step through the segment lists: one traversal that
-            # keeps them, then the adjoint from the lists (no second traversal)
-            cap = st["crossings"]
+        res[prec] = (cap * k / (ms / 1e3), ms / k, n_kernels, clocks, r.stats, tr_ms / max(launches, 1))
+    v32, ms32, nk, clocks, st, kern = res["fp32"]
+    deg = info["nnz"] / info["M"]
+    # the traversal's algorithmic bytes per crossing plus the 8-byte slot
+    # it stores per segment
+    bpc = 28.0 + 20.0 * deg + 8.0
+    return dict(_base_line(), value=v32, ms_per_step=ms32, steps=steps, warmup=warmup,
+                config={"workload": "exp-disk 1e5 sites, 1e6 rays, segment list (cell, length) of every ray in "
+                                    "CSR form plus tau", "sites": info["M"], "rays": N,
+                        "segments": st["crossings"], "l2": "flushed between timed steps"},
+                fp64={"value": res["fp64"][0], "ms_per_step": res["fp64"][1],
+                      "traversal_ms_per_launch": res["fp64"][5]},
+                stats_per_step=st, gpu_launches=nk, clocks=clocks,
+                roofline=roofline(st["crossings"], bpc, kern, info["rel_bytes"], ceil), e2e=None)
 
-            def fn_seg():
-                r = vg.trace(O, D, precision="fp32", segments=True, seg_capacity=cap)
-                e = torch.exp(-r.tau)
-                dL = -2.0 * (e - target) * e
-                grad.zero_()
-                vg.segments_grad(r, dL, out=grad)
 
-            g_two = grad.clone()
-            fn_seg()
-            torch.cuda.synchronize()
-            rel = float(((grad - g_two).abs().max() / g_two.abs().max()).item())
-            for _ in range(args.warmup):
-                fn_seg()
-            ms_seg = _events_ms(fn_seg, args.steps, flush)
-            via_segments = {"value": segs * args.steps / (ms_seg / 1e3), "ms_per_step": ms_seg / args.steps,
-                            "max_rel_diff_vs_two_traversals": rel}
-        line.update({"value": segs * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "config": {"workload": desc, "sites": info["M"], "rays": N, "mean_degree": round(deg, 3),
-                                "traversals_per_step": passes, "host_build_s": round(build_s, 2),
-                                "device_bytes": info["device_bytes"], "l2": "flushed between timed steps"},
-                     "stats_per_traversal": st, "rays_per_s": N * passes * args.steps / (ms / 1e3),
-                     "via_segment_lists": via_segments,
-                     "gpu_launches": n_kernels,
-                     "roofline": {"bound": "hbm", "achieved": st["crossings"] * bpc / (kern / 1e3) / 1e9, "peak": peak,
-                                  "unit": "GB/s", "frac": st["crossings"] * bpc / (kern / 1e3) / 1e9 / peak,
-                                  "traffic": None, "kernel_ms_per_launch": kern,
-                                  "algorithmic_bytes_per_crossing": bpc, "peak_source": peak_kind},
-                     "e2e": None, "clocks": clocks})
-    else:
-        t0 = time.time()
-        sets = gen.config4()
-        grids = []
-        total_sites = 0
-        for g, r in sets:
-            vg = VoronoiGrid(g.sites, g.box)
-            vg.set_density(torch.from_numpy(g.rho).to(dev))
-            grids.append((vg, torch.from_numpy(r.origin).to(dev), torch.from_numpy(r.dir).to(dev)))
-            total_sites += g.sites.shape[0]
-        build_s = time.time() - t0
-        b = Batch(grids)
-        st = b.run(stats=True)
-        s = torch.cuda.Stream()
-        with torch.cuda.stream(s):
-            for _ in range(args.warmup):
-                b.run(graph=True, stream=s)
-            s.synchronize()
-            sampler.start()
-            n0 = kernel_launches()
-            ms = _events_ms(lambda: b.run(graph=True, stream=s), args.steps, flush)
-            n_kernels = kernel_launches() - n0
-            clocks = sampler.stop()
-        line.update({"value": st["crossings"] * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "config": {"workload": "64 grids, sites log-uniform 2e3..2e5, rays log-uniform 1e4..1e6, "
-                                            "one persistent launch replayed from a CUDA graph",
-                                "grids": len(sets), "sites": total_sites, "rays": st["rays"],
-                                "host_build_s": round(build_s, 2), "l2": "flushed between timed steps"},
-                     "stats_per_step": st, "rays_per_s": st["rays"] * args.steps / (ms / 1e3),
-                     "gpu_launches": n_kernels, "roofline": None, "e2e": None, "clocks": clocks})
-    print(json.dumps(line), flush=True)
+def run_extra(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    sampler = ClockSampler(gpu_index(0))
+    if args.workload == "next":
+        base = dict(_base_line(), steps=args.steps, warmup=args.warmup)
+        return run_next(args, base, flush, sampler)
+    fn = {"segments1e5": measure_segments1e5, "clumpy1e6": measure_clumpy1e6, "grad1e6": measure_grad1e6,
+          "batched64": measure_batched64}[args.workload]
+    print(json.dumps(fn(args.steps, args.warmup, flush, sampler)), flush=True)
 
 
 def run_next(args, base, flush, sampler):

@@ -130,6 +130,9 @@ typedef struct {
     double phase_seconds[6];   /* vgrid_create by phase: checks and duplicates,
                                   cell order, cells (host or GPU), block lists,
                                   device layout, copies to the device */
+    int64_t rel_bytes;     /* bytes of the cell blocks the float32 traversal
+                              reads (the part that must stay in L2 for it to
+                              run from L2) */
 } vgrid_info_t;
 
 /* launch shape of the traversal kernels */
@@ -291,7 +294,8 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
  * Adjoint of tau = sum kappa rho l (the optical depth along the path of
  * Sect. 2.2, linear in the cell densities) with respect to rho: for every ray
  * r and every segment (c, l) of its path, dL_drho[c] += dL_dtau[r] * kappa * l.
- * The path is the one vgrid_trace finds with VGRID_FP32_RECHECK.
+ * The path is the one vgrid_trace finds with VGRID_FP32_RECHECK, and kappa
+ * is the grid's current one (vgrid_set_density).
  *   dL_dtau  device float32[N]; dL_drho device float32[M], accumulated into
  *   (caller ids; zero it first for a plain gradient).
  */
@@ -303,17 +307,20 @@ int vgrid_trace_grad(vgrid_t *g, const double *origin, const double *dir, int64_
  * the segment lists that vgrid_trace returned (VGRID_SEGMENTS with
  * VGRID_FP32_RECHECK), without tracing again: for every
  * ray r and every k in [seg_off[r], seg_off[r+1]),
- * dL_drho[seg_cell[k]] += dL_dtau[r] * kappa * seg_len[k], kappa the grid's.
+ * dL_drho[seg_cell[k]] += dL_dtau[r] * kappa * seg_len[k].
  * Each term is the product vgrid_trace_grad adds; the order of the float32
  * atomic sums differs.
  *   seg_off  device int64[N+1]; seg_cell device int32 and seg_len device
  *            float32, seg_off[N] entries each (caller ids, as returned).
  *   dL_dtau  device float32[N]; dL_drho device float32[M], accumulated into.
+ *   kappa    the opacity that the tau of these lists was computed with (the
+ *            lists do not depend on it, and the grid may hold another one
+ *            by now).
  * One pass over the lists (about 8 bytes read and one atomic per segment).
- * Errors: VGRID_ERR_ARG.
+ * Errors: VGRID_ERR_ARG (also for a kappa that is not finite).
  */
 int vgrid_segments_grad(vgrid_t *g, const int64_t *seg_off, const int32_t *seg_cell, const float *seg_len, int64_t N,
-                        const float *dL_dtau, float *dL_drho, vgrid_stream_t stream);
+                        const float *dL_dtau, float kappa, float *dL_drho, vgrid_stream_t stream);
 
 /*
  * Interaction sampling along the path: the Monte Carlo step that consumes
@@ -373,6 +380,17 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
  */
 int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_stream_t stream);
 
+/*
+ * Launch shape of a batch (lanes per ray, block, blocks per SM, ray order;
+ * fp64_lanes_per_ray is unused). NULL resets to the built-in default. A
+ * graph captured by vgrid_batch_run holds the old shape and is dropped; the
+ * next graph run captures again. Results do not depend on the shape. The
+ * first setting with order = 1 allocates the order's buffers (5 bytes per
+ * ray and the bin counts). Errors: VGRID_ERR_ARG, VGRID_ERR_NOMEM.
+ */
+int vgrid_batch_set_launch(vgrid_batch_t *b, const vgrid_launch *launch);
+int vgrid_batch_get_launch(const vgrid_batch_t *b, vgrid_launch *launch);
+
 int vgrid_batch_destroy(vgrid_batch_t *b);
 
 /*
@@ -408,6 +426,23 @@ int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *
  * race on it and must be serialised by the caller. No counters are returned
  * and nothing is synchronised.
  */
+/*
+ * Measurement helper (no counterpart in the paper): a read-bandwidth ceiling
+ * of the memory level that serves the traversal, measured on the current
+ * device, for roofline figures. It allocates a buffer of `bytes` (1 MiB to
+ * 4 GiB; below the L2 size it stays in L2 after the first pass), fills it,
+ * runs the probe once to warm it and once timed on `stream`, frees the
+ * buffer and returns the read rate in *gbs (1e9 bytes per second).
+ *   mode 0  stream: 256-bit loads of 32-byte pairs over the whole buffer,
+ *           repeated for about 8 GB.
+ *   mode 1  chase: each thread reads 288-byte blocks (nine 32-byte pairs,
+ *           the size of an average cell block of the float32 traversal) at
+ *           random positions, the next block's index taken from the data of
+ *           the previous one, at full occupancy.
+ * Synchronises `stream`. Errors: VGRID_ERR_ARG, VGRID_ERR_NOMEM, VGRID_ERR_CUDA.
+ */
+int vgrid_probe_l2(int64_t bytes, int mode, double *gbs, vgrid_stream_t stream);
+
 #define VGRID_NOALLOC_MAX_RAYS (1 << 18)
 #define VGRID_NOALLOC_SCRATCH_BYTES (512 + 64 * VGRID_NOALLOC_MAX_RAYS)
 int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import VGridError, check, load
 
-__all__ = ["VoronoiGrid", "Batch", "TraceResult", "optical_depth", "VGridError", "load"]
+__all__ = ["VoronoiGrid", "Batch", "TraceResult", "optical_depth", "probe_l2", "VGridError", "load"]
 
 _PREC = {"fp64": _lib.FP64, "fp32": _lib.FP32_RECHECK}
 
@@ -114,7 +114,8 @@ class VoronoiGrid:
         check(load().vgrid_info(self._h, ctypes.byref(i)))
         return {"M": i.M, "nnz": i.nnz, "block_entries": i.block_entries, "block_dim": list(i.block_dim),
                 "box": list(i.box), "build_seconds": i.build_seconds, "device_bytes": i.device_bytes,
-                "host_fallback_cells": i.host_fallback_cells, "phase_seconds": list(i.phase_seconds)}
+                "host_fallback_cells": i.host_fallback_cells, "phase_seconds": list(i.phase_seconds),
+                "rel_bytes": i.rel_bytes}
 
     def neighbors(self):
         """CSR (off int64[M+1], idx int32) in the caller's ids, walls -1..-6."""
@@ -263,10 +264,12 @@ class VoronoiGrid:
                                     _stream(stream)))
         return cell, s, ab
 
-    def segments_grad(self, res: TraceResult, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    def segments_grad(self, res: TraceResult, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None,
+                      kappa: float | None = None):
         """dL/drho (float32[M]) from the float32 segment lists of a trace
         (``trace(..., segments=True)``) without tracing again; accumulates
-        into ``out``."""
+        into ``out``. ``kappa``: the opacity the lists' tau was computed
+        with (default: the grid's current one)."""
         if res.seg_off is None or res.seg_len.dtype != torch.float32:
             raise TypeError("needs the float32 segment lists of trace(..., precision='fp32', segments=True)")
         N = res.seg_off.shape[0] - 1
@@ -275,8 +278,9 @@ class VoronoiGrid:
             raise ValueError("dL_dtau needs one value per ray of the trace")
         if out is None:
             out = torch.zeros(self.M, dtype=torch.float32, device=self.device)
+        k = self.kappa if kappa is None else float(kappa)
         check(load().vgrid_segments_grad(self._h, _ptr(res.seg_off), _ptr(res.seg_cell), _ptr(res.seg_len), N, _ptr(g),
-                                         _ptr(out), _stream(stream)))
+                                         k, _ptr(out), _stream(stream)))
         return out
 
     def trace_grad(self, origin, direction, dL_dtau: torch.Tensor, out: torch.Tensor | None = None, stream=None):
@@ -298,8 +302,9 @@ class Batch:
     CUDA graph on the first run and replayed afterwards.
     """
 
-    def __init__(self, sets, lanes_per_ray=1, block=128, blocks_per_sm=0):
+    def __init__(self, sets, lanes_per_ray=1, block=128, blocks_per_sm=0, order=0):
         self._keep = []
+        self.sets = list(sets)
         arr = (_lib.Rayset * len(sets))()
         self.tau = []
         self.status = []
@@ -314,10 +319,27 @@ class Batch:
             arr[i] = _lib.Rayset(grid._h.value, O.data_ptr() if O.numel() else None,
                                  D.data_ptr() if D.numel() else None, O.shape[0],
                                  t.data_ptr() if t.numel() else None, s.data_ptr() if s.numel() else None)
-        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), 0)
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), 0, int(order))
         h = ctypes.c_void_p()
         check(load().vgrid_batch_create(arr, len(sets), ctypes.byref(l), ctypes.byref(h)))
         self._h = h
+
+    def set_launch(self, lanes_per_ray=1, block=128, blocks_per_sm=0, order=0):
+        """Launch shape of the batch's traversal; order 1 takes the work items
+        of all sets longest estimated path first, otherwise set after set.
+        A captured graph is dropped (the next graph run captures again)."""
+        l = _lib.Launch(int(lanes_per_ray), int(block), int(blocks_per_sm), 0, int(order))
+        check(load().vgrid_batch_set_launch(self._h, ctypes.byref(l)))
+
+    def get_launch(self):
+        l = _lib.Launch()
+        check(load().vgrid_batch_get_launch(self._h, ctypes.byref(l)))
+        return {"lanes_per_ray": l.lanes_per_ray, "block": l.block, "blocks_per_sm": l.blocks_per_sm,
+                "order": l.order}
+
+    @property
+    def rays(self) -> int:
+        return sum(int(t.numel()) for t in self.tau)
 
     def run(self, graph=False, stats=False, stream=None):
         cs = _lib.Stats() if stats else None
@@ -335,26 +357,48 @@ class Batch:
             self._h = None
 
 
+def probe_l2(nbytes: int, mode: str = "stream", stream=None) -> float:
+    """Read-bandwidth ceiling (GB/s) measured on the current device with a
+    buffer of ``nbytes`` (held in L2 when smaller than it): ``"stream"``,
+    256-bit loads over the whole buffer, or ``"chase"``, a dependent chain of
+    288-byte blocks at random positions per thread (vgrid_probe_l2)."""
+    out = ctypes.c_double()
+    check(load().vgrid_probe_l2(int(nbytes), {"stream": 0, "chase": 1}[mode], ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
 class _OpticalDepth(torch.autograd.Function):
     """tau(rho) for fixed rays. Backward is the adjoint from the segment lists
-    kept by forward (keep_segments), else the library's adjoint traversal."""
+    kept by forward (keep_segments), else the library's adjoint traversal.
+    The adjoint uses the kappa of this forward call, whatever the grid holds
+    by the time backward runs (the paths do not depend on rho or kappa)."""
 
     @staticmethod
     def forward(ctx, rho, grid, origin, direction, kappa, keep_segments):
         grid.set_density(rho.detach().to(torch.float32).contiguous(), kappa)
         res = grid.trace(origin, direction, precision="fp32", segments=keep_segments)
         ctx.grid = grid
+        ctx.kappa = float(kappa)
         ctx.res = res if keep_segments else None
         ctx.save_for_backward(origin, direction)
         return res.tau
 
     @staticmethod
     def backward(ctx, g):
+        grid, kappa = ctx.grid, ctx.kappa
+        g = g.contiguous()
         if ctx.res is not None:
-            d = ctx.grid.segments_grad(ctx.res, g.contiguous())
+            d = grid.segments_grad(ctx.res, g, kappa=kappa)
         else:
             origin, direction = ctx.saved_tensors
-            d = ctx.grid.trace_grad(origin, direction, g.contiguous())
+            if grid.kappa == kappa:
+                d = grid.trace_grad(origin, direction, g)
+            elif grid.kappa != 0.0:
+                # the adjoint traversal multiplies by the grid's kappa
+                d = grid.trace_grad(origin, direction, g * (kappa / grid.kappa))
+            else:
+                d = grid.segments_grad(grid.trace(origin, direction, precision="fp32", segments=True), g,
+                                       kappa=kappa)
         return d, None, None, None, None, None
 
 

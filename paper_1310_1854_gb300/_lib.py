@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("M", c_int64), ("nnz", c_int64), ("block_entries", c_int64), ("block_dim", c_int32 * 3),
                 ("box", c_double * 6), ("build_seconds", c_double), ("device_bytes", c_int64),
-                ("host_fallback_cells", c_int64), ("phase_seconds", c_double * 6)]
+                ("host_fallback_cells", c_int64), ("phase_seconds", c_double * 6), ("rel_bytes", c_int64)]
 
 
 class Launch(ctypes.Structure):
@@ -94,18 +94,22 @@ SIGNATURES = [
     ("vgrid_trace_host", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_int64,
                                    c_void_p, c_void_p]),
     ("vgrid_trace_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
-    ("vgrid_segments_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    ("vgrid_segments_grad", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_float, c_void_p,
+                                      c_void_p]),
     ("vgrid_set_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_get_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_batch_create", c_int32, [ctypes.POINTER(Rayset), c_int32, ctypes.POINTER(Launch),
                                      ctypes.POINTER(c_void_p)]),
     ("vgrid_batch_run", c_int32, [c_void_p, c_int32, ctypes.POINTER(Stats), c_void_p]),
     ("vgrid_batch_destroy", c_int32, [c_void_p]),
+    ("vgrid_batch_set_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
+    ("vgrid_batch_get_launch", c_int32, [c_void_p, ctypes.POINTER(Launch)]),
     ("vgrid_enable_timing", c_int32, [c_void_p, c_int32]),
     ("vgrid_read_timing", c_int32, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                     ctypes.POINTER(c_int64)]),
     ("vgrid_interact", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p, c_void_p]),
+    ("vgrid_probe_l2", c_int32, [c_int64, c_int32, ctypes.POINTER(c_double), c_void_p]),
     ("vgrid_trace_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p, c_void_p]),
 ]
 

@@ -20,7 +20,7 @@ LIB = os.path.join(OUT, "libvgrid.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "aux.cu", "trace_lpr1.cu", "trace_lpr2.cu", "trace_lpr4.cu", "trace_lpr8.cu", "build.cpp",
-           "noalloc.cu", "build_gpu.cu"]
+           "noalloc.cu", "build_gpu.cu", "probe.cu"]
 
 
 def nvcc() -> str:

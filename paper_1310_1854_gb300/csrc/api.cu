@@ -142,6 +142,7 @@ struct vgrid {
     double phase_seconds[6] = {0, 0, 0, 0, 0, 0};
     int64_t device_bytes = 0;
     int64_t host_fallback_cells = 0;
+    int64_t rel_bytes = 0;           // bytes of the relative cell blocks
     // optional event record: {locate start, locate end} or {trace start, trace end}
     bool timing = false;
     std::vector<std::array<cudaEvent_t, 2>> ev_loc, ev_trace;
@@ -369,6 +370,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     }
     const int64_t nrec = boffs[M] + 8;   // room past the end for the last block's reads
     const int64_t nrel = foffs[M] + 8;
+    g->rel_bytes = nrel * (int64_t)sizeof(float4);
     // every float of both block arrays is written below (in parallel), so
     // they are allocated without the sequential zero fill
     std::unique_ptr<float[]> blocks(new float[4 * nrec]), rel(new float[4 * nrel]);
@@ -626,6 +628,7 @@ int vgrid_info(const vgrid_t *g, vgrid_info_t *info) {
     for (int k = 0; k < 6; k++) info->phase_seconds[k] = g->phase_seconds[k];
     info->device_bytes = g->device_bytes;
     info->host_fallback_cells = g->host_fallback_cells;
+    info->rel_bytes = g->rel_bytes;
     return VGRID_OK;
 }
 
@@ -1201,14 +1204,15 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
 }
 
 int vgrid_segments_grad(vgrid_t *g, const int64_t *seg_off, const int32_t *seg_cell, const float *seg_len, int64_t N,
-                        const float *dL_dtau, float *dL_drho, vgrid_stream_t stream) {
+                        const float *dL_dtau, float kappa, float *dL_drho, vgrid_stream_t stream) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
     if (N < 0 || (N > 0 && (!seg_off || !seg_cell || !seg_len || !dL_dtau || !dL_drho)))
         return fail(VGRID_ERR_ARG, "bad arguments");
+    if (!std::isfinite(kappa)) return fail(VGRID_ERR_ARG, "kappa is not finite");
     if (N == 0) return VGRID_OK;
     DeviceGuard dg(g->device);
-    VG_CUDA(vg::launch_segments_grad(seg_off, seg_cell, seg_len, N, dL_dtau, g->hd.kappa, dL_drho, g->sms,
+    VG_CUDA(vg::launch_segments_grad(seg_off, seg_cell, seg_len, N, dL_dtau, kappa, dL_drho, g->sms,
                                      (cudaStream_t)stream));
     return VGRID_OK;
 }
@@ -1331,13 +1335,27 @@ static void free_batch(vgrid_batch_t *b) {
     delete b;
 }
 
+static bool valid_batch_launch(const vgrid_launch *l) {
+    return valid_lpr(l->lanes_per_ray) && l->block >= 32 && l->block <= 256 && l->block % 32 == 0 &&
+           l->blocks_per_sm >= 0 && l->order >= -1 && l->order <= 1;
+}
+
+// the ray order's buffers of a batch (bins, counts, permutation)
+static int batch_order_buffers(vgrid_batch_t *b) {
+    if (b->d_order || b->total <= 0 || b->total > INT32_MAX) return VGRID_OK;
+    int64_t bytes = 0;
+    int rc;
+    if ((rc = dmalloc(&b->d_bin, (size_t)b->total, bytes)) || (rc = dmalloc(&b->d_order, (size_t)b->total, bytes)) ||
+        (rc = dmalloc(&b->d_hist, 2 * vg::kOrderBins, bytes)))
+        return rc;
+    return VGRID_OK;
+}
+
 int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *launch, vgrid_batch_t **out) {
     if (!out) return fail(VGRID_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!sets || G < 1) return fail(VGRID_ERR_ARG, "need at least one ray set");
-    if (launch && (!valid_lpr(launch->lanes_per_ray) || launch->block < 32 || launch->block > 256 ||
-                   launch->block % 32 || launch->blocks_per_sm < 0 || launch->order < -1 || launch->order > 1))
-        return fail(VGRID_ERR_ARG, "bad launch shape");
+    if (launch && !valid_batch_launch(launch)) return fail(VGRID_ERR_ARG, "bad launch shape");
     const int dev = sets[0].grid ? sets[0].grid->device : 0;
     std::vector<const vgrid_t *> uniq;
     std::vector<GridDev> descs;
@@ -1375,15 +1393,9 @@ int vgrid_batch_create(const vgrid_rayset *sets, int32_t G, const vgrid_launch *
     // longest-first ray order over all work items of the batch, only on
     // request: it interleaves the grids, whose blocks together may not fit
     // in L2, where the caller's order takes them one after another
-    {
-        const bool want = b->launch.order == 1;
-        if (want && total <= INT32_MAX && total > 0) {
-            if ((rc = dmalloc(&b->d_bin, (size_t)total, bytes)) || (rc = dmalloc(&b->d_order, (size_t)total, bytes)) ||
-                (rc = dmalloc(&b->d_hist, 2 * vg::kOrderBins, bytes))) {
-                free_batch(b);
-                return rc;
-            }
-        }
+    if (b->launch.order == 1 && (rc = batch_order_buffers(b))) {
+        free_batch(b);
+        return rc;
     }
     for (int32_t i = 0; i < G; i++) rs[i].start = b->d_start + rs[i].first;
     cudaError_t e = cudaMemcpy(b->d_grids, descs.data(), sizeof(GridDev) * descs.size(), cudaMemcpyHostToDevice);
@@ -1400,7 +1412,7 @@ static int batch_issue(vgrid_batch_t *b, cudaStream_t s) {
     RaySetDev none{};
     VG_CUDA(vg::launch_prepare(nullptr, none, b->d_queue, b->d_stats, s));
     vg::TraceArgs a{};
-    if (b->d_order) {
+    if (b->launch.order == 1 && b->d_order) {
         const vg::RayOrder ord{b->d_bin, b->d_hist, b->d_order};
         VG_CUDA(cudaMemsetAsync(b->d_hist, 0, 2 * vg::kOrderBins * sizeof(uint32_t), s));
         VG_CUDA(vg::launch_locate_ordered(b->d_grids, b->d_sets, b->G, b->total, ord, vg::PREP_FP32, b->sms, s));
@@ -1447,6 +1459,31 @@ int vgrid_batch_run(vgrid_batch_t *b, int use_graph, vgrid_stats *stats, vgrid_s
         if (rc) return rc;
     }
     if (stats) return read_stats(b->d_stats, stats, s);
+    return VGRID_OK;
+}
+
+int vgrid_batch_set_launch(vgrid_batch_t *b, const vgrid_launch *launch) {
+    if (!b) return fail(VGRID_ERR_ARG, "null batch");
+    vgrid_launch l{1, 128, 0, 1, 0};
+    if (launch) l = *launch;
+    if (!valid_batch_launch(&l)) return fail(VGRID_ERR_ARG, "bad launch shape");
+    DeviceGuard dg(b->device);
+    if (l.order == 1) {
+        int rc = batch_order_buffers(b);
+        if (rc) return rc;
+    }
+    b->launch = l;
+    // a captured graph holds the old shape: capture again on the next run
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    return VGRID_OK;
+}
+
+int vgrid_batch_get_launch(const vgrid_batch_t *b, vgrid_launch *launch) {
+    if (!b || !launch) return fail(VGRID_ERR_ARG, "null argument");
+    *launch = b->launch;
     return VGRID_OK;
 }
 

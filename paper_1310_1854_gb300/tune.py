@@ -1,4 +1,4 @@
-"""Launch-shape autotuner for the traversal kernels.
+"""Launch-shape autotuner for the traversal kernels (single grids and batches).
 
 The shape that traces fastest depends on the GPU, the arithmetic form and
 the workload (sites per grid, rays, mean path length): lanes per ray
@@ -119,6 +119,87 @@ def autotune(grid, origin, direction, precision: str = "fp32", sample: int = 200
     time_fn(best)
     entry = {"lanes_per_ray": best[0], "block": best[1], "blocks_per_sm": best[2], "ms": table[f"{best[0]},{best[1]},{best[2]}"],
              "sample_rays": n, "table": table}
+    if use_cache:
+        store(key, entry, path)
+    return dict(entry, cached=False, key=key)
+
+
+# lanes per ray, threads per block, blocks per SM, ray order (-1: set after
+# set in the caller's order, 1: all work items longest estimated path first)
+BATCH_SPACE = tuple((l, b, 0, o) for l in (1, 2, 4) for b in (64, 128, 256) for o in (-1, 1))
+
+
+def batch_key(gpu: str, G: int, sites: int, rays: int) -> str:
+    ls = int(round(math.log2(max(sites, 1))))
+    lr = int(round(math.log2(max(rays, 1))))
+    return f"{gpu}|batch|G{G}|M2^{ls}|N2^{lr}"
+
+
+def autotune_batch(batch, sample_rays: int = 4_000_000, space=BATCH_SPACE, use_cache: bool = True,
+                   path: str | None = None, repeats: int = 3) -> dict:
+    """Pick and apply the fastest launch shape (lanes per ray, block, blocks
+    per SM, ray order) for a Batch: each candidate is timed with CUDA events
+    over whole batch runs (start records and the persistent traversal) of a
+    seeded sample of every set's rays (all rays when the batch has at most
+    ``sample_rays``), the median of ``repeats`` runs; the best is cached per
+    (GPU, size class) and applied to ``batch``. Results do not depend on the
+    shape. Returns {"lanes_per_ray", "block", "blocks_per_sm", "order", "ms",
+    "cached", "key", "sample_rays", "table"}."""
+    import torch
+
+    from . import Batch
+
+    dev = batch.tau[0].device if batch.tau else torch.device("cuda")
+    name = torch.cuda.get_device_name(dev).replace("|", "/")
+    grids = {id(g): g for g, _, _ in batch.sets}
+    key = batch_key(name, len(batch.sets), sum(g.M for g in grids.values()), batch.rays)
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit:
+            batch.set_launch(hit["lanes_per_ray"], hit["block"], hit["blocks_per_sm"], hit["order"])
+            return dict(hit, cached=True, key=key)
+    total = batch.rays
+    if total > sample_rays:
+        frac = sample_rays / total
+        gen_ = torch.Generator(device="cpu").manual_seed(1310_1854)
+        sub = []
+        for g, o, d in batch.sets:
+            n = o.shape[0]
+            k = max(1, int(round(n * frac))) if n else 0
+            sel = torch.randperm(n, generator=gen_)[:k].sort().values.to(o.device)
+            sub.append((g, o.index_select(0, sel).contiguous(), d.index_select(0, sel).contiguous()))
+        probe = Batch(sub)
+        n_sample = probe.rays
+    else:
+        probe = batch
+        n_sample = total
+    prev = batch.get_launch()
+    stream = torch.cuda.current_stream(dev)
+
+    def time_fn(shape):
+        probe.set_launch(*shape)
+        probe.run(stream=stream)  # warm
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        probe.run(stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    results = {}
+    try:
+        for shape in space:
+            ts = sorted(time_fn(shape) for _ in range(repeats))
+            results[shape] = ts[len(ts) // 2]
+    except Exception:
+        batch.set_launch(prev["lanes_per_ray"], prev["block"], prev["blocks_per_sm"], prev["order"])
+        raise
+    best = min(results, key=results.get)
+    batch.set_launch(*best)
+    entry = {"lanes_per_ray": best[0], "block": best[1], "blocks_per_sm": best[2], "order": best[3],
+             "ms": results[best], "sample_rays": n_sample,
+             "table": {",".join(str(v) for v in k): t for k, t in results.items()}}
     if use_cache:
         store(key, entry, path)
     return dict(entry, cached=False, key=key)

@@ -39,8 +39,8 @@ def make(g, **kw):
 def oracle_full(g, rays, **kw):
     c = oracle.cells(g.sites, g.box)
     off, idx = oracle.csr(c, len(g.sites))
-    return oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin, rays.dir, off=off, idx=idx,
-                        kappa=float(g.kappa), **kw)
+    kw.setdefault("kappa", float(g.kappa))
+    return oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin, rays.dir, off=off, idx=idx, **kw)
 
 
 def check_segments(ref, sel, seg_off, seg_cell, seg_len, diag, len_rel):
@@ -441,6 +441,36 @@ def test_gradient_matches_oracle():
     assert np.all(np.abs(gg2 - want) <= 1e-3 * wabs + 1e-30)
 
 
+def test_gradient_uses_the_forward_kappa():
+    """Two forward calls with different kappa on one grid before backward:
+    the gradient of the first call uses its own kappa (the grid holds the
+    second one by then), on both backward routes (kept segment lists,
+    second traversal) and when the grid's kappa has been set to 0."""
+    from paper_1310_1854_gb300 import optical_depth
+    g, rays = gen.config1(2000)
+    ref = oracle_full(g, rays, kappa=2.0)
+    target = np.exp(-0.9 * ref.tau)
+    _, dL = oracle.exp_loss(ref.tau, target)
+    want = oracle.tau_grad(ref, len(g.sites), dL, kappa=2.0)
+    wabs = oracle.tau_grad(ref, len(g.sites), np.abs(dL), kappa=2.0)
+    vg = make(g)
+    O, D = dev(rays.origin), dev(rays.dir)
+    t = dev(target.astype(np.float32))
+    for keep in (True, False):
+        for later_kappa in (1.0, 0.0):
+            rho = dev(g.rho).requires_grad_(True)
+            tau = optical_depth(vg, rho, O, D, 2.0, keep_segments=keep)
+            other = dev(g.rho).requires_grad_(True)
+            optical_depth(vg, other, O, D, later_kappa, keep_segments=keep)
+            assert vg.kappa == later_kappa
+            ok = ref.near_tie == 0
+            tt = tau.detach().cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(tt[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
+            ((torch.exp(-tau) - t) ** 2).sum().backward()
+            gg = rho.grad.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(gg - want) <= 1e-3 * wabs + 1e-30), (keep, later_kappa)
+
+
 def test_batched_matches_single():
     from paper_1310_1854_gb300 import Batch
     sets = gen.config4(G=12, scale=0.02)
@@ -467,6 +497,45 @@ def test_batched_matches_single():
     ok = ref.near_tie == 0
     t = b.tau[3].cpu().numpy().astype(np.float64)
     assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
+
+
+def test_autotuned_batch_matches_single(tmp_path):
+    """The batch autotuner times its candidate shapes (lanes per ray, block,
+    ray order) on a seeded sample of every set's rays, applies the fastest to
+    the batch and caches it; a tuned batch, every shape of the space, and the
+    graph replay after a change of shape give the single-grid tau to the bit."""
+    from paper_1310_1854_gb300 import Batch, tune
+    sets = gen.config4(G=10, scale=0.02)
+    grids, single = [], []
+    for g, r in sets:
+        vg = make(g)
+        grids.append((vg, dev(r.origin), dev(r.dir)))
+        single.append(vg.trace(grids[-1][1], grids[-1][2], precision="fp32").tau.cpu().numpy())
+    b = Batch(grids)
+    space = ((1, 128, 0, -1), (2, 64, 0, 1), (1, 256, 0, 1), (4, 128, 0, -1))
+    path = str(tmp_path / "tune.json")
+    r = tune.autotune_batch(b, sample_rays=b.rays // 3, space=space, path=path)
+    assert not r["cached"] and r["sample_rays"] < b.rays and len(r["table"]) == len(space)
+    L = b.get_launch()
+    assert (L["lanes_per_ray"], L["block"], L["blocks_per_sm"], L["order"]) == \
+        (r["lanes_per_ray"], r["block"], r["blocks_per_sm"], r["order"])
+    s = torch.cuda.Stream()
+    for shape in (None,) + space:
+        if shape is not None:
+            b.set_launch(*shape)
+        b.run()
+        for k in range(len(sets)):
+            np.testing.assert_array_equal(b.tau[k].cpu().numpy(), single[k])
+        with torch.cuda.stream(s):
+            for k in range(len(sets)):
+                b.tau[k].fill_(-1.0)
+            b.run(graph=True, stream=s)
+        s.synchronize()
+        for k in range(len(sets)):
+            np.testing.assert_array_equal(b.tau[k].cpu().numpy(), single[k])
+    b.set_launch()
+    r2 = tune.autotune_batch(b, sample_rays=b.rays // 3, space=space, path=path)
+    assert r2["cached"] and b.get_launch()["order"] == r["order"]
 
 
 @pytest.mark.slow

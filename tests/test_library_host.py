@@ -36,19 +36,30 @@ def _grid(sites, box, **kw):
     return VoronoiGrid(sites, box, host_only=True, **kw)
 
 
+def _delaunay_neighbours(sites):
+    spatial = pytest.importorskip("scipy.spatial")
+    tri = spatial.Delaunay(sites)
+    ptr, nb = tri.vertex_neighbor_vertices
+    return lambda m: set(nb[ptr[m]:ptr[m + 1]].tolist())
+
+
 def _assert_cells_match(vg, sites, box, ids, area_rel=1e-9):
     off, idx = vg.neighbors()
     vol, bb = vg.cells()
     c = oracle.cells(sites, box, ids=ids)
+    delaunay = _delaunay_neighbours(sites)
     for k, m in enumerate(ids):
         ours = set(idx[off[m]:off[m + 1]].tolist())
         faces = c.nbr[k]
         big = set(faces[c.area[k] > area_rel * c.area[k].sum()].tolist())
         # every face of non-negligible area is in our list; ours may add
-        # planes that only touch the cell (they never change an exit)
+        # planes that only touch the cell (they never change an exit):
+        # those are still Delaunay neighbours (their bisector meets the
+        # cell), never walls, and there are at most two of them
         assert big <= ours, (m, big - ours)
-        assert ours <= set(faces.tolist()) | (ours - set(faces.tolist())), m
         extra = ours - set(faces.tolist())
+        assert all(j >= 0 for j in extra), (m, extra)
+        assert extra <= delaunay(m), (m, extra - delaunay(m))
         assert len(extra) <= 2, (m, extra)
     np.testing.assert_allclose(vol[ids], c.vol, rtol=1e-10)
     np.testing.assert_allclose(bb[ids], c.bbox, atol=1e-12 * np.linalg.norm(box[3:] - box[:3]))
@@ -156,7 +167,7 @@ def test_host_only_grid_refuses_device_calls(libvgrid):
     assert b"host_only" in lib.vgrid_last_error()
     assert lib.vgrid_locate(vg._h, dummy, 1, 0, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_trace_grad(vg._h, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
-    assert lib.vgrid_segments_grad(vg._h, dummy, dummy, dummy, 1, dummy, dummy, None) == _lib.ERR_ARG
+    assert lib.vgrid_segments_grad(vg._h, dummy, dummy, dummy, 1, dummy, 1.0, dummy, None) == _lib.ERR_ARG
     assert lib.vgrid_enable_timing(vg._h, 1) == _lib.ERR_ARG
 
 

@@ -80,3 +80,37 @@ def test_two_gloo_ranks_match_single_process():
         assert segs == tr.nseg.sum()
         assert tmax == world
         np.testing.assert_allclose(grad, full, rtol=1e-12, atol=1e-15)
+
+
+def _bench(*args, env=None):
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    e = dict(os.environ)
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        e.pop(k, None)
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                          env=e, timeout=600)
+
+
+def test_bench_gpus_flag_starts_the_ranks():
+    """`bench.py --gpus 2` outside torchrun starts two ranks itself (under
+    torch.distributed.run, rendezvous on 127.0.0.1); --dry-run runs their
+    bookkeeping with gloo on the CPU: rank 0 alone prints one line that
+    reports both ranks and sums their own rays."""
+    import json
+    p = _bench("--gpus", "2", "--dry-run", "--rays", "3000")
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, p.stdout
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["gpus_requested"] == 2 and d["rays_all"] == 6000
+    import bench
+    want = sum(float(np.abs(gen.disk_rays(3000, bench.rank_rays_seed(r)).origin).sum()) for r in range(2))
+    assert d["origin_abs_sum"] == pytest.approx(want, rel=1e-12)
+
+
+def test_bench_refuses_a_world_size_that_differs_from_gpus():
+    p = _bench("--gpus", "2", "--dry-run", env={"WORLD_SIZE": "1", "RANK": "0", "LOCAL_RANK": "0"})
+    assert p.returncode != 0 and "WORLD_SIZE=1" in p.stderr
