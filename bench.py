@@ -255,7 +255,9 @@ def cpu_baseline(g, rays, tau32, tau64, target_s=10.0):
             "sample": f"{n} of the {len(rays.origin)} rays (seeded), neighbour-list traversal with "
                       f"brute-force C(r0), float64; cell construction ({setup_s:.1f} s) not timed",
             "seconds": dt, "segments": segs}
-    ok = (tr.near_tie == 0) & (tr.status == 0) & (tr.tau > 0)
+    # status 3 (capacity) only says that the timing run kept one segment per
+    # ray; its tau is complete
+    ok = (tr.near_tie == 0) & np.isin(tr.status, (0, 3)) & (tr.tau > 0)
     t32 = tau32[sel].astype(np.float64)
     t64 = tau64[sel]
     rel32 = np.abs(t32 - tr.tau) / np.maximum(tr.tau, 1e-300)
