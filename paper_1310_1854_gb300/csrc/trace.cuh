@@ -54,6 +54,13 @@ constexpr float kCA = 4.0f * kU;                    // |num~ - num| <= |n|_1 (kC
 constexpr float kCB = 8.0f * kU;
 constexpr float kDivLo = 0.99999952316284180f;      // 1 - 2^-21: covers 2 ulp of __fdividef
 constexpr float kDivHi = 1.00000047683715820f;      // 1 + 2^-21
+// __fdividef's 2-ulp bound holds for divisors in [2^-126, 2^126]; above,
+// it returns 0 (a valid lower bound, not an upper one). An accepted winner
+// has its divisor below 2^125, so that the length divided out of it (by the
+// rounded denominator, at most the upper divisor plus twice its error term)
+// is in range too.
+constexpr float kDivMin = 0x1p-126f;
+constexpr float kDivMax = 0x1p125f;
 
 
 // ---------------------------------------------------------------------------
@@ -470,11 +477,14 @@ __device__ __forceinline__ Plane32 plane32(float4 q, float rx, float ry, float r
     return p;
 }
 
-// Planes with den~ <= -dden face away for certain (R2); the others get the
-// lower bound max(num~ - dnum, 0) / (den~ + dden) on s (Eq. 4), rounded down.
-// den~ + dden rounded up is > 0 exactly when den~ > -dden, so that one test
-// masks the planes facing away, and the NaN records that pad a block (for
-// which it is false) too. Branch-free: in a warp some lane nearly always has
+// dden carries 2^-126 on top of the rounding bound of den~ (added once per
+// crossing), so den_hi = den~ + dden rounded up exceeds 2^-126 for every
+// plane that may face ahead: the test den_hi > 2^-126 masks only planes with
+// n.k <= 0 (R2), and the NaN records that pad a block (for which it is
+// false), and every plane it keeps divides by a normal number, where the
+// division's error bound holds. Those planes get the lower bound
+// max(num~ - dnum, 0) / den_hi on s (Eq. 4), rounded down (above 2^126 the
+// division returns 0, still a lower bound). Branch-free: in a warp some lane nearly always has
 // a plane facing ahead, so skipping the numerator for planes facing away (the
 // sign shortcut of Sect. 2.2) would only add divergence; a masked result
 // costs nothing more. Positions past the count (several lanes per ray) are
@@ -485,7 +495,7 @@ __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float 
     const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
     float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
-    lower = (valid && den_hi > 0.0f) ? lower : __int_as_float(0x7f800000);
+    lower = (valid && den_hi > kDivMin) ? lower : __int_as_float(0x7f800000);
     const bool b = lower < c.L1;
     c.L2 = b ? c.L1 : fminf(c.L2, lower);
     c.p1 = b ? pos : c.p1;
@@ -838,7 +848,8 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
             const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
             const float n1m = hdr1.z;  // the cell's bound on |n|_1
-            const float dden = __fmul_ru(kCDen, n1m);
+            // the rounding bound of den~ plus 2^-126 (see consider32)
+            const float dden = __fadd_ru(__fmul_ru(kCDen, n1m), kDivMin);
             const float dnum = __fmul_ru(n1m, __fmaf_ru(kCA, n1m, rr));
             Cand32 c;
             exit32<LPR>(recs, cnt, f0, f1, f2, f3, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
@@ -867,7 +878,9 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 w1 = plane32(qw, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
                 const float den_lo = __fsub_rd(w1.den, w1.dden);
                 const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
-                upper = den_lo > 0.0f ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : upper;
+                // an upper bound needs the divisor in the division's range;
+                // outside it the crossing is not separated (float64 recheck)
+                upper = den_lo >= kDivMin && den_lo <= kDivMax ? __fmul_ru(__fdividef(num_hi, den_lo), kDivHi) : upper;
             }
             if (upper < c.L2) {
                 found = true;

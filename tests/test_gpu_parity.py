@@ -897,6 +897,20 @@ def test_gpu_cell_construction_matches_host(kind):
     dv, db = dev_.cells()
     np.testing.assert_allclose(dv, hv, rtol=1e-10)
     np.testing.assert_allclose(db, hb, rtol=0, atol=1e-12 * np.linalg.norm(g.box[3:] - g.box[:3]))
+    # against the oracle's own clipping on sampled cells: every face of
+    # non-negligible area is in the GPU-built list (which may add planes
+    # that only touch the cell, R7), volumes and bounding boxes agree
+    ids = np.sort(gen.rng_for(334).choice(len(g.sites), min(400, len(g.sites)), replace=False))
+    c = oracle.cells(g.sites, g.box, ids=ids)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    for k, m in enumerate(ids):
+        ours = set(di[do[m]:do[m + 1]].tolist())
+        faces = c.nbr[k]
+        big = set(faces[c.area[k] > 1e-9 * c.area[k].sum()].tolist())
+        assert big <= ours, (m, big - ours)
+        assert len(ours - set(faces.tolist())) <= 2, m
+    np.testing.assert_allclose(dv[ids], c.vol, rtol=1e-10)
+    np.testing.assert_allclose(db[ids], c.bbox, rtol=0, atol=1e-12 * diag)
     assert dev_.info()["host_fallback_cells"] < 0.001 * len(g.sites)
     # same lists, same layout: traversal agrees to the bit
     rays = gen.uniform_rays(2000, 333, g.box)
