@@ -578,8 +578,22 @@ __device__ __forceinline__ int find_set(const RaySetDev *sets, int nsets, int64_
 
 // BATCH = false: one grid, read from the parameter space (a.g1, a.s1);
 // BATCH = true: many grids and ray sets, looked up per ray.
+// Register caps of the float32 traversals: the kernel is bound by the L1
+// data pipe and load latency, and the warps it keeps in flight set how much
+// of that latency is hidden, so each instance is held to the largest count
+// that still gives it one more block of 128 threads per SM: 72 (seven
+// blocks) for tau, the adjoint and interaction sampling, 80 (six) for
+// segment lists (both forms) and the batch. The float64 tau traversal, bound
+// by the FP64 pipe, is left alone (80 registers; held to 72 it was slower).
+// The per-ray values that a crossing of the float32 form reads once live in
+// shared memory, which is what lets the float32 instances fit.
+template <bool FP64, int MODE, bool BATCH>
+constexpr int trace_max_regs() {
+    return FP64 ? (MODE == MODE_SEGS ? 80 : 255) : (BATCH || MODE == MODE_SEGS) ? 80 : 72;
+}
+
 template <int LPR, bool FP64, int MODE, bool BATCH>
-__global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
+__global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, BATCH>())) trace_kernel(TraceArgs a) {
     static_assert(LPR == 1 || LPR == 2 || LPR == 4 || LPR == 8, "lanes per ray");
     const int lane = threadIdx.x & 31;
     const int gl = lane & (LPR - 1);
@@ -605,10 +619,22 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
     // float32 for the pre-test of the planes)
     double r64[3] = {0, 0, 0}, k64[3] = {0, 0, 0};
     float kf64[3] = {0.f, 0.f, 0.f};
-    // float32 form: origin and direction as float pairs, ray parameter t, wall exit
-    float R0h[3], R0l[3], Kh[3], Kl[3];
-    float th = 0.f, tl = 0.f, tmh = 0.f, tml = 0.f, er = 0.f, ewall = 0.f;
-    int wall = -1;
+    // float32 form: origin and direction as float pairs, ray parameter t, wall
+    // exit. Only the high words of the direction (used by every plane test)
+    // and t stay in registers; the origin pairs, the low words of the
+    // direction, the wall distance and the error terms (read once per
+    // crossing) are kept per thread in shared memory.
+    float Kh[3];
+    float th = 0.f, tl = 0.f;
+    __shared__ float s_ray[FP64 ? 1 : 13][FP64 ? 1 : 256];
+    const int tix = threadIdx.x;
+#define R0h_(c) s_ray[(c)][tix]
+#define R0l_(c) s_ray[3 + (c)][tix]
+#define Kl_(c) s_ray[6 + (c)][tix]
+#define tmh_ s_ray[9][tix]
+#define tml_ s_ray[10][tix]
+#define er_ s_ray[11][tix]
+#define ewall_ s_ray[12][tix]
     int B = 0;              // block offset of the current cell
     float pmx = 0.f, pmy = 0.f, pmz = 0.f;
     double tau64 = 0.0;
@@ -754,16 +780,15 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
                 ldg_pair(p4, a0, a1);
                 ldg_pair(p4 + 2, a2, a3);
                 m = __float_as_int(a0.x);
-                wall = __float_as_int(a0.y);
-                tmh = a0.z;
-                tml = a0.w;
-                R0h[0] = a1.x; R0h[1] = a1.y; R0h[2] = a1.z;
-                R0l[0] = a1.w; R0l[1] = a2.x; R0l[2] = a2.y;
+                tmh_ = a0.z;
+                tml_ = a0.w;
+                R0h_(0) = a1.x; R0h_(1) = a1.y; R0h_(2) = a1.z;
+                R0l_(0) = a1.w; R0l_(1) = a2.x; R0l_(2) = a2.y;
                 Kh[0] = a2.z;  Kh[1] = a2.w;  Kh[2] = a3.x;
-                Kl[0] = a3.y;  Kl[1] = a3.z;  Kl[2] = a3.w;
+                Kl_(0) = a3.y;  Kl_(1) = a3.z;  Kl_(2) = a3.w;
                 const float scale = BATCH ? (float)gp->scale : (float)a.g1.scale;
-                er = 16.0f * kU2 * (scale + tmh);
-                ewall = 16.0f * kU2 * tmh;
+                er_ = 16.0f * kU2 * (scale + a0.z);
+                ewall_ = 16.0f * kU2 * a0.z;
             }
             status = m == -2 ? RAY_BAD_DIR : (m < 0 ? RAY_OUTSIDE : RAY_OK);
             if (status == RAY_OK) {
@@ -842,11 +867,11 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             pmx = hdr.x;
             pmy = hdr.y;
             pmz = hdr.z;
-            const float rx = local_coord(R0h[0], R0l[0], Kh[0], Kl[0], th, tl, pmx);
-            const float ry = local_coord(R0h[1], R0l[1], Kh[1], Kl[1], th, tl, pmy);
-            const float rz = local_coord(R0h[2], R0l[2], Kh[2], Kl[2], th, tl, pmz);
+            const float rx = local_coord(R0h_(0), R0l_(0), Kh[0], Kl_(0), th, tl, pmx);
+            const float ry = local_coord(R0h_(1), R0l_(1), Kh[1], Kl_(1), th, tl, pmy);
+            const float rz = local_coord(R0h_(2), R0l_(2), Kh[2], Kl_(2), th, tl, pmz);
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
-            const float rr = __fmaf_rn(kCB, r1, 2.0f * er);
+            const float rr = __fmaf_rn(kCB, r1, 2.0f * er_);
             const float n1m = hdr1.z;  // the cell's bound on |n|_1
             // the rounding bound of den~ plus 2^-126 (see consider32)
             const float dden = __fadd_ru(__fmul_ru(kCDen, n1m), kDivMin);
@@ -855,9 +880,9 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
             exit32<LPR>(recs, cnt, f0, f1, f2, f3, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
             // the wall ahead is one more candidate: s_w = t_max - t
             float sw, swl;
-            two_sum(tmh, -th, sw, swl);
-            sw = __fadd_rn(sw, __fadd_rn(swl, __fsub_rn(tml, tl)));
-            const float Ew = __fmaf_rn(3.0f * kU, fabsf(sw), ewall);
+            two_sum(tmh_, -th, sw, swl);
+            sw = __fadd_rn(sw, __fadd_rn(swl, __fsub_rn(tml_, tl)));
+            const float Ew = __fmaf_rn(3.0f * kU, fabsf(sw), ewall_);
             const float lw = __fsub_rd(sw, Ew);
             bool wall_wins = false;
             if (lw < c.L1) {
@@ -1054,6 +1079,13 @@ __global__ void __launch_bounds__(256) trace_kernel(TraceArgs a) {
 
     // ---------------- statistics: one global atomic per block and counter ----------------
 #undef VG_STAT
+#undef R0h_
+#undef R0l_
+#undef Kl_
+#undef tmh_
+#undef tml_
+#undef er_
+#undef ewall_
     __syncthreads();
     if (threadIdx.x < 9 && s_stats[threadIdx.x])
         atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + threadIdx.x, s_stats[threadIdx.x]);
