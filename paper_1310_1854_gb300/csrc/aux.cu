@@ -44,7 +44,10 @@ cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long
 // PREP_FP32: float32 form (cell, direction check, wall exit of Eq. 5 and the
 // float pairs of origin and direction); PREP_FP64: float64 form (cell and
 // direction check). The caller's id of the cell goes to out_caller if given.
-__global__ void __launch_bounds__(256, 4) locate_kernel(const GridDev *grids, const RaySetDev *sets, int nsets,
+// Held to five blocks of 256 threads per SM (48 registers, a few spilled):
+// the kernel waits on its loads, and the extra warps hide more of that wait
+// than the spilled bytes cost.
+__global__ void __launch_bounds__(256, 5) locate_kernel(const GridDev *grids, const RaySetDev *sets, int nsets,
                                                      int64_t total, int prep, int32_t *out_caller, uint8_t *bin,
                                                      uint32_t *hist) {
     __shared__ uint32_t s_hist[kOrderBins];
