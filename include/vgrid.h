@@ -231,9 +231,11 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  *   ray_status    device int32[N] or NULL: VGRID_RAY_* per ray.
  *   stats         host or NULL: counters of this call (synchronises `stream`).
  * Segment mode traces once: each ray appends its segments to chunks of 8 in
- * a work buffer of the library, the counts are scanned into seg_off, the
- * total is read back to the host, and a copy kernel moves the chunks into
- * seg_cell / seg_len in ray order. If seg_capacity is too small it returns
+ * a work buffer of the library, the counts are scanned into seg_off, and a
+ * copy kernel moves the chunks into seg_cell / seg_len in ray order (the
+ * copy compares the total with seg_capacity on the device and writes
+ * nothing if it does not fit); the call reads the total back and
+ * synchronises once, at its end. If seg_capacity is too small it returns
  * VGRID_ERR_CAPACITY with seg_off filled so the caller can size the buffers
  * and call again (seg_capacity = 0 only counts). The work buffer holds
  * ceil(seg_capacity/8) + min(N, seg_capacity) + 32 x (warps of the launch)

@@ -1074,19 +1074,23 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     if ((rc = launch_trace(fn, L, g->sms, N, a, s))) return rc;
     mark(g, 1, 1, s);
     VG_CUDA(vg::launch_exclusive_scan(seg_off, N, g->d_scan, s));
+    // the copy compares the total with the capacity on the device, so the
+    // call synchronises once, at its end
+    const bool have = seg_cell && seg_len;
+    VG_CUDA(vg::launch_compact_segments(seg_off, N, chunks, g->d_cursor, g->d_chunk_meta, g->d_slots, fp64 != 0,
+                                        have ? seg_capacity : 0, g->d_coff, g->d_scan, g->d_chunk_inv, seg_cell,
+                                        seg_len, g->sms, s));
     int64_t total = 0;
     unsigned long long taken = 0;
     VG_CUDA(cudaMemcpyAsync(&total, seg_off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     VG_CUDA(cudaMemcpyAsync(&taken, g->d_cursor, sizeof(taken), cudaMemcpyDeviceToHost, s));
-    VG_CUDA(cudaStreamSynchronize(s));
-    if (total > seg_capacity || (total > 0 && (!seg_cell || !seg_len)))
+    const int src = read_stats(g->d_stats, stats, s);  // synchronises
+    if (total > seg_capacity || (total > 0 && !have))
         return fail(VGRID_ERR_CAPACITY, "segment buffers hold " + std::to_string(seg_capacity) + ", need " +
                                             std::to_string(total));
     if ((int64_t)taken > chunks)  // cannot happen when the total fits (see above)
         return fail(VGRID_ERR_CUDA, "segment chunk pool ran out");
-    VG_CUDA(vg::launch_compact_segments(seg_off, N, (int64_t)taken, g->d_chunk_meta, g->d_slots, fp64 != 0, g->d_coff,
-                                        g->d_scan, g->d_chunk_inv, seg_cell, seg_len, g->sms, s));
-    return read_stats(g->d_stats, stats, s);
+    return src;
 }
 
 int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_t N, int precision, void *tau,

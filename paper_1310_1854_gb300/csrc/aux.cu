@@ -404,13 +404,19 @@ __global__ void __launch_bounds__(kScanThreads) scan_fix_kernel(int64_t *data, i
 // stores are coalesced: (1) chunks per ray, ceil(n / kSegChunk), scanned into
 // coff; (2) each used chunk c of ray r at position k is entered as
 // inv[coff[r] + k] = c; (3) kSegChunk threads per destination chunk copy its
-// slots to the ray's offset plus kSegChunk * k.
+// slots to the ray's offset plus kSegChunk * k. The number of chunks the
+// traversal took and the total are read on the device: when the total
+// exceeds the caller's capacity (some chunks were never stored) steps 2 and
+// 3 do nothing, and only the offsets go back.
 __global__ void chunk_counts_kernel(const int64_t *off, int64_t N, int64_t *ccount) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x)
         ccount[r] = (__ldg(off + r + 1) - __ldg(off + r) + kSegChunk - 1) / kSegChunk;
 }
 
-__global__ void chunk_invert_kernel(const int2 *meta, int64_t nchunks, const int64_t *coff, int32_t *inv) {
+__global__ void chunk_invert_kernel(const int2 *meta, const unsigned long long *cursor, int64_t chunk_cap,
+                                    const int64_t *off, int64_t N, int64_t cap, const int64_t *coff, int32_t *inv) {
+    if (__ldg(off + N) > cap) return;
+    const int64_t nchunks = min((int64_t)*cursor, chunk_cap);
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nchunks;
          c += (int64_t)gridDim.x * blockDim.x) {
         const int2 m = __ldg(meta + c);
@@ -420,8 +426,9 @@ __global__ void chunk_invert_kernel(const int2 *meta, int64_t nchunks, const int
 
 template <bool FP64>
 __global__ void __launch_bounds__(256) compact_segments_kernel(const int64_t *off, const int64_t *coff, int64_t N,
-                                                               const int32_t *inv, const int2 *meta, const void *slots,
-                                                               int32_t *cell, void *len) {
+                                                               int64_t cap, const int32_t *inv, const int2 *meta,
+                                                               const void *slots, int32_t *cell, void *len) {
+    if (__ldg(off + N) > cap) return;
     const int64_t nd = __ldg(coff + N);  // destination chunks
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nd * kSegChunk; t += stride) {
@@ -447,23 +454,24 @@ static int grid_for(int64_t threads, int sms) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)sms * 8));
 }
 
-cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchunks, const int2 *meta,
-                                    const void *slots, bool fp64, int64_t *coff, int64_t *scan_tmp, int32_t *inv,
-                                    int32_t *cell, void *len, int sms, cudaStream_t s) {
-    if (N <= 0 || nchunks <= 0) return cudaSuccess;
+cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t chunk_cap, const unsigned long long *cursor,
+                                    const int2 *meta, const void *slots, bool fp64, int64_t cap, int64_t *coff,
+                                    int64_t *scan_tmp, int32_t *inv, int32_t *cell, void *len, int sms,
+                                    cudaStream_t s) {
+    if (N <= 0 || chunk_cap <= 0 || !cell || !len) return cudaSuccess;
     chunk_counts_kernel<<<grid_for(N, sms), 256, 0, s>>>(off, N, coff);
     count_launches(1);
     cudaError_t e = launch_exclusive_scan(coff, N, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    chunk_invert_kernel<<<grid_for(nchunks, sms), 256, 0, s>>>(meta, nchunks, coff, inv);
+    chunk_invert_kernel<<<grid_for(chunk_cap, sms), 256, 0, s>>>(meta, cursor, chunk_cap, off, N, cap, coff, inv);
     count_launches(1);
-    // destination chunks: coff[N] (read on the device), at most nchunks
+    // destination chunks: coff[N] (read on the device), at most chunk_cap
     if (fp64)
-        compact_segments_kernel<true><<<grid_for(nchunks * kSegChunk, sms), 256, 0, s>>>(off, coff, N, inv, meta,
-                                                                                         slots, cell, len);
+        compact_segments_kernel<true><<<grid_for(chunk_cap * kSegChunk, sms), 256, 0, s>>>(off, coff, N, cap, inv,
+                                                                                           meta, slots, cell, len);
     else
-        compact_segments_kernel<false><<<grid_for(nchunks * kSegChunk, sms), 256, 0, s>>>(off, coff, N, inv, meta,
-                                                                                          slots, cell, len);
+        compact_segments_kernel<false><<<grid_for(chunk_cap * kSegChunk, sms), 256, 0, s>>>(off, coff, N, cap, inv,
+                                                                                            meta, slots, cell, len);
     count_launches(1);
     return cudaGetLastError();
 }

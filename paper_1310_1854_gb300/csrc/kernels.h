@@ -104,12 +104,15 @@ cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm,
 // nrec entries of `cells`
 cudaError_t launch_build_rec64(const float4 *site, const float4 *rel, const float4 *cells, int64_t M, int64_t nrec,
                                float4 *rec64, int sms, cudaStream_t s);
-// copy the segments in chunks 0..nchunks-1 (see kSegChunk) of rays 0..N-1
-// into the CSR arrays at the scanned offsets off[0..N]; coff holds N+1 and
-// inv nchunks values of scratch, scan_tmp scan_tmp_elems(N)
-cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t nchunks, const int2 *meta,
-                                    const void *slots, bool fp64, int64_t *coff, int64_t *scan_tmp, int32_t *inv,
-                                    int32_t *cell, void *len, int sms, cudaStream_t s);
+// copy the segments of the chunks the traversal took (read from the chunk
+// cursor on the device, at most chunk_cap; see kSegChunk) of rays 0..N-1
+// into the CSR arrays at the scanned offsets off[0..N], unless off[N]
+// exceeds cap (then nothing is written); coff holds N+1 and inv chunk_cap
+// values of scratch, scan_tmp scan_tmp_elems(N)
+cudaError_t launch_compact_segments(const int64_t *off, int64_t N, int64_t chunk_cap, const unsigned long long *cursor,
+                                    const int2 *meta, const void *slots, bool fp64, int64_t cap, int64_t *coff,
+                                    int64_t *scan_tmp, int32_t *inv, int32_t *cell, void *len, int sms,
+                                    cudaStream_t s);
 // adjoint from segment lists: out[cell[k]] += g[r] * kappa * len[k] for the
 // segments k of every ray r (CSR offsets off[0..N])
 cudaError_t launch_segments_grad(const int64_t *off, const int32_t *cell, const float *len, int64_t N, const float *g,
