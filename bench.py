@@ -65,12 +65,18 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the sources that define the traversal kernel (a committed ncu
-    summary carries it, so a figure taken from an older kernel is not used)."""
+    """Hash of the sources that define the traversal kernel: trace.cuh, the
+    descriptors in internal.h and fsplit.h, and the kernel's argument struct
+    in kernels.h (a committed ncu summary carries it, so a figure taken from
+    an older kernel is not used)."""
     h = hashlib.sha256()
-    for f in ("trace.cuh", "kernels.h", "internal.h", "fsplit.h"):
-        with open(os.path.join(ROOT, "paper_1310_1854_gb300", "csrc", f), "rb") as fh:
+    src = os.path.join(ROOT, "paper_1310_1854_gb300", "csrc")
+    for f in ("trace.cuh", "internal.h", "fsplit.h"):
+        with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
+    k = open(os.path.join(src, "kernels.h")).read()
+    i = k.index("struct TraceArgs")
+    h.update(k[i:k.index("};", i)].encode())
     return h.hexdigest()[:16]
 
 
