@@ -205,3 +205,28 @@ def test_launch_shape_validation(libvgrid):
     lib = _lib.load()
     assert lib.vgrid_set_launch(vg._h, None) == 0
     assert vg.get_launch()["order"] == 0
+
+
+def test_probe_rejects_bad_arguments(libvgrid):
+    """vgrid_probe_l2 checks its arguments before touching a device."""
+    from paper_1310_1854_gb300 import _lib
+    lib = _lib.load()
+    out = ctypes.c_double(-1.0)
+    assert lib.vgrid_probe_l2(1 << 24, 2, ctypes.byref(out), None) == _lib.ERR_ARG
+    assert lib.vgrid_probe_l2(1000, 0, ctypes.byref(out), None) == _lib.ERR_ARG
+    assert lib.vgrid_probe_l2((1 << 32) + 1, 1, ctypes.byref(out), None) == _lib.ERR_ARG
+    assert lib.vgrid_probe_l2(1 << 24, 0, None, None) == _lib.ERR_ARG
+    assert out.value == -1.0
+
+
+def test_zero_run_limit_option(libvgrid):
+    """opts.zero_run_max: 4 by default, 0 allowed, negative refused."""
+    from paper_1310_1854_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.Opts()
+    lib.vgrid_default_opts(ctypes.byref(o))
+    assert o.zero_run_max == 4
+    _grid(gen.cubic_lattice(2), gen.CUBE_BOX, zero_run_max=0)
+    with pytest.raises(_lib.VGridError) as e:
+        _grid(gen.cubic_lattice(2), gen.CUBE_BOX, zero_run_max=-1)
+    assert e.value.code == _lib.ERR_ARG
