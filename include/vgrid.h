@@ -86,7 +86,7 @@ typedef struct {
     int32_t round_sites;       /* 1: round sites to float32; 0: reject sites that are
                                   not exactly representable in float32 */
     int32_t reorder;           /* 1 (default): store cells along a Morton curve */
-    double blocks_per_site;    /* locate block grid: blocks per site (default 4) */
+    double blocks_per_site;    /* locate block grid: blocks per site (default 8) */
     int64_t max_steps;         /* exit decisions per ray before VGRID_RAY_STEP_LIMIT
                                   (default 100,000) */
     int32_t host_only;         /* 1: build the neighbour lists, volumes and block

@@ -67,7 +67,7 @@ class VoronoiGrid:
     bounding boxes and block lists are built on the host by the library.
     """
 
-    def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=4.0,
+    def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=8.0,
                  max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False, zero_run_max=4):
         lib = load()
         S = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 3))

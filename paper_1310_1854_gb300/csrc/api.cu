@@ -179,7 +179,7 @@ void vgrid_default_opts(vgrid_opts *o) {
     o->threads = 0;
     o->round_sites = 0;
     o->reorder = 1;
-    o->blocks_per_site = 4.0;
+    o->blocks_per_site = 8.0;
     o->max_steps = 100000;
     o->host_only = 0;
     o->gpu_build = 0;
@@ -256,7 +256,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     vgrid_opts o;
     vgrid_default_opts(&o);
     if (opts) o = *opts;
-    if (!(o.blocks_per_site > 0)) o.blocks_per_site = 4.0;
+    if (!(o.blocks_per_site > 0)) o.blocks_per_site = 8.0;
     if (o.max_steps <= 0) o.max_steps = 100000;
     if (o.zero_run_max < 0) return fail(VGRID_ERR_ARG, "zero_run_max must be >= 0");
     const auto t0 = std::chrono::steady_clock::now();
