@@ -2,7 +2,9 @@
 
 Rays are independent (Sect. 2.2 traces each path on its own), so the forward
 pass splits the rays across ranks with the grid replicated and needs no
-exchange; results stay on the rank that traced them. The adjoint is the one
+exchange; results stay on the rank that traced them. A batch of many grids
+is split by whole grids instead, each rank taking a set of grids whose
+estimated crossings add up to about the same work. The adjoint is the one
 place with a real exchange: every rank adds its rays' contributions to the
 same per-cell gradient, so the partial gradients are summed across ranks.
 These helpers work with any torch.distributed backend (NCCL on GPUs, gloo
@@ -52,3 +54,31 @@ def sharded_density_grad(grid, origin, direction, dL_dtau, group=None):
     its own rays, then the per-cell partial gradients are summed."""
     g = grid.trace_grad(origin, direction, dL_dtau)
     return allreduce_sum_(g, group)
+
+
+def estimated_crossings(n_rays: int, n_sites: int) -> float:
+    """Relative work of tracing n_rays through a grid of n_sites sites in a
+    box of fixed size: the faces a line crosses per unit length grow as the
+    cube root of the site density, so crossings ~ n_rays n_sites^(1/3)."""
+    return float(n_rays) * float(max(n_sites, 1)) ** (1.0 / 3.0)
+
+
+def assign_sets(weights, world: int) -> list[int]:
+    """Rank of each set (grid and its rays) of a batch, for `world` ranks:
+    the sets are taken heaviest first and each goes to the rank with the
+    least work so far (ties to the lower rank). Deterministic, so every rank
+    computes the same assignment without an exchange; the most loaded rank
+    carries at most 4/3 of the optimum (the bound of this greedy rule)."""
+    if world < 1:
+        raise ValueError("world size must be at least 1")
+    w = [float(x) for x in weights]
+    if any(x < 0 for x in w):
+        raise ValueError("weights must be non-negative")
+    order = sorted(range(len(w)), key=lambda i: (-w[i], i))
+    load = [0.0] * world
+    out = [0] * len(w)
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        out[i] = r
+        load[r] += w[i]
+    return out

@@ -114,3 +114,69 @@ def test_bench_gpus_flag_starts_the_ranks():
 def test_bench_refuses_a_world_size_that_differs_from_gpus():
     p = _bench("--gpus", "2", "--dry-run", env={"WORLD_SIZE": "1", "RANK": "0", "LOCAL_RANK": "0"})
     assert p.returncode != 0 and "WORLD_SIZE=1" in p.stderr
+
+
+def test_assign_sets_balances_the_batch():
+    from paper_1310_1854_gb300.shard import assign_sets, estimated_crossings
+    plan = gen.config4_plan()
+    w = [estimated_crossings(n, m) for _, m, n in plan]
+    for world in (1, 2, 3, 4, 8):
+        a = assign_sets(w, world)
+        assert len(a) == len(w) and set(a) <= set(range(world))
+        load = np.bincount(a, weights=w, minlength=world)
+        # greedy largest-first: within 4/3 of the optimum, and no worse than
+        # the mean plus the largest single set
+        lower = max(sum(w) / world, max(w))
+        assert load.max() <= 4.0 / 3.0 * lower + 1e-9
+        assert load.max() <= sum(w) / world + max(w) + 1e-9
+        assert a == assign_sets(w, world)  # the same on every rank
+    assert assign_sets([], 4) == []
+    with pytest.raises(ValueError):
+        assign_sets([1.0], 0)
+    with pytest.raises(ValueError):
+        assign_sets([-1.0], 2)
+
+
+def _batch_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1310_1854_gb300.shard import assign_sets, estimated_crossings, sum_over_ranks
+        sets = gen.config4(G=6, scale=0.01)
+        a = assign_sets([estimated_crossings(len(r.origin), len(g.sites)) for g, r in sets], world)
+        segs = 0.0
+        for k, (g, r) in enumerate(sets):
+            if a[k] != rank:
+                continue
+            c = oracle.cells(g.sites, g.box, threads=1)
+            off, idx = oracle.csr(c, len(g.sites))
+            tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), r.origin, r.dir, off=off, idx=idx, threads=1)
+            segs += float(tr.nseg.sum())
+        out[rank] = (sum_over_ranks(segs), a)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_split_a_batch_by_grid():
+    """A batch split by whole grids over two gloo ranks (oracle standing in
+    for the GPUs): both ranks compute the same assignment, and the summed
+    crossings equal those of one process tracing every grid."""
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_batch_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    total = 0
+    for g, r in gen.config4(G=6, scale=0.01):
+        c = oracle.cells(g.sites, g.box)
+        off, idx = oracle.csr(c, len(g.sites))
+        total += int(oracle.trace(g.sites, g.box, g.rho.astype(np.float64), r.origin, r.dir, off=off, idx=idx).nseg.sum())
+    assert out[0][1] == out[1][1] and set(out[0][1]) == {0, 1}
+    assert out[0][0] == out[1][0] == total
