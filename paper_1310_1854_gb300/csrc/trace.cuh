@@ -131,9 +131,11 @@ __device__ __forceinline__ int rec_w(float4 q) { return __float_as_int(q.w); }
 
 // Two consecutive float4 in one 256-bit load (p 32-byte aligned). The lanes of
 // a warp read unrelated blocks, so every lane touches its own 32-byte sector:
-// one request per sector instead of one per half sector.
+// one request per sector instead of one per half sector. The data is used
+// once by the lane that reads it and almost never found in L1 again (the
+// blocks the resident warps read exceed it), so it is not kept there.
 __device__ __forceinline__ void ldg_pair(const float4 *p, float4 &a, float4 &b) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }
@@ -450,6 +452,10 @@ static __device__ __noinline__ int locate_point(const GridDev *gp, const LocPt P
 struct Cand32 {
     float L1, L2;        // smallest and second smallest lower bound
     int p1;              // record position (1-based) of the smallest, 0 if none
+    // one lane per ray: the smallest's plane terms and neighbour offset, kept
+    // so that the winner's record is not read again
+    float num1, den1;
+    int w1;
 };
 
 // Terms of the bisector of the current site p (origin of the local frame)
@@ -483,22 +489,33 @@ __device__ __forceinline__ Plane32 plane32(float4 q, float rx, float ry, float r
 // n.k <= 0 (R2), and the NaN records that pad a block (for which it is
 // false), and every plane it keeps divides by a normal number, where the
 // division's error bound holds. Those planes get the lower bound
-// max(num~ - dnum, 0) / den_hi on s (Eq. 4), rounded down (above 2^126 the
-// division returns 0, still a lower bound). Branch-free: in a warp some lane nearly always has
+// a / den_hi on s (Eq. 4), a = max((num~ - dnum) kDivLo, 0) rounded down in
+// one fused multiply-add (dnumK = dnum kDivLo rounded up, once per
+// crossing): the factor kDivLo = 1 - 2^-21 taken out of the numerator covers
+// the division's 2 ulp (2^-22 relative), so the quotient stays below
+// (num~ - dnum) / den_hi (above 2^126 the division returns 0, still a lower
+// bound). Branch-free: in a warp some lane nearly always has
 // a plane facing ahead, so skipping the numerator for planes facing away (the
 // sign shortcut of Sect. 2.2) would only add divergence; a masked result
 // costs nothing more. Positions past the count (several lanes per ray) are
 // masked by `valid`.
-__device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float rx, float ry, float rz, float dnum,
+template <bool KEEP>
+__device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float rx, float ry, float rz, float dnumK,
                                            float dden, float Kx, float Ky, float Kz, Cand32 &c) {
-    const Plane32 p = plane32(q, rx, ry, rz, dnum, dden, Kx, Ky, Kz);
-    const float num_lo = fmaxf(__fsub_rd(p.num, p.dnum), 0.0f);
+    const Plane32 p = plane32(q, rx, ry, rz, dnumK, dden, Kx, Ky, Kz);
+    const float num_lo = fmaxf(__fmaf_rd(p.num, kDivLo, -dnumK), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
-    float lower = __fmul_rd(__fdividef(num_lo, den_hi), kDivLo);
+    float lower = __fdividef(num_lo, den_hi);
     lower = (valid && den_hi > kDivMin) ? lower : __int_as_float(0x7f800000);
     const bool b = lower < c.L1;
     c.L2 = b ? c.L1 : fminf(c.L2, lower);
-    c.p1 = b ? pos : c.p1;
+    if (KEEP) {
+        c.num1 = b ? p.num : c.num1;
+        c.den1 = b ? p.den : c.den1;
+        c.w1 = b ? rec_w(q) : c.w1;
+    } else {
+        c.p1 = b ? pos : c.p1;
+    }
     c.L1 = fminf(c.L1, lower);
 }
 
@@ -508,26 +525,29 @@ __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float 
 // so they do not wait for the count, and no position is ever past the count.
 template <int LPR>
 __device__ __forceinline__ void exit32(const float4 *recs, int cnt, float4 f0, float4 f1, float4 f2, float4 f3,
-                                       float rx, float ry, float rz, float dnum, float dden, float Kx, float Ky,
+                                       float rx, float ry, float rz, float dnumK, float dden, float Kx, float Ky,
                                        float Kz, unsigned gmask, int gl, int gbase, Cand32 &c) {
     c.L1 = __int_as_float(0x7f800000);
     c.L2 = c.L1;
     c.p1 = 0;
+    c.num1 = 0.f;
+    c.den1 = 1.f;
+    c.w1 = 0;
     if (LPR == 1) {
-        consider32(1, true, f0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(2, true, f1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(3, true, f2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-        consider32(4, true, f3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+        consider32<true>(1, true, f0, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+        consider32<true>(2, true, f1, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+        consider32<true>(3, true, f2, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+        consider32<true>(4, true, f3, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
         const float nan = __int_as_float(0x7fc00000);
         for (int p = 5; p <= cnt; p += 4) {
             // the last group may hold one pair: the other reads as NaN records
             float4 q0, q1, q2 = make_float4(nan, nan, nan, nan), q3 = q2;
             ldg_pair(recs + p, q0, q1);
             if (p + 2 <= cnt) ldg_pair(recs + p + 2, q2, q3);
-            consider32(p, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p + 1, true, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p + 2, true, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p + 3, true, q3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32<true>(p, true, q0, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<true>(p + 1, true, q1, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<true>(p + 2, true, q2, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<true>(p + 3, true, q3, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
         }
     } else {
         const float nan = __int_as_float(0x7fc00000);
@@ -538,10 +558,10 @@ __device__ __forceinline__ void exit32(const float4 *recs, int cnt, float4 f0, f
             const float4 q1 = p1 <= cnt ? __ldg(recs + p1) : pad;
             const float4 q2 = p2 <= cnt ? __ldg(recs + p2) : pad;
             const float4 q3 = p3 <= cnt ? __ldg(recs + p3) : pad;
-            consider32(p0, true, q0, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p1, p1 <= cnt, q1, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p2, p2 <= cnt, q2, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
-            consider32(p3, p3 <= cnt, q3, rx, ry, rz, dnum, dden, Kx, Ky, Kz, c);
+            consider32<false>(p0, true, q0, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<false>(p1, p1 <= cnt, q1, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<false>(p2, p2 <= cnt, q2, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
+            consider32<false>(p3, p3 <= cnt, q3, rx, ry, rz, dnumK, dden, Kx, Ky, Kz, c);
         }
     }
     if (LPR > 1) {
@@ -877,7 +897,8 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
             const float dden = __fadd_ru(__fmul_ru(kCDen, n1m), kDivMin);
             const float dnum = __fmul_ru(n1m, __fmaf_ru(kCA, n1m, rr));
             Cand32 c;
-            exit32<LPR>(recs, cnt, f0, f1, f2, f3, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2], gmask, gl, gbase, c);
+            exit32<LPR>(recs, cnt, f0, f1, f2, f3, rx, ry, rz, __fmul_ru(dnum, kDivLo), dden, Kh[0], Kh[1], Kh[2], gmask,
+                        gl, gbase, c);
             // the wall ahead is one more candidate: s_w = t_max - t
             float sw, swl;
             two_sum(tmh_, -th, sw, swl);
@@ -897,10 +918,15 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
             float4 qw = make_float4(0.f, 0.f, 0.f, 0.f);
             if (wall_wins) {
                 upper = __fadd_ru(sw, Ew);
-            } else if (c.p1 > 0) {
-                // the winner's terms again (same operations, same values)
-                qw = __ldg(recs + c.p1);
-                w1 = plane32(qw, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
+            } else if (LPR == 1 ? c.L1 < __int_as_float(0x7f800000) : c.p1 > 0) {
+                if (LPR == 1) {
+                    w1 = Plane32{c.num1, c.den1, dnum, dden};  // kept by the exit search
+                    qw.w = __int_as_float(c.w1);
+                } else {
+                    // the winner's terms again (same operations, same values)
+                    qw = __ldg(recs + c.p1);
+                    w1 = plane32(qw, rx, ry, rz, dnum, dden, Kh[0], Kh[1], Kh[2]);
+                }
                 const float den_lo = __fsub_rd(w1.den, w1.dden);
                 const float num_hi = fmaxf(__fadd_ru(w1.num, w1.dnum), 0.0f);
                 // an upper bound needs the divisor in the division's range;
