@@ -32,6 +32,7 @@ SEED_BASE = 1310_1854
 
 CUBE_BOX = np.array([-1.0, -1.0, -1.0, 1.0, 1.0, 1.0])
 DISK_BOX = np.array([-4.0, -4.0, -0.5, 4.0, 4.0, 0.5])
+UNIT_BALL = np.array([0.0, 0.0, 0.0, 1.0])   # (cx, cy, cz, R): the ball inscribed in CUBE_BOX
 
 # exponential disk: rho = exp(-R/H_R - |z|/H_Z)
 DISK_HR = 1.0
@@ -65,6 +66,26 @@ def _dedupe_f32(p: np.ndarray, redraw, rng) -> np.ndarray:
 def uniform_points(n: int, rng, box=CUBE_BOX) -> np.ndarray:
     lo, hi = box[:3], box[3:]
     return lo + (hi - lo) * rng.random((n, 3))
+
+
+def in_ball(p: np.ndarray, sphere) -> np.ndarray:
+    """Closed ball test for generating sites inside a spherical domain:
+    ((dx dx + dy dy) + dz dz) <= R R in float64."""
+    c = np.asarray(sphere, np.float64)
+    d = np.asarray(p, np.float64) - c[:3]
+    return (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2] <= c[3] * c[3]
+
+
+def ball_points(n: int, rng, sphere=UNIT_BALL) -> np.ndarray:
+    """Uniform points in the ball (cx, cy, cz, R), by rejection from its
+    bounding cube; the points stay inside after rounding to float32."""
+    c = np.asarray(sphere, np.float64)
+    out = np.empty((0, 3))
+    while out.shape[0] < n:
+        q = c[:3] + c[3] * (2.0 * rng.random((2 * (n - out.shape[0]) + 16, 3)) - 1.0)
+        q = q[in_ball(_round_f32(q), c)]
+        out = np.concatenate([out, q])
+    return out[:n]
 
 
 def disk_points(n: int, rng, box=DISK_BOX) -> np.ndarray:
@@ -162,6 +183,21 @@ def make_clumpy_grid(M: int, seed: int, box=CUBE_BOX, n_clumps=2000):
     p = _dedupe_f32(p, lambda k, r: uniform_points(k, r, box), rng)
     rho = np.where(flag, 100.0, 1.0).astype(np.float32)
     return Grid(p, np.array(box, dtype=np.float64), rho, 1.0, f"clumpy{M}")
+
+
+def make_ball_grid(M: int, seed: int, sphere=UNIT_BALL, box=CUBE_BOX):
+    """Sites uniform in a ball inside the box (a spherical domain), density
+    falling off from the centre: rho = exp(-|r - c| / (R / 3))."""
+    rng = rng_for(seed)
+    p = _dedupe_f32(ball_points(M, rng, sphere), lambda k, r: ball_points(k, r, sphere), rng)
+    c = np.asarray(sphere, np.float64)
+    rho = np.exp(-np.linalg.norm(p - c[:3], axis=1) / (c[3] / 3.0)).astype(np.float32)
+    return Grid(p, np.array(box, dtype=np.float64), rho, 1.0, f"ball{M}")
+
+
+def ball_rays(N: int, seed: int, sphere=UNIT_BALL) -> Rays:
+    rng = rng_for(seed)
+    return Rays(ball_points(N, rng, sphere), isotropic_dirs(N, rng))
 
 
 def uniform_rays(N: int, seed: int, box=CUBE_BOX) -> Rays:

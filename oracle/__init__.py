@@ -12,6 +12,11 @@ numpy arrays and adds the plain numpy parts:
                lists with walls as -1..-6, volumes, bounding boxes.
 * ``locate``   C(r) by brute-force nearest site (Sect. 2.3).
 * ``trace``    the straight-path loop of Sect. 2.2 (Eq. 1-5).
+* a spherical domain (``sphere=(cx, cy, cz, R)``, a ball inside the box;
+  Sect. 2.2 notes the method carries over to other domain geometries):
+  cells keep the box's neighbour lists, a point is inside when its squared
+  distance to the centre is at most R^2, and the exit from the domain is the
+  sphere's, from the current point at every step (wall id -7).
 * ``tau_grad`` gradient of a loss of tau with respect to cell densities:
                tau_r = sum_c kappa rho_c l_rc is linear in rho, so
                d tau_r / d rho_c = kappa l_rc (the segment bookkeeping of
@@ -63,9 +68,9 @@ def _load():
         lib.oracle_cells.argtypes = [P, i64, P, P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, P, P, P, P, P, P, ctypes.c_int]
         lib.oracle_cells.restype = ctypes.c_int
-        lib.oracle_locate.argtypes = [P, i64, P, P, i64, P, ctypes.c_int]
+        lib.oracle_locate.argtypes = [P, i64, P, P, P, i64, P, ctypes.c_int]
         lib.oracle_locate.restype = None
-        lib.oracle_trace.argtypes = [P, i64, P, P, P, P, ctypes.c_double, P, P, i64, i64, P, P, P, P, P, P,
+        lib.oracle_trace.argtypes = [P, i64, P, P, P, P, P, ctypes.c_double, P, P, i64, i64, P, P, P, P, P, P,
                                      P, P, P, i64, ctypes.c_int, ctypes.c_double, ctypes.c_int]
         lib.oracle_trace.restype = None
         _lib = lib
@@ -84,6 +89,14 @@ def _threads(n):
 
 def _f64c(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _sphere(sphere):
+    if sphere is None:
+        return None
+    sph = _f64c(sphere).reshape(4)
+    assert sph[3] > 0, "sphere radius must be positive"
+    return sph
 
 
 def default_eps(box) -> float:
@@ -136,14 +149,16 @@ def csr(c: Cells, M: int):
     return off, idx
 
 
-def locate(sites, box, pts, threads=None) -> np.ndarray:
-    """Nearest site per point (lowest index on exact ties); -1 outside the box."""
+def locate(sites, box, pts, threads=None, sphere=None) -> np.ndarray:
+    """Nearest site per point (lowest index on exact ties); -1 outside the
+    box (or outside the ball ``sphere``)."""
     lib = _load()
     S = _f64c(sites)
     box = _f64c(box)
+    sph = _sphere(sphere)
     P = _f64c(pts).reshape(-1, 3)
     out = np.empty(P.shape[0], np.int64)
-    lib.oracle_locate(_p(S), S.shape[0], _p(box), _p(P), P.shape[0], _p(out), _threads(threads))
+    lib.oracle_locate(_p(S), S.shape[0], _p(box), _p(sph), _p(P), P.shape[0], _p(out), _threads(threads))
     return out
 
 
@@ -165,14 +180,16 @@ class Trace:
 
 
 def trace(sites, box, rho, origin, direction, off=None, idx=None, kappa=1.0, cap=1024, max_steps=1_000_000,
-          tie_rel=TIE_REL, zero_run_max=ZERO_RUN_MAX, threads=None) -> Trace:
+          tie_rel=TIE_REL, zero_run_max=ZERO_RUN_MAX, threads=None, sphere=None) -> Trace:
     """Trace rays with the paper's loop. With off/idx None every site and all
     walls are candidates (the plain definition of the exit). More than
     ``zero_run_max`` zero-length steps in a row nudge the point by
-    epsilon = 1e-12 |Dmax - Dmin| and locate it again (Sect. 2.2)."""
+    epsilon = 1e-12 |Dmax - Dmin| and locate it again (Sect. 2.2). With
+    ``sphere`` the domain is that ball and its exit ends the path."""
     lib = _load()
     S = _f64c(sites)
     box = _f64c(box)
+    sph = _sphere(sphere)
     rho = _f64c(rho)
     O = _f64c(origin).reshape(-1, 3)
     D = _f64c(direction).reshape(-1, 3)
@@ -186,7 +203,8 @@ def trace(sites, box, rho, origin, direction, off=None, idx=None, kappa=1.0, cap
     out = {k: np.zeros(N, t) for k, t in [("nseg", np.int32), ("tau", np.float64), ("length", np.float64),
                                          ("min_margin", np.float64), ("near_tie", np.int32),
                                          ("nfallback", np.int32), ("status", np.int32)]}
-    lib.oracle_trace(_p(S), S.shape[0], _p(box), _p(off), _p(idx), _p(rho), float(kappa), _p(O), _p(D), N, cap,
+    lib.oracle_trace(_p(S), S.shape[0], _p(box), _p(sph), _p(off), _p(idx), _p(rho), float(kappa), _p(O), _p(D), N,
+                     cap,
                      _p(seg_cell), _p(seg_len), _p(out["nseg"]), _p(out["tau"]), _p(out["length"]),
                      _p(out["min_margin"]), _p(out["near_tie"]), _p(out["nfallback"]), _p(out["status"]),
                      int(max_steps), int(zero_run_max), float(tie_rel), _threads(threads))
@@ -206,15 +224,37 @@ def tau_grad(tr: Trace, M: int, dL_dtau, kappa=1.0) -> np.ndarray:
     return np.bincount(cells_, weights=w, minlength=M)[:M] if N else np.zeros(M)
 
 
-def enter_points(box, origin, direction):
+def enter_points(box, origin, direction, sphere=None):
     """For rays that start outside the closed box, the first point of the ray
     r0 + s k (s >= 0) inside it: the largest of the per-axis entry parameters
     of the slabs, if it does not exceed the smallest exit parameter. Rays
-    inside are returned unchanged; rays that miss keep their origin."""
+    inside are returned unchanged; rays that miss keep their origin.
+
+    With ``sphere`` (a ball inside the box): a ray outside the ball that
+    meets it ahead starts epsilon = 1e-12 |Dmax - Dmin| past its entry point,
+    the smaller root of |r0 + s k - c|^2 = R^2 (written as q / (sqrt(b^2 - q)
+    - b), b = k.(r0 - c) < 0, q = |r0 - c|^2 - R^2 > 0, so that no digits
+    cancel), where it is inside the ball unless it only grazes it."""
     box = np.asarray(box, np.float64)
     O = np.array(origin, np.float64).reshape(-1, 3)
     D = np.asarray(direction, np.float64).reshape(-1, 3)
     out = O.copy()
+    if sphere is not None:
+        sph = _sphere(sphere)
+        eps = default_eps(box)
+        for i in range(O.shape[0]):
+            r, k = O[i], D[i]
+            o = r - sph[:3]
+            q = ((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]) - sph[3] * sph[3]
+            if q <= 0.0:
+                continue
+            b = (k[0] * o[0] + k[1] * o[1]) + k[2] * o[2]
+            disc = b * b - q
+            if not (b < 0.0 and disc >= 0.0):
+                continue
+            t = q / (np.sqrt(disc) - b) + eps
+            out[i] = r + t * k
+        return out
     for i in range(O.shape[0]):
         r, k = O[i], D[i]
         if np.all((r >= box[:3]) & (r <= box[3:])):

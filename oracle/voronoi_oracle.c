@@ -25,6 +25,15 @@
  *                  -1..-6), the cell volume and bounding box (Sect. 2.3).
  *   oracle_locate  C(r): nearest site by brute force over all sites,
  *                  negative index outside the domain (Sect. 2.3 steps 1, 4).
+ *   Domains: the box, or a sphere inside the box (Sect. 2.2 notes that the
+ *                  method carries over to other domain geometries). In a
+ *                  spherical domain the cells keep the lists of the box's
+ *                  clipping (a face outside the sphere is never reached, as
+ *                  the path leaves the domain first), a point is inside when
+ *                  its squared distance to the centre is at most R^2, and the
+ *                  domain exit is the sphere's: the larger root s of
+ *                  |r + s k - c|^2 = R^2 from the current point, in place of
+ *                  the box walls' Eq. 5, with the wall id -7.
  *   oracle_trace   the straight-path loop of Sect. 2.2 with the exit-point
  *                  algorithm (steps 1-3), bisector intersection Eq. 1-4,
  *                  wall intersection Eq. 5 and the epsilon nudge when no exit
@@ -586,10 +595,40 @@ int oracle_cells(const double *sites, int64_t M, const double *box, const int64_
 /* Nearest site to r (lowest index on exact ties), -1 outside the closed box.
  * If mu is given it receives the relative gap (d2 - d1) / d2 between the
  * nearest and second-nearest site distances (+inf with one site). */
-static int64_t locate_mu(const double *S, int64_t M, const double *box, const double *r, double *mu)
+/* Inside the closed domain: the box, and the ball when sph (cx, cy, cz, R)
+ * is given. */
+static int inside_domain(const double *box, const double *sph, const double *r)
 {
     for (int c = 0; c < 3; c++)
-        if (!(r[c] >= box[c] && r[c] <= box[3 + c])) return -1;
+        if (!(r[c] >= box[c] && r[c] <= box[3 + c])) return 0;
+    if (sph) {
+        double dx = r[0] - sph[0], dy = r[1] - sph[1], dz = r[2] - sph[2];
+        if (!((dx * dx + dy * dy) + dz * dz <= sph[3] * sph[3])) return 0;
+    }
+    return 1;
+}
+
+/* Exit of r + s k (s >= 0) from the ball (cx, cy, cz, R): with o = r - c,
+ * b = k.o and q = o.o - R^2, the larger root of s^2 + 2 b s + q = 0 (k a unit
+ * vector), -b + sqrt(b^2 - q), written as -q / (b + sqrt(b^2 - q)) when
+ * b > 0 so that no digits cancel. */
+static double sphere_exit(const double *sph, const double *r, const double *k)
+{
+    double o[3];
+    for (int c = 0; c < 3; c++) o[c] = r[c] - sph[c];
+    double b = (k[0] * o[0] + k[1] * o[1]) + k[2] * o[2];
+    double q = ((o[0] * o[0] + o[1] * o[1]) + o[2] * o[2]) - sph[3] * sph[3];
+    double disc = b * b - q;
+    if (disc < 0.0) disc = 0.0;
+    double sq = sqrt(disc);
+    double s = b > 0.0 ? -q / (b + sq) : sq - b;
+    return s < 0.0 ? 0.0 : s;
+}
+
+static int64_t locate_mu(const double *S, int64_t M, const double *box, const double *sph, const double *r,
+                         double *mu)
+{
+    if (!inside_domain(box, sph, r)) return -1;
     int64_t best = -1;
     double bd = INFINITY, sd = INFINITY;
     for (int64_t j = 0; j < M; j++) {
@@ -602,26 +641,27 @@ static int64_t locate_mu(const double *S, int64_t M, const double *box, const do
     return best;
 }
 
-static int64_t locate1(const double *S, int64_t M, const double *box, const double *r)
+static int64_t locate1(const double *S, int64_t M, const double *box, const double *sph, const double *r)
 {
-    return locate_mu(S, M, box, r, NULL);
+    return locate_mu(S, M, box, sph, r, NULL);
 }
 
-typedef struct { const double *S; int64_t M; const double *box; const double *pts; int64_t *out; } loc_ctx;
+typedef struct { const double *S; int64_t M; const double *box, *sph; const double *pts; int64_t *out; } loc_ctx;
 
 static void loc_item(void *vctx, int64_t i, void *scratch)
 {
     (void)scratch;
     loc_ctx *X = (loc_ctx *)vctx;
-    X->out[i] = locate1(X->S, X->M, X->box, X->pts + 3 * i);
+    X->out[i] = locate1(X->S, X->M, X->box, X->sph, X->pts + 3 * i);
 }
 
 /* C(r) for N points: index of the nearest site (lowest index on exact ties),
- * -1 for points outside the closed box. */
-void oracle_locate(const double *sites, int64_t M, const double *box, const double *pts, int64_t N, int64_t *out,
-                   int nthreads)
+ * -1 for points outside the closed domain (the box, and the ball sphere =
+ * (cx, cy, cz, R) unless NULL). */
+void oracle_locate(const double *sites, int64_t M, const double *box, const double *sphere, const double *pts,
+                   int64_t N, int64_t *out, int nthreads)
 {
-    loc_ctx X = {sites, M, box, pts, out};
+    loc_ctx X = {sites, M, box, sphere, pts, out};
     or_parallel_for(N, loc_item, &X, 0, nthreads);
 }
 
@@ -635,6 +675,7 @@ typedef struct {
     const double *S;
     int64_t M;
     const double *box;
+    const double *sph;  /* NULL: the box is the domain; else (cx, cy, cz, R) */
     const int64_t *off;
     const int32_t *idx; /* NULL: every site and all walls are candidates */
     const double *rho;
@@ -651,8 +692,9 @@ typedef struct {
     double eps_nudge, tie_rel;
 } trace_ctx;
 
-/* One candidate plane: s from Eq. 4 (bisector) or Eq. 5 (wall).
- * Returns 0 if the plane is not a candidate (n.k <= 0). */
+/* One candidate plane: s from Eq. 4 (bisector) or Eq. 5 (wall), or the
+ * sphere's exit (id -7). Returns 0 if it is not a candidate (n.k <= 0; the
+ * box walls of a spherical domain). */
 static int plane_s(const trace_ctx *X, int64_t m, int64_t j, const double *r, const double *k, double *s_out,
                    double *num_out, double *nlen_out)
 {
@@ -670,7 +712,14 @@ static int plane_s(const trace_ctx *X, int64_t m, int64_t j, const double *r, co
         if (num < 0.0) num = 0.0;                                   /* R3 */
         *s_out = num / den;
         return 1;
+    } else if (j == -7) {
+        double s = sphere_exit(X->sph, r, k);
+        *num_out = s;
+        *nlen_out = 1.0;
+        *s_out = s;
+        return 1;
     } else {
+        if (X->sph) return 0;
         int w = (int)(-j - 1), axis = w / 2, hi = w % 2;
         double kc = k[axis];
         if (hi ? !(kc > 0.0) : !(kc < 0.0)) return 0;             /* n.k > 0 */
@@ -692,7 +741,7 @@ static void trace_item(void *vctx, int64_t i, void *scratch)
     const double *k = X->dir + 3 * i;
     double r[3] = {X->org[3 * i], X->org[3 * i + 1], X->org[3 * i + 2]};
     double mu0;
-    int64_t m = locate_mu(X->S, X->M, X->box, r, &mu0);
+    int64_t m = locate_mu(X->S, X->M, X->box, X->sph, r, &mu0);
     double tau = 0.0, len = 0.0, mmin = INFINITY;
     int32_t ns = 0, nfb = 0, tie = 0, st = OR_OK;
     /* a start point (nearly) equidistant from two sites is a near tie too */
@@ -708,10 +757,14 @@ static void trace_item(void *vctx, int64_t i, void *scratch)
         double best = INFINITY, second = INFINITY, best_num = 0.0, best_nlen = 1.0;
         int64_t best_id = INT64_MAX;
         double hmin2 = INFINITY;
-        int64_t nc = X->idx ? (X->off[m + 1] - X->off[m]) : (X->M + 6);
+        /* the cell's list (or every site and the six walls), then the
+           sphere of a spherical domain */
+        int64_t nl = X->idx ? (X->off[m + 1] - X->off[m]) : (X->M + 6);
+        int64_t nc = nl + (X->sph ? 1 : 0);
         for (int64_t q = 0; q < nc; q++) {
             int64_t j;
-            if (X->idx) j = X->idx[X->off[m] + q];
+            if (q == nl) j = -7;
+            else if (X->idx) j = X->idx[X->off[m] + q];
             else j = q < X->M ? q : -(q - X->M + 1);
             if (j == m) continue;
             if (j >= 0) {
@@ -736,7 +789,7 @@ static void trace_item(void *vctx, int64_t i, void *scratch)
             /* no exit found: nudge over epsilon and relocate (Sect. 2.2) */
             nfb++;
             for (int c = 0; c < 3; c++) r[c] = r[c] + X->eps_nudge * k[c];
-            m = locate1(X->S, X->M, X->box, r);
+            m = locate1(X->S, X->M, X->box, X->sph, r);
             zrun = 0;
             if (m < 0) break;
             continue;
@@ -766,7 +819,7 @@ static void trace_item(void *vctx, int64_t i, void *scratch)
         if (zrun > X->zmax) {
             nfb++;
             for (int c = 0; c < 3; c++) r[c] = r[c] + X->eps_nudge * k[c];
-            m = locate1(X->S, X->M, X->box, r);
+            m = locate1(X->S, X->M, X->box, X->sph, r);
             zrun = 0;
             if (m < 0) break;
         }
@@ -783,12 +836,14 @@ out:
 
 /* Straight paths for N rays (origin, unit direction). With idx == NULL the
  * candidates are all other sites plus the six walls; otherwise the CSR
- * neighbour lists off/idx (walls as -1..-6). Per ray: segments (cell, length)
+ * neighbour lists off/idx (walls as -1..-6). With sphere = (cx, cy, cz, R)
+ * the domain is that ball (inside the box): its exit replaces the walls. Per ray: segments (cell, length)
  * up to cap, the count, tau = sum kappa rho l, the summed length, the
  * smallest decision margin, a near-tie flag, fallback count, status. More
  * than zmax zero-length steps in a row nudge the point by epsilon and locate
  * it again, as a decision without any exit does (Sect. 2.2). */
-void oracle_trace(const double *sites, int64_t M, const double *box, const int64_t *off, const int32_t *idx,
+void oracle_trace(const double *sites, int64_t M, const double *box, const double *sphere, const int64_t *off,
+                  const int32_t *idx,
                   const double *rho, double kappa, const double *org, const double *dir, int64_t N, int64_t cap,
                   int32_t *seg_cell, double *seg_len, int32_t *nseg, double *tau, double *length,
                   double *min_margin, int32_t *near_tie, int32_t *nfallback, int32_t *status, int64_t max_steps,
@@ -799,6 +854,7 @@ void oracle_trace(const double *sites, int64_t M, const double *box, const int64
     X.S = sites;
     X.M = M;
     X.box = box;
+    X.sph = sphere;
     X.off = off;
     X.idx = idx;
     X.rho = rho;

@@ -552,3 +552,148 @@ def test_enter_points_closed_form():
     for i in np.nonzero(missed)[0][:100]:
         p = O[i] + ts[:, None] * D[i]
         assert not np.any(np.all(np.abs(p) <= 1 - 1e-9, axis=1))
+
+
+# --------------------------------------------------------------------------
+# a spherical domain (Sect. 2.2: the method carries over to other domain
+# geometries): cells keep the box's lists, the path ends on the sphere
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", _load("sphere_examples.json")["cases"], ids=lambda c: c["name"])
+@pytest.mark.parametrize("mode", ["neighbours", "all_sites"])
+def test_sphere_examples(case, mode):
+    S = np.array(case["sites"], np.float64)
+    box = np.array(case["box"], np.float64)
+    rho = np.array(case["rho"], np.float64)
+    kw = {}
+    if mode == "neighbours":
+        _, off, idx = _full(S, box)
+        kw = dict(off=off, idx=idx)
+    tr = oracle.trace(S, box, rho, np.array([case["origin"]], np.float64), np.array([case["dir"]], np.float64),
+                      sphere=case["sphere"], **kw)
+    assert oracle.STATUS[int(tr.status[0])] == case.get("status", "ok")
+    cells, lens = tr.segments(0)
+    assert [int(c) for c in cells] == [e[0] for e in case["segments"]]
+    np.testing.assert_allclose(lens, [e[1] for e in case["segments"]], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr.tau[0], case["tau"], rtol=1e-12, atol=0)
+
+
+def test_sphere_locate_example():
+    L = _load("sphere_examples.json")["locate"]
+    got = oracle.locate(np.array(L["sites"], np.float64), L["box"], np.array(L["points"], np.float64),
+                        sphere=L["sphere"])
+    assert [int(x) for x in got] == L["cells"]
+
+
+def test_sphere_enter_example():
+    E = _load("sphere_examples.json")["enter"]
+    S = np.array(E["sites"], np.float64)
+    O = np.array([E["origin"]], np.float64)
+    D = np.array([E["dir"]], np.float64)
+    P = oracle.enter_points(E["box"], O, D, sphere=E["sphere"])
+    np.testing.assert_allclose(P[0], E["entry"], rtol=0, atol=1e-15)
+    _, off, idx = _full(S, np.array(E["box"], np.float64))
+    tr = oracle.trace(S, E["box"], np.array(E["rho"]), P, D, off=off, idx=idx, sphere=E["sphere"])
+    cells, lens = tr.segments(0)
+    assert [int(c) for c in cells] == [e[0] for e in E["segments"]]
+    np.testing.assert_allclose(lens, [e[1] for e in E["segments"]], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(tr.tau[0], E["tau"], rtol=0, atol=4e-15)
+
+
+@pytest.fixture(scope="module")
+def ball300():
+    g = gen.make_ball_grid(300, 41)
+    c, off, idx = _full(g.sites, g.box)
+    rays = gen.ball_rays(500, 42)
+    tr = oracle.trace(g.sites, g.box, g.rho, rays.origin, rays.dir, off=off, idx=idx, sphere=gen.UNIT_BALL)
+    return g, off, idx, rays, tr
+
+
+def test_sphere_paths_end_on_the_sphere(ball300):
+    """Every path ends on the sphere: |r0 + L k - c| = R, with L the summed
+    length and the end point's distance taken by numpy's norm; and L is the
+    positive root of s^2 + 2 b s + q (numpy.roots)."""
+    g, off, idx, rays, tr = ball300
+    assert np.all(tr.status == 0)
+    end = rays.origin + tr.length[:, None] * rays.dir
+    np.testing.assert_allclose(np.linalg.norm(end, axis=1), 1.0, rtol=0, atol=1e-13)
+    for i in range(0, 500, 25):
+        o, k = rays.origin[i], rays.dir[i]
+        roots = np.roots([k @ k, 2 * (k @ o), o @ o - 1.0])
+        np.testing.assert_allclose(tr.length[i], roots.real.max(), rtol=1e-12)
+
+
+def test_sphere_neighbour_exit_equals_all_sites_exit(ball300):
+    g, off, idx, rays, tr = ball300
+    tr2 = oracle.trace(g.sites, g.box, g.rho, rays.origin[:200], rays.dir[:200], sphere=gen.UNIT_BALL)
+    for i in range(200):
+        a, b = tr.segments(i), tr2.segments(i)
+        assert np.array_equal(a[0], b[0])
+        np.testing.assert_allclose(a[1], b[1], rtol=1e-12, atol=1e-15)
+
+
+def test_sphere_uniform_density_closed_form(ball300):
+    g, off, idx, rays, tr = ball300
+    t = oracle.trace(g.sites, g.box, np.full(len(g.sites), 2.5), rays.origin, rays.dir, off=off, idx=idx,
+                     kappa=0.8, sphere=gen.UNIT_BALL)
+    np.testing.assert_allclose(t.tau, 0.8 * 2.5 * tr.length, rtol=1e-13)
+
+
+def test_sphere_dense_sampling_reproduces_cell_sequence():
+    """Brute force: points sampled along the path, inside the ball, owned by
+    their nearest site, give the oracle's cell sequence; just past the end the
+    path is outside the ball."""
+    g = gen.make_ball_grid(120, 43)
+    _, off, idx = _full(g.sites, g.box)
+    rays = gen.ball_rays(60, 44)
+    tr = oracle.trace(g.sites, g.box, g.rho, rays.origin, rays.dir, off=off, idx=idx, sphere=gen.UNIT_BALL)
+    checked = 0
+    for i in range(60):
+        cells, lens = tr.segments(i)
+        if lens.min() < 2e-3:
+            continue
+        ts = np.arange(0.0, tr.length[i], 2.5e-4) + 1.25e-4
+        ts = ts[ts < tr.length[i]]
+        P = rays.origin[i] + ts[:, None] * rays.dir[i]
+        assert np.all(np.linalg.norm(P, axis=1) < 1.0 + 1e-12)
+        own = nearest_site(g.sites, P)
+        runs = own[np.concatenate([[True], own[1:] != own[:-1]])]
+        assert [int(x) for x in runs] == [int(x) for x in cells]
+        beyond = rays.origin[i] + (tr.length[i] + 1e-9) * rays.dir[i]
+        assert np.linalg.norm(beyond) > 1.0
+        checked += 1
+    assert checked > 40
+
+
+def test_sphere_locate_matches_brute_force():
+    g = gen.make_ball_grid(200, 45)
+    rng = gen.rng_for(46)
+    P = gen.uniform_points(3000, rng, g.box)
+    got = oracle.locate(g.sites, g.box, P, sphere=gen.UNIT_BALL)
+    inside = np.linalg.norm(P, axis=1) <= 1.0
+    assert (~inside).sum() > 1000 and inside.sum() > 1000
+    assert np.all(got[~inside] == -1)
+    np.testing.assert_array_equal(got[inside], nearest_site(g.sites, P[inside]))
+
+
+def test_sphere_enter_points():
+    """Rays from outside the ball: the start lies epsilon past the sphere
+    along k (so |E - c| is R to within epsilon), and a ray that misses keeps
+    its origin (dense sampling never comes within the ball)."""
+    rng = gen.rng_for(47)
+    box = np.array([-2.0, -2, -2, 2, 2, 2])
+    O = gen.uniform_points(2000, rng, box)
+    D = gen.isotropic_dirs(2000, rng)
+    E = oracle.enter_points(box, O, D, sphere=gen.UNIT_BALL)
+    out = np.linalg.norm(O, axis=1) > 1.0
+    moved = out & np.any(E != O, axis=1)
+    assert moved.sum() > 100
+    eps = oracle.default_eps(box)
+    rad = np.linalg.norm(E[moved], axis=1)
+    assert np.all(rad < 1.0) and np.all(rad > 1.0 - 1.01 * eps)
+    back = E[moved] - 1.5 * eps * D[moved]
+    assert np.all(np.linalg.norm(back, axis=1) > 1.0 - 1e-15)
+    ts = np.linspace(0, 8, 8001)
+    for i in np.nonzero(out & ~moved)[0][:100]:
+        p = O[i] + ts[:, None] * D[i]
+        assert not np.any(np.linalg.norm(p, axis=1) < 1.0 - 1e-3)
