@@ -105,7 +105,30 @@ typedef struct {
                                   after every zero-length step. Epsilon is
                                   1e-12 |Dmax - Dmin| in the float64 form and
                                   1e-6 |Dmax - Dmin| in the float32 form. */
+    int32_t domain;            /* VGRID_DOMAIN_BOX (default): the domain is bbox.
+                                  VGRID_DOMAIN_SPHERE: the ball `sphere` inside
+                                  bbox (Sect. 2.2: the method carries over to
+                                  other domain geometries). Every site must lie
+                                  in the closed ball ((dx dx + dy dy) + dz dz <=
+                                  R R in float64, else VGRID_ERR_OUTSIDE). The
+                                  cells keep the neighbour lists, volumes and
+                                  bounding boxes of bbox's clipping (a face that
+                                  lies outside the ball is never reached: the
+                                  path leaves the domain first); a point outside
+                                  the ball is outside the domain, and a path ends
+                                  where it leaves the ball: the larger root s of
+                                  |r + s k - c|^2 = R^2 (wall id -7), in float64
+                                  from the current point in the float64 form, once
+                                  per ray from the origin in the float32 form.
+                                  With VGRID_ENTER a ray outside the ball that
+                                  meets it ahead starts 1e-12 |Dmax - Dmin| past
+                                  its entry point. */
+    double sphere[4];          /* VGRID_DOMAIN_SPHERE: centre x, y, z and radius
+                                  R > 0; the ball must lie in bbox */
 } vgrid_opts;
+
+/* domains (vgrid_opts.domain) */
+enum { VGRID_DOMAIN_BOX = 0, VGRID_DOMAIN_SPHERE = 1 };
 
 typedef struct {
     int64_t rays;          /* rays traced */

@@ -65,10 +65,14 @@ class VoronoiGrid:
     sites: (M, 3) array of float32-representable positions inside ``box``
     (xmin, ymin, zmin, xmax, ymax, zmax). The neighbour lists, cell volumes,
     bounding boxes and block lists are built on the host by the library.
+    ``sphere=(cx, cy, cz, R)`` makes the domain that ball (inside ``box``,
+    every site inside it): paths end on the sphere, points outside it are
+    outside the domain.
     """
 
     def __init__(self, sites, box, *, round_sites=False, reorder=True, blocks_per_site=8.0,
-                 max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False, zero_run_max=4):
+                 max_steps=100_000, threads=0, device=None, host_only=False, gpu_build=False, zero_run_max=4,
+                 sphere=None):
         lib = load()
         S = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 3))
         B = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(6))
@@ -82,6 +86,10 @@ class VoronoiGrid:
         opts.host_only = int(bool(host_only))
         opts.gpu_build = int(bool(gpu_build))
         opts.zero_run_max = int(zero_run_max)
+        if sphere is not None:
+            opts.domain = _lib.DOMAIN_SPHERE
+            for c, v in enumerate(np.asarray(sphere, np.float64).reshape(4)):
+                opts.sphere[c] = float(v)
         h = ctypes.c_void_p()
         args = (S.ctypes.data_as(ctypes.c_void_p), S.shape[0], B.ctypes.data_as(ctypes.c_void_p),
                 ctypes.byref(opts), ctypes.byref(h))
@@ -96,6 +104,7 @@ class VoronoiGrid:
         self._h = h
         self.M = S.shape[0]
         self.box = B.copy()
+        self.sphere = None if sphere is None else np.asarray(sphere, np.float64).reshape(4).copy()
         self.kappa = 1.0
         self._seg_per_ray = None  # segments per ray of the last segment-list call
 

@@ -34,6 +34,7 @@ FP32_RECHECK = 1
 TAU = 0
 SEGMENTS = 1
 ENTER = 0x100
+DOMAIN_BOX, DOMAIN_SPHERE = 0, 1
 
 RAY_OK, RAY_OUTSIDE, RAY_STEP_LIMIT, RAY_BAD_DIR = 0, 1, 2, 3
 
@@ -41,7 +42,8 @@ RAY_OK, RAY_OUTSIDE, RAY_STEP_LIMIT, RAY_BAD_DIR = 0, 1, 2, 3
 class Opts(ctypes.Structure):
     _fields_ = [("threads", c_int32), ("round_sites", c_int32), ("reorder", c_int32),
                 ("blocks_per_site", c_double), ("max_steps", c_int64), ("host_only", c_int32),
-                ("gpu_build", c_int32), ("zero_run_max", c_int32)]
+                ("gpu_build", c_int32), ("zero_run_max", c_int32), ("domain", c_int32),
+                ("sphere", c_double * 4)]
 
 
 class Stats(ctypes.Structure):

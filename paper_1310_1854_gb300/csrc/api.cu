@@ -184,6 +184,8 @@ void vgrid_default_opts(vgrid_opts *o) {
     o->host_only = 0;
     o->gpu_build = 0;
     o->zero_run_max = 4;
+    o->domain = VGRID_DOMAIN_BOX;
+    for (int c = 0; c < 4; c++) o->sphere[c] = 0.0;
 }
 
 static void free_events(vgrid_t *g) {
@@ -259,6 +261,15 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (!(o.blocks_per_site > 0)) o.blocks_per_site = 8.0;
     if (o.max_steps <= 0) o.max_steps = 100000;
     if (o.zero_run_max < 0) return fail(VGRID_ERR_ARG, "zero_run_max must be >= 0");
+    if (o.domain != VGRID_DOMAIN_BOX && o.domain != VGRID_DOMAIN_SPHERE)
+        return fail(VGRID_ERR_ARG, "domain must be VGRID_DOMAIN_BOX or VGRID_DOMAIN_SPHERE");
+    if (o.domain == VGRID_DOMAIN_SPHERE) {
+        const double R = o.sphere[3];
+        if (!(R > 0) || !std::isfinite(R)) return fail(VGRID_ERR_ARG, "sphere radius must be positive and finite");
+        for (int c = 0; c < 3; c++)
+            if (!std::isfinite(o.sphere[c]) || !(o.sphere[c] - R >= bbox[c]) || !(o.sphere[c] + R <= bbox[3 + c]))
+                return fail(VGRID_ERR_ARG, "the sphere must lie inside bbox");
+    }
     const auto t0 = std::chrono::steady_clock::now();
 
     // sites as float32 values (the device stores float4)
@@ -275,6 +286,12 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         for (int c = 0; c < 3; c++)
             if (!(S[3 * i + c] >= bbox[c] && S[3 * i + c] <= bbox[3 + c]))
                 return fail(VGRID_ERR_OUTSIDE, "site " + std::to_string(i) + " lies outside the box");
+    if (o.domain == VGRID_DOMAIN_SPHERE)
+        for (int64_t i = 0; i < M; i++) {
+            const double dx = S[3 * i] - o.sphere[0], dy = S[3 * i + 1] - o.sphere[1], dz = S[3 * i + 2] - o.sphere[2];
+            if (!((dx * dx + dy * dy) + dz * dz <= o.sphere[3] * o.sphere[3]))
+                return fail(VGRID_ERR_OUTSIDE, "site " + std::to_string(i) + " lies outside the sphere");
+        }
     // duplicates: coinciding sites share a Morton code, so with the Morton
     // order they sit in one run of equal codes (runs are a few sites long);
     // without it, a lexicographic sort puts them next to each other
@@ -592,6 +609,9 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     hd.scale = dmax + diag;
     hd.max_steps = o.max_steps;
     hd.zmax = o.zero_run_max;
+    hd.domain = o.domain;
+    hd.pad1 = 0;
+    for (int c = 0; c < 4; c++) hd.sph[c] = o.domain == VGRID_DOMAIN_SPHERE ? o.sphere[c] : 0.0;
     if (e == cudaSuccess) e = cudaMemcpy(g->d_desc, &hd, sizeof(GridDev), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         free_grid(g);

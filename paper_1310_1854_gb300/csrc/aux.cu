@@ -105,10 +105,16 @@ __global__ void __launch_bounds__(256, 5) locate_kernel(const GridDev *grids, co
         p.cell = m >= 0 && !fp64 ? __float_as_int(__ldg(&gp->site[m]).w) : m;
         // distance to the wall ahead (Eq. 5 for the walls the ray faces), as
         // a float pair: q1 = n/k rounded, the exact remainder n - q1 k by
-        // fma, then q2 = remainder / k (relative error a few 2^-48)
+        // fma, then q2 = remainder / k (relative error a few 2^-48); in a
+        // spherical domain the sphere's exit from the origin in float64,
+        // split into a float pair
         float th = 3.0e38f, tl = 0.0f;
         int wid = -1;
-        for (int c = 0; c < 3; c++) {
+        if (gp->domain == VGRID_DOMAIN_SPHERE) {
+            split_pair(sphere_exit64(gp, P.x, k), th, tl);
+            wid = kSphereWall;
+        }
+        for (int c = 0; c < 3 && gp->domain != VGRID_DOMAIN_SPHERE; c++) {
             const uint64_t kb = dbits(k[c]);
             if ((kb << 1) == 0) continue;  // k_c = +-0
             const bool up = (kb >> 63) == 0;
@@ -282,6 +288,10 @@ cudaError_t launch_permute_density(const float *rho_caller, const int32_t *perm,
 // inside every slab; a ray with t_in <= t_out and t_out >= 0 starts at
 // r0 + max(t_in, 0) k, clamped into the closed box against rounding. Rays
 // inside are copied unchanged, rays that miss keep their outside origin.
+// In a spherical domain a ray outside the ball (q = o.o - R^2 > 0, o = r0 -
+// c) that meets it ahead (b = k.o < 0, b^2 - q >= 0) starts epsilon past the
+// smaller root, q / (sqrt(b^2 - q) - b) + epsilon (no digits cancel), every
+// operation rounded to nearest in this order.
 __global__ void enter_kernel(const double *__restrict__ origin, const double *__restrict__ dir, int64_t N,
                              const GridDev *gp, double *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -292,7 +302,21 @@ __global__ void enter_kernel(const double *__restrict__ origin, const double *__
             k[c] = dir[3 * i + c];
             in = in && r[c] >= gp->lo[c] && r[c] <= gp->hi[c];
         }
-        if (!in) {
+        if (gp->domain == VGRID_DOMAIN_SPHERE) {
+            double o[3];
+            for (int c = 0; c < 3; c++) o[c] = __dsub_rn(r[c], gp->sph[c]);
+            const double q = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(o[0], o[0]), __dmul_rn(o[1], o[1])),
+                                                 __dmul_rn(o[2], o[2])),
+                                       __dmul_rn(gp->sph[3], gp->sph[3]));
+            if (q > 0.0) {
+                const double b = __dadd_rn(__dadd_rn(__dmul_rn(k[0], o[0]), __dmul_rn(k[1], o[1])), __dmul_rn(k[2], o[2]));
+                const double disc = __dsub_rn(__dmul_rn(b, b), q);
+                if (b < 0.0 && disc >= 0.0) {
+                    const double t = __dadd_rn(__ddiv_rn(q, __dsub_rn(__dsqrt_rn(disc), b)), gp->eps64);
+                    for (int c = 0; c < 3; c++) r[c] = __dadd_rn(r[c], __dmul_rn(t, k[c]));
+                }
+            }
+        } else if (!in) {
             double t_in = -1e300, t_out = 1e300;
             bool miss = false;
             for (int c = 0; c < 3; c++) {

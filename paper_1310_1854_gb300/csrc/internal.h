@@ -97,6 +97,9 @@ struct GridDev {
     double eps32;             // epsilon nudge, float32 path
     double scale;             // max |coordinate| of the box + diagonal
     int64_t max_steps;
+    int32_t domain;           // VGRID_DOMAIN_BOX or VGRID_DOMAIN_SPHERE
+    int32_t pad1;
+    double sph[4];            // spherical domain: centre and radius
 };
 
 // Per-ray record written by the start-cell kernel (full warps, where the

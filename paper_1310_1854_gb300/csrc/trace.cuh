@@ -41,6 +41,7 @@
 #include "fsplit.h"
 #include "internal.h"
 #include "kernels.h"
+#include "vgrid.h"
 
 namespace vg {
 
@@ -172,10 +173,38 @@ __device__ __forceinline__ bool better64(const Hot &h, double n, double d, int w
     return key64(h, w) < key64(h, bw);
 }
 
+// A spherical domain (the ball sph = centre, R inside the box): a point is
+// inside when ((dx dx + dy dy) + dz dz) <= R R, and the path leaves it at the
+// larger root s of s^2 + 2 b s + q = 0, b = k.o, q = o.o - R^2, o = r - c (k a
+// unit vector): -q / (b + sqrt(b^2 - q)) for b > 0, so that no digits cancel,
+// else sqrt(b^2 - q) - b; every operation rounded to nearest, in this order.
+constexpr int kSphereWall = -7;         // its wall id
+constexpr int kSphereWin = 0x40000000;  // exit64's result when the sphere is the exit
+
+__device__ __forceinline__ bool in_sphere(const GridDev *gp, const double *x) {
+    const double dx = __dsub_rn(x[0], gp->sph[0]), dy = __dsub_rn(x[1], gp->sph[1]), dz = __dsub_rn(x[2], gp->sph[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 <= __dmul_rn(gp->sph[3], gp->sph[3]);
+}
+
+__device__ __forceinline__ double sphere_exit64(const GridDev *gp, const double *r, const double *k) {
+    double o[3];
+    for (int c = 0; c < 3; c++) o[c] = __dsub_rn(r[c], gp->sph[c]);
+    const double b = __dadd_rn(__dadd_rn(__dmul_rn(k[0], o[0]), __dmul_rn(k[1], o[1])), __dmul_rn(k[2], o[2]));
+    const double q = __dsub_rn(__dadd_rn(__dadd_rn(__dmul_rn(o[0], o[0]), __dmul_rn(o[1], o[1])), __dmul_rn(o[2], o[2])),
+                               __dmul_rn(gp->sph[3], gp->sph[3]));
+    double disc = __dsub_rn(__dmul_rn(b, b), q);
+    if (disc < 0.0) disc = 0.0;
+    const double sq = __dsqrt_rn(disc);
+    const double s = b > 0.0 ? __ddiv_rn(-q, __dadd_rn(b, sq)) : __dsub_rn(sq, b);
+    return s < 0.0 ? 0.0 : s;
+}
+
 // A wall (Eq. 5) as the fraction num / den; false unless the ray faces it.
+// In a spherical domain the box's walls are not part of the boundary.
 __device__ __forceinline__ bool wall64(const GridDev *gp, int w, const double *r, const double *k, double &num,
                                       double &den) {
-    if (w < -6) return false;
+    if (w < -6 || gp->domain == VGRID_DOMAIN_SPHERE) return false;
     const int wi = -w - 1, axis = wi >> 1, hi = wi & 1;
     const double kc = k[axis];
     if (hi ? !(kc > 0.0) : !(kc < 0.0)) return false;
@@ -236,7 +265,8 @@ __device__ __forceinline__ bool plane64x(const GridDev *gp, const float4 *crec, 
 
 // Exit of the cell whose records are blk[1..cnt] for the group: the
 // lexicographically smallest (s, id); returns the winner's record position
-// (1-based) or 0 if there is no candidate, and its s in bs.
+// (1-based), kSphereWin if the exit is a spherical domain's boundary, or 0 if
+// there is no candidate, and its s in bs.
 // The float64 form's pre-test: false only for a record whose plane
 // certainly faces away (n.k <= 0), so that the float64 test can skip it; the
 // results are the same bits. The stored n's high words are truncated to
@@ -317,6 +347,16 @@ __device__ __forceinline__ int exit64(const Hot &h, const GridDev *gp, const flo
             }
         }
     }
+    // a spherical domain: its exit from r is one more candidate (s / 1)
+    if (gp->domain == VGRID_DOMAIN_SPHERE) {
+        const double s = sphere_exit64(gp, r, k);
+        if (better64<FRAC>(h, s, 1.0, kSphereWall, bn, bd, bw, bp != 0)) {
+            bn = s;
+            bd = 1.0;
+            bp = kSphereWin;
+            bw = kSphereWall;
+        }
+    }
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) {
         const double on = __shfl_xor_sync(gmask, bn, o);
@@ -361,7 +401,7 @@ __device__ __forceinline__ bool inside(const GridDev *gp, const LocPt &P) {
         const int64_t k = dkey(P.x[c]);
         in = in && !disnan(P.x[c]) && k >= gp->lokey[c] && k <= gp->hikey[c];
     }
-    return in;
+    return in && (gp->domain != VGRID_DOMAIN_SPHERE || in_sphere(gp, P.x));
 }
 
 // Block of the point, from its float pairs: (x - lo) is formed to within
@@ -871,7 +911,10 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
         if (FP64) {
             const int win = exit64<LPR, true>(h, gp, blk, a.g1.rec64 + 2 * (int64_t)B, cnt, (double)pmx, (double)pmy,
                                               (double)pmz, r64, k64, kf64, gmask, gl, s64);
-            if (win > 0) {
+            if (win == kSphereWin) {
+                found = true;
+                to_wall = true;
+            } else if (win > 0) {
                 qn = __ldg(blk + win);
                 found = true;
                 to_wall = rec_w(qn) < 0;
@@ -960,7 +1003,10 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
                 const int acnt = hdr_count(__ldg(ablk));
                 const int win = exit64<LPR, false>(h, gp, ablk, nullptr, acnt, (double)pmx, (double)pmy, (double)pmz,
                                                    rp, kd, nullptr, gmask, gl, s64);
-                if (win > 0) {
+                if (win == kSphereWin) {
+                    found = true;
+                    to_wall = true;
+                } else if (win > 0) {
                     const float4 qa = __ldg(ablk + win);
                     found = true;
                     to_wall = rec_w(qa) < 0;

@@ -58,10 +58,10 @@ def check_segments(ref, sel, seg_off, seg_cell, seg_len, diag, len_rel):
             assert np.all(np.abs(gl - rl) <= tol), f"ray {i}: lengths differ by {np.max(np.abs(gl - rl) / rl)}"
 
 
-def run_case(g, rays, ref, lanes=(1, 4)):
+def run_case(g, rays, ref, lanes=(1, 4), **mk):
     """Every ray: float64 and float32 segment lists and tau against the
     oracle, for each lanes-per-ray shape; tau identical across shapes."""
-    vg = make(g)
+    vg = make(g, **mk)
     diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
     O, D = dev(rays.origin), dev(rays.dir)
     ok = np.nonzero(ref.near_tie == 0)[0]
@@ -859,6 +859,78 @@ def test_rays_entering_from_outside():
     t = t32.tau.cpu().numpy().astype(np.float64)[ok]
     assert np.all(np.abs(t - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
     assert np.all(t32.tau.cpu().numpy()[~hit] == 0)
+
+
+def test_sphere_domain_parity():
+    """A spherical domain (the paper notes the method carries over to other
+    domain geometries, Sect. 2.2): the ball inscribed in the box, sites and
+    rays inside it. Both forms against the oracle on every ray and in two
+    lanes-per-ray shapes; every float64 path ends on the sphere."""
+    g = gen.make_ball_grid(3000, 51)
+    rays = gen.ball_rays(4000, 52)
+    ref = oracle_full(g, rays, sphere=gen.UNIT_BALL)
+    assert np.all(ref.status == 0)
+    vg = run_case(g, rays, ref, sphere=gen.UNIT_BALL)
+    r64 = vg.trace(dev(rays.origin), dev(rays.dir), precision="fp64", segments=True)
+    so = r64.seg_off.cpu().numpy()
+    L = np.add.reduceat(r64.seg_len.cpu().numpy(), so[:-1])
+    end = rays.origin + L[:, None] * rays.dir
+    np.testing.assert_allclose(np.linalg.norm(end, axis=1), 1.0, rtol=0, atol=1e-12)
+
+
+def test_sphere_domain_locate_and_entry():
+    """C(r) in a spherical domain (points of the box outside the ball are
+    outside the domain), and rays from outside the ball: each starts epsilon
+    past its entry point, as the oracle's, and the paths match; rays that
+    miss the ball are outside."""
+    g = gen.make_ball_grid(2000, 53)
+    vg = make(g, sphere=gen.UNIT_BALL)
+    rng = gen.rng_for(54)
+    P = np.concatenate([gen.uniform_points(4000, rng, g.box),
+                        np.array([[0.0, 0, 1.0], [0.6, -0.8, 0], [0.0, 0.8, 0.6000001], [1.0, 1.0, 1.0]])])
+    ref = oracle.locate(g.sites, g.box, P, sphere=gen.UNIT_BALL)
+    assert (ref == -1).sum() > 1000
+    for prec in ("fp32", "fp64"):
+        np.testing.assert_array_equal(vg.locate(dev(P), precision=prec).cpu().numpy(), ref)
+    O = gen.uniform_points(3000, rng, np.array([-2.5, -2.5, -2.5, 2.5, 2.5, 2.5]))
+    D = gen.isotropic_dirs(3000, rng)
+    E = oracle.enter_points(g.box, O, D, sphere=gen.UNIT_BALL)
+    c = oracle.cells(g.sites, g.box)
+    off, idx = oracle.csr(c, len(g.sites))
+    tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), E, D, off=off, idx=idx, sphere=gen.UNIT_BALL)
+    diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+    r64 = vg.trace(dev(O), dev(D), precision="fp64", segments=True, status=True, enter=True)
+    t32 = vg.trace(dev(O), dev(D), precision="fp32", status=True, enter=True)
+    from paper_1310_1854_gb300 import _lib
+    hit = tr.status == 0
+    assert hit.sum() > 300 and (~hit).sum() > 300
+    assert np.all(r64.status.cpu().numpy()[~hit] == _lib.RAY_OUTSIDE)
+    assert np.all(r64.status.cpu().numpy()[hit] == 0) and np.all(t32.status.cpu().numpy()[hit] == 0)
+    ok = np.nonzero(hit & (tr.near_tie == 0))[0]
+    check_segments(tr, ok, r64.seg_off, r64.seg_cell, r64.seg_len, diag, LEN64_REL)
+    t = t32.tau.cpu().numpy().astype(np.float64)[ok]
+    assert np.all(np.abs(t - tr.tau[ok]) <= TAU32_REL * tr.tau[ok])
+
+
+def test_sphere_domain_in_a_batch():
+    """A batch that mixes a spherical-domain grid with box grids gives each
+    grid's single-grid tau bit for bit."""
+    from paper_1310_1854_gb300 import Batch
+    gs = gen.make_ball_grid(2000, 55)
+    rs = gen.ball_rays(3000, 56)
+    gb = gen.make_uniform_grid(1500, 57)
+    rb = gen.uniform_rays(2000, 58)
+    a = make(gs, sphere=gen.UNIT_BALL)
+    b = make(gb)
+    want = [a.trace(dev(rs.origin), dev(rs.dir)).tau.cpu().numpy(), b.trace(dev(rb.origin), dev(rb.dir)).tau.cpu().numpy()]
+    bt = Batch([(a, dev(rs.origin), dev(rs.dir)), (b, dev(rb.origin), dev(rb.dir))])
+    bt.run()
+    for k in range(2):
+        np.testing.assert_array_equal(bt.tau[k].cpu().numpy(), want[k])
+    ref = oracle_full(gs, rs, sphere=gen.UNIT_BALL)
+    ok = ref.near_tie == 0
+    t = want[0].astype(np.float64)
+    assert np.all(np.abs(t[ok] - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
 
 
 def test_grid_quality_matches_oracle_locate():

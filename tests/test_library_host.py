@@ -230,3 +230,35 @@ def test_zero_run_limit_option(libvgrid):
     with pytest.raises(_lib.VGridError) as e:
         _grid(gen.cubic_lattice(2), gen.CUBE_BOX, zero_run_max=-1)
     assert e.value.code == _lib.ERR_ARG
+
+
+def test_sphere_domain_options(libvgrid):
+    """opts.domain / opts.sphere: box by default; a ball must lie inside the
+    box with a positive radius and hold every site; its grid keeps the box's
+    neighbour lists (the cells are the box's clipping)."""
+    from paper_1310_1854_gb300 import _lib
+    lib = _lib.load()
+    o = _lib.Opts()
+    lib.vgrid_default_opts(ctypes.byref(o))
+    assert o.domain == _lib.DOMAIN_BOX and list(o.sphere) == [0.0] * 4
+    g = gen.make_ball_grid(400, 61)
+    a = _grid(g.sites, g.box, sphere=gen.UNIT_BALL)
+    b = _grid(g.sites, g.box)
+    for x, y in zip(a.neighbors(), b.neighbors()):
+        np.testing.assert_array_equal(x, y)
+    for bad in ((0.0, 0, 0, 1.5), (0.5, 0, 0, 0.6), (0.0, 0, 0, 0.0), (0.0, 0, 0, -1.0), (0.0, np.nan, 0, 0.5)):
+        with pytest.raises(_lib.VGridError) as e:
+            _grid(g.sites, g.box, sphere=bad)
+        assert e.value.code == _lib.ERR_ARG
+    # a site outside the ball (but inside the box)
+    S = np.concatenate([g.sites, [[0.875, 0.875, 0.0]]])  # float32 values, 1.53125 > 1
+    with pytest.raises(_lib.VGridError) as e:
+        _grid(S, g.box, sphere=gen.UNIT_BALL)
+    assert e.value.code == _lib.ERR_OUTSIDE
+    o.domain = 2
+    M = len(g.sites)
+    h = ctypes.c_void_p()
+    S = np.ascontiguousarray(g.sites, np.float64)
+    B = np.ascontiguousarray(g.box, np.float64)
+    assert lib.vgrid_create(S.ctypes.data_as(ctypes.c_void_p), M, B.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.byref(o), ctypes.byref(h)) == _lib.ERR_ARG
