@@ -824,8 +824,9 @@ def run_extra(args):
 
 def run_next(args, base, flush, sampler):
     """One line per row built after the hot path: Monte Carlo interaction
-    sampling along the path, rays entering from outside the box, and C(r)
-    at uniform points for the grid-quality measure (Table 1)."""
+    sampling along the path, rays entering from outside the box, a spherical
+    domain, and C(r) at uniform points for the grid-quality measure
+    (Table 1)."""
     import torch
 
     import gen
@@ -881,6 +882,23 @@ def run_next(args, base, flush, sampler):
                 config={"workload": "exp-disk 1e5 sites, 1e6 rays from a sphere around the box aimed at uniform "
                                     "points inside it (entry point by the slab test, then the same traversal)",
                         "sites": g.sites.shape[0], "rays": N, "l2": "flushed between timed steps"},
+                stats_per_step=st, roofline=None, e2e=None)
+    print(json.dumps(line), flush=True)
+
+    # f2, another domain geometry: a ball (the unit ball inscribed in
+    # [-1,1]^3), 1e5 sites and 1e6 rays inside it
+    gb = gen.make_ball_grid(100_000, gen.SEED_BASE + 80)
+    vb = VoronoiGrid(gb.sites, gb.box, sphere=gen.UNIT_BALL)
+    vb.set_density(torch.from_numpy(gb.rho).to(dev))
+    rb = gen.ball_rays(N, gen.SEED_BASE + 81)
+    Ob = torch.from_numpy(rb.origin).to(dev)
+    Db = torch.from_numpy(rb.dir).to(dev)
+    st = vb.trace(Ob, Db, precision="fp32", stats=True).stats
+    ms, nk, clocks = timed(lambda: vb.trace(Ob, Db, precision="fp32", out_tau=tau), args.steps)
+    line = dict(base, value=st["crossings"] / (ms / 1e3), ms_per_step=ms, gpu_launches=nk, clocks=clocks,
+                config={"workload": "spherical domain: 1e5 sites uniform in the unit ball, rho = exp(-3|r|), "
+                                    "1e6 rays from uniform points of the ball, paths ending on the sphere",
+                        "sites": gb.sites.shape[0], "rays": N, "l2": "flushed between timed steps"},
                 stats_per_step=st, roofline=None, e2e=None)
     print(json.dumps(line), flush=True)
 
