@@ -548,10 +548,39 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
             brec[4 * q + 0] = brec[4 * q + 1] = brec[4 * q + 2] = fnan;
             put_int(&brec[4 * q + 3], -1);
         }
+        // each list ordered by the sites' distance from its block's centre,
+        // flo_hi + (i + 1/2) fbw per axis in float32 (the operations the
+        // start-cell search repeats), ties by cell: the search stops once the
+        // rest of the list is certainly farther than its best site
+        const int32_t *bd = g->blocks.dim;
+        float fbw[3], flo[3];
+        for (int c = 0; c < 3; c++) {
+            fbw[c] = (float)((bbox[3 + c] - bbox[c]) / bd[c]);
+            flo[c] = (float)bbox[c];
+        }
         vg::parallel_for((int64_t)nblk, o.threads, 1 << 12, [&](int64_t b0, int64_t b1) {
+            std::vector<std::pair<double, int32_t>> ord;
             for (int64_t b = b0; b < b1; b++) {
+                const int64_t bk[3] = {b / ((int64_t)bd[1] * bd[2]), (b / bd[2]) % bd[1], b % bd[2]};
+                double cen[3];
+                for (int c = 0; c < 3; c++) {
+                    volatile float t = (float)bk[c] + 0.5f;
+                    volatile float m = t * fbw[c];
+                    cen[c] = (double)(float)(flo[c] + m);
+                }
+                ord.clear();
                 for (int64_t q = g->blocks.off[b]; q < g->blocks.off[b + 1]; q++) {
                     const int32_t c = g->blocks.idx[q];
+                    double d2 = 0.0;
+                    for (int a = 0; a < 3; a++) {
+                        const double d = (double)(float)Si[3 * (int64_t)c + a] - cen[a];
+                        d2 += d * d;
+                    }
+                    ord.emplace_back(d2, c);
+                }
+                std::sort(ord.begin(), ord.end());
+                for (int64_t q = g->blocks.off[b]; q < g->blocks.off[b + 1]; q++) {
+                    const int32_t c = ord[(size_t)(q - g->blocks.off[b])].second;
                     float *r = &brec[4 * ((size_t)boff[b] + (size_t)(q - g->blocks.off[b]))];
                     r[0] = (float)Si[3 * (int64_t)c + 0];
                     r[1] = (float)Si[3 * (int64_t)c + 1];
@@ -596,6 +625,7 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
         hd.flo_hi[c] = (float)bbox[c];
         hd.flo_lo[c] = (float)(bbox[c] - (double)hd.flo_hi[c]);
         hd.fbscale[c] = (float)hd.bscale[c];
+        hd.fbw[c] = (float)((bbox[3 + c] - bbox[c]) / g->blocks.dim[c]);
         hd.ddim[c] = ddim[c];
         hd.dscale[c] = (float)((double)ddim[c] / (bbox[3 + c] - bbox[c]));
         dmax = std::max(dmax, std::max(std::fabs(bbox[c]), std::fabs(bbox[3 + c])));

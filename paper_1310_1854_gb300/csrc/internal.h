@@ -85,6 +85,9 @@ struct GridDev {
     int64_t lokey[3], hikey[3];        // order keys of lo and hi (exact box test)
     float flo_hi[3], flo_lo[3];        // lo as float pairs
     float fbscale[3];                  // bscale in float32
+    float fbw[3];                      // block width in float32; block (i, j, k) has the
+                                       // centre flo_hi + (i + 1/2) fbw (float32 operations),
+                                       // and its list is ordered by distance from it
     const float *dens;                 // coarse grid of (sites per unit volume)^(1/3), for the ray order
     int32_t ddim[3];                   // its cells per axis
     float dscale[3];                   // its cells per unit length

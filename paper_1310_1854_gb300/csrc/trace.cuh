@@ -408,8 +408,7 @@ __device__ __forceinline__ bool inside(const GridDev *gp, const LocPt &P) {
 // 2u|x - lo| + 4u^2 max|coordinate|, so the index may be off only for points
 // closer to a block face than the padding of the block lists, and those
 // lists name every cell within that padding.
-__device__ __forceinline__ int block_of(const GridDev *gp, const LocPt &P) {
-    int i[3];
+__device__ __forceinline__ int block_of(const GridDev *gp, const LocPt &P, int *i) {
 #pragma unroll
     for (int c = 0; c < 3; c++) {
         const float d = __fadd_rn(__fsub_rn(P.h[c], gp->flo_hi[c]), __fsub_rn(P.l[c], gp->flo_lo[c]));
@@ -443,13 +442,21 @@ static __device__ __noinline__ int locate64(const GridDev *gp, double x, double 
 // D2 - E(D2) > D1 + E(D1), E(D) = u (10 D + 4 X sqrt D), X = max |x_c|,
 // which bounds the rounding error of a float32 squared distance; otherwise
 // the list is rescanned in float64. *rechecked is set when that happened.
+// A block's list is ordered by the sites' distance from the block's centre
+// c, so the float32 scan can stop early: a site not scanned yet is at least
+// as far from c as the last one scanned, s, hence at least |s - c| - |p - c|
+// from the point p (triangle inequality). That bound, rounded down with
+// margins for the float32 distances (16u relative) and for p's low words
+// (4uX), stops the scan once its square exceeds D1, and takes the place of
+// D2 when smaller, so the acceptance test above stays rigorous.
 // Block lists start on 32-byte boundaries and have an even length (NaN
 // records pad them; a NaN distance never wins), so they can be read in pairs
 // (PAIRS; the traversal kernel's rare relocation reads them one by one).
 template <bool PAIRS>
 static __device__ __noinline__ int locate_point(const GridDev *gp, const LocPt P, bool fp32, int *rechecked) {
     if (!inside(gp, P)) return -1;
-    const int b = block_of(gp, P);
+    int bi[3];
+    const int b = block_of(gp, P, bi);
     const int beg = __ldg(&gp->blk_off[b]), end = __ldg(&gp->blk_off[b + 1]);
     if (fp32) {
         const float4 *rec = gp->blk_rec;
@@ -457,6 +464,17 @@ static __device__ __noinline__ int locate_point(const GridDev *gp, const LocPt P
         const float X = fmaxf(fabsf(xf), fmaxf(fabsf(yf), fabsf(zf)));
         float D1 = __int_as_float(0x7f800000), D2 = D1;
         int i1 = -1;
+        float cc[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++)
+            cc[c] = __fadd_rn(gp->flo_hi[c], __fmul_rn(__fadd_rn((float)bi[c], 0.5f), gp->fbw[c]));
+        float rp;
+        {
+            const float ex = __fsub_rn(xf, cc[0]), ey = __fsub_rn(yf, cc[1]), ez = __fsub_rn(zf, cc[2]);
+            rp = __fsqrt_rn(__fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex))));
+        }
+        // |p - c| rounded up, plus p's low words: subtracted from the bound
+        const float slack = __fadd_ru(__fmul_ru(rp, 1.0f + 16.0f * kU), __fmul_ru(4.0f * kU, X));
         for (int i = beg; i < end; i += 2) {
             float4 q[2];
             if (PAIRS) {
@@ -473,6 +491,17 @@ static __device__ __noinline__ int locate_point(const GridDev *gp, const LocPt P
                 D2 = better ? D1 : fminf(D2, D);
                 i1 = better ? __float_as_int(q[u].w) : i1;
                 D1 = fminf(D1, D);
+            }
+            // the rest of the list is at least lb from p (NaN padding: no stop)
+            const float ex = __fsub_rn(q[1].x, cc[0]), ey = __fsub_rn(q[1].y, cc[1]), ez = __fsub_rn(q[1].z, cc[2]);
+            const float dl = __fsqrt_rn(__fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex))));
+            const float lb = __fsub_rd(__fmul_rd(dl, 1.0f - 16.0f * kU), slack);
+            if (lb > 0.0f) {
+                const float lb2 = __fmul_rd(lb, lb);
+                if (lb2 > D1) {
+                    D2 = fminf(D2, lb2);
+                    break;
+                }
             }
         }
         if (i1 >= 0 && D2 == __int_as_float(0x7f800000)) return i1;  // a single candidate
