@@ -262,6 +262,26 @@ def test_tiny_coordinates_parity():
     run_case(g, rays, ref)
 
 
+@pytest.mark.parametrize("box", [(1000.0, 1000.0, 1000.0, 1002.0, 1002.0, 1002.0),
+                                 (-1e-3, -1e-3, -1e-3, 1e-3, 1e-3, 1e-3),
+                                 (0.0, 0.0, 0.0, 4.0, 4.0, 0.02)],
+                         ids=["far_from_origin", "millimetre", "thin_slab"])
+def test_offset_scaled_and_thin_boxes_parity(box):
+    """The error bounds of the float32 form carry the coordinates' size (the
+    float pairs of r0 and k, C(r)'s 4uX term): a box far from the origin
+    (coordinates 1000 times the cell size), a tiny box (cells of 1e-4) and a
+    thin slab (cells wider than the slab is thick) give the oracle's cells
+    and lengths in both forms."""
+    B = np.array(box, np.float64)
+    rng = gen.rng_for(109)
+    S = gen.uniform_points(1500, rng, B).astype(np.float32).astype(np.float64)
+    S = np.unique(S[np.all((S >= B[:3]) & (S <= B[3:]), axis=1)], axis=0)
+    g = gen.Grid(S, B, rng.uniform(0.5, 1.5, len(S)).astype(np.float32))
+    rays = gen.uniform_rays(3000, 110, B)
+    ref = oracle_full(g, rays)
+    run_case(g, rays, ref)
+
+
 def test_locate_parity():
     g = gen.make_disk_grid(20_000, 107)
     vg = make(g)
