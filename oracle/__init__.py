@@ -46,15 +46,23 @@ STATUS = {0: "ok", 1: "outside", 2: "step_limit", 3: "capacity"}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle's C source with gcc (no contraction, -O2, pthreads)."""
+    """Compile the oracle's C source with gcc (no contraction, -O2, pthreads).
+    ORACLE_LIB names an already built library instead (the tests' planted
+    mistakes: a copy of the source with one change, built the same way)."""
+    if os.environ.get("ORACLE_LIB"):
+        return os.environ["ORACLE_LIB"]
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-pthread", "-o", tmp, _SRC, "-lm"]
+        cmd = compile_command(_SRC, tmp)
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def compile_command(src: str, out: str) -> list:
+    return ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
+            "-o", out, src, "-lm"]
 
 
 def _load():

@@ -697,3 +697,17 @@ def test_sphere_enter_points():
     for i in np.nonzero(out & ~moved)[0][:100]:
         p = O[i] + ts[:, None] * D[i]
         assert not np.any(np.linalg.norm(p, axis=1) < 1.0 - 1e-3)
+
+
+@pytest.mark.parametrize("case", _load("tie_examples.json")["cases"], ids=lambda c: c["name"])
+def test_tie_examples(case):
+    """R4 on a path where the tie-break shows: with every site a candidate, a
+    ray through the edge where four cells meet goes straight into the
+    diagonal cell, whose id is the lowest of the three tied planes."""
+    S = np.array(case["sites"], np.float64)
+    tr = oracle.trace(S, np.array(case["box"], np.float64), np.array(case["rho"]), np.array([case["origin"]]),
+                      np.array([case["dir"]]), zero_run_max=case["zero_run_max"])
+    assert int(tr.nfallback[0]) == case["nfallback"]
+    cells, lens = tr.segments(0)
+    assert [int(c) for c in cells] == [e[0] for e in case["segments"]]
+    np.testing.assert_allclose(lens, [e[1] for e in case["segments"]], rtol=1e-12)
