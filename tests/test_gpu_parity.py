@@ -967,6 +967,23 @@ def test_grid_quality_matches_oracle_locate():
     assert q["mean"] == pytest.approx(float(d.mean()), rel=1e-9, abs=1e-15)
 
 
+def test_grid_quality_in_a_spherical_domain():
+    """The same measure over a ball: the sample points are spread over the
+    ball, and the GPU's cells equal the oracle's C(r) there."""
+    from paper_1310_1854_gb300.quality import grid_quality, sample_points
+    g = gen.make_ball_grid(5000, 321)
+    vg = make(g, sphere=gen.UNIT_BALL)
+
+    def rho_true(p):
+        return np.exp(-3.0 * np.linalg.norm(p, axis=1))
+    q = grid_quality(vg, g.rho, rho_true, n_points=20_000, seed=6)
+    P = sample_points(g.box, 20_000, 6, gen.UNIT_BALL)
+    cell = oracle.locate(g.sites, g.box, P, sphere=gen.UNIT_BALL)
+    assert np.all(cell >= 0)
+    d = rho_true(P) - g.rho.astype(np.float64)[cell]
+    assert q["std"] == pytest.approx(float(d.std()), rel=1e-12)
+
+
 @pytest.mark.parametrize("kind", ["uniform", "disk", "clumpy", "lattice"])
 def test_gpu_cell_construction_matches_host(kind):
     from paper_1310_1854_gb300 import VoronoiGrid

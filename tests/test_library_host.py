@@ -262,3 +262,16 @@ def test_sphere_domain_options(libvgrid):
     B = np.ascontiguousarray(g.box, np.float64)
     assert lib.vgrid_create(S.ctypes.data_as(ctypes.c_void_p), M, B.ctypes.data_as(ctypes.c_void_p),
                             ctypes.byref(o), ctypes.byref(h)) == _lib.ERR_ARG
+
+
+def test_quality_samples_cover_the_domain():
+    """grid_quality's points: uniform in the box, or in the ball of a
+    spherical domain (every point inside it; the share within half the
+    radius is 1/8, the ratio of the volumes)."""
+    from paper_1310_1854_gb300.quality import sample_points
+    P = sample_points(gen.CUBE_BOX, 20_000, 3)
+    assert np.all((P >= -1) & (P <= 1))
+    B = sample_points(gen.CUBE_BOX, 40_000, 4, gen.UNIT_BALL)
+    r = np.linalg.norm(B, axis=1)
+    assert B.shape == (40_000, 3) and np.all(r <= 1.0)
+    assert abs(np.mean(r < 0.5) - 0.125) < 0.01
