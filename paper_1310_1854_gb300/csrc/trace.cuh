@@ -574,8 +574,20 @@ __device__ __forceinline__ void consider32(int pos, bool valid, float4 q, float 
     const Plane32 p = plane32(q, rx, ry, rz, dnumK, dden, Kx, Ky, Kz);
     const float num_lo = fmaxf(__fmaf_rd(p.num, kDivLo, -dnumK), 0.0f);
     const float den_hi = __fadd_ru(p.den, p.dden);
-    float lower = __fdividef(num_lo, den_hi);
-    lower = (valid && den_hi > kDivMin) ? lower : __int_as_float(0x7f800000);
+    float lower;
+    if (KEEP) {
+        // one lane per ray (every position valid): the divisor clamped at 0
+        // masks a plane certainly facing away (den_hi <= 0 and the NaN
+        // padding: a / 0 = +inf, 0 / 0 = NaN, and a NaN loses every
+        // comparison and min below); 0 < den_hi <= 2^-126 means den~ < 0,
+        // a plane facing away too, whatever value it gets can only lower
+        // L2 or win without an upper bound (den_lo < 0), which sends the
+        // crossing to the float64 recheck
+        lower = __fdividef(num_lo, fmaxf(den_hi, 0.0f));
+    } else {
+        lower = __fdividef(num_lo, den_hi);
+        lower = (valid && den_hi > kDivMin) ? lower : __int_as_float(0x7f800000);
+    }
     const bool b = lower < c.L1;
     c.L2 = b ? c.L1 : fminf(c.L2, lower);
     if (KEEP) {
@@ -711,19 +723,18 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
     // float32 form: origin and direction as float pairs, ray parameter t, wall
     // exit. Only the high words of the direction (used by every plane test)
     // and t stay in registers; the origin pairs, the low words of the
-    // direction, the wall distance and the error terms (read once per
-    // crossing) are kept per thread in shared memory.
+    // direction and the wall distance (read once per crossing) are kept per
+    // thread in shared memory, and the error terms are formed from the wall
+    // distance when needed.
     float Kh[3];
     float th = 0.f, tl = 0.f;
-    __shared__ float s_ray[FP64 ? 1 : 13][FP64 ? 1 : 256];
+    __shared__ float s_ray[FP64 ? 1 : 11][FP64 ? 1 : 256];
     const int tix = threadIdx.x;
 #define R0h_(c) s_ray[(c)][tix]
 #define R0l_(c) s_ray[3 + (c)][tix]
 #define Kl_(c) s_ray[6 + (c)][tix]
 #define tmh_ s_ray[9][tix]
 #define tml_ s_ray[10][tix]
-#define er_ s_ray[11][tix]
-#define ewall_ s_ray[12][tix]
     int B = 0;              // block offset of the current cell
     float pmx = 0.f, pmy = 0.f, pmz = 0.f;
     double tau64 = 0.0;
@@ -875,9 +886,6 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
                 R0l_(0) = a1.w; R0l_(1) = a2.x; R0l_(2) = a2.y;
                 Kh[0] = a2.z;  Kh[1] = a2.w;  Kh[2] = a3.x;
                 Kl_(0) = a3.y;  Kl_(1) = a3.z;  Kl_(2) = a3.w;
-                const float scale = BATCH ? (float)gp->scale : (float)a.g1.scale;
-                er_ = 16.0f * kU2 * (scale + a0.z);
-                ewall_ = 16.0f * kU2 * a0.z;
             }
             status = m == -2 ? RAY_BAD_DIR : (m < 0 ? RAY_OUTSIDE : RAY_OK);
             if (status == RAY_OK) {
@@ -963,7 +971,11 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
             const float ry = local_coord(R0h_(1), R0l_(1), Kh[1], Kl_(1), th, tl, pmy);
             const float rz = local_coord(R0h_(2), R0l_(2), Kh[2], Kl_(2), th, tl, pmz);
             const float r1 = __fadd_rn(__fadd_rn(fabsf(rx), fabsf(ry)), fabsf(rz));
-            const float rr = __fmaf_rn(kCB, r1, 2.0f * er_);
+            // the error terms of r and of the wall distance from t_max (no
+            // shared-memory reads)
+            const float tmax_h = tmh_;
+            const float scale = BATCH ? (float)gp->scale : (float)a.g1.scale;
+            const float rr = __fmaf_rn(kCB, r1, 2.0f * (16.0f * kU2 * (scale + tmax_h)));
             const float n1m = hdr1.z;  // the cell's bound on |n|_1
             // the rounding bound of den~ plus 2^-126 (see consider32)
             const float dden = __fadd_ru(__fmul_ru(kCDen, n1m), kDivMin);
@@ -975,7 +987,7 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
             float sw, swl;
             two_sum(tmh_, -th, sw, swl);
             sw = __fadd_rn(sw, __fadd_rn(swl, __fsub_rn(tml_, tl)));
-            const float Ew = __fmaf_rn(3.0f * kU, fabsf(sw), ewall_);
+            const float Ew = __fmaf_rn(3.0f * kU, fabsf(sw), 16.0f * kU2 * tmax_h);
             const float lw = __fsub_rd(sw, Ew);
             bool wall_wins = false;
             if (lw < c.L1) {
@@ -1185,8 +1197,6 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
 #undef Kl_
 #undef tmh_
 #undef tml_
-#undef er_
-#undef ewall_
     __syncthreads();
     if (threadIdx.x < 9 && s_stats[threadIdx.x])
         atomicAdd(reinterpret_cast<unsigned long long *>(a.stats) + threadIdx.x, s_stats[threadIdx.x]);
