@@ -5,9 +5,12 @@
 // largest vertex radius cannot, so the search stops once every unvisited
 // site is that far (security radius).
 //
-// Sites are first sorted into a uniform grid of buckets (counting sort; each
+// Sites are first sorted into a grid of buckets (counting sort; each
 // bucket's list is then ordered by site index so the result does not depend
-// on atomic order). One thread builds one cell: a convex polyhedron in
+// on atomic order). The grid lines of each axis sit at quantiles of the
+// sites' coordinates on that axis, so that where the sites are dense the
+// buckets are small: a density that is a product of functions of x, y and z
+// gives every bucket about the same number of sites. One thread builds one cell: a convex polyhedron in
 // float64 with shared vertices and faces as vertex loops, cut plane by plane
 // while the buckets are visited ring by ring around the site. Fixed
 // capacities keep the polyhedron in local memory; a cell that would overflow
@@ -33,9 +36,7 @@ constexpr int kNE = 64;    // crossed edges of one cut
 constexpr int kCap = 64;   // neighbour ids written back per cell
 
 struct BucketGrid {
-    double lo[3];
-    double inv[3];   // buckets per unit length
-    double wmin;     // smallest bucket width
+    const double *edge[3];  // grid lines of each axis: dim + 1 non-decreasing values, box bounds at both ends
     int dim[3];
 };
 
@@ -61,16 +62,23 @@ struct Scratch {
     double x[kNV], y[kNV], z[kNV];
 };
 
-__device__ __forceinline__ int bucket_coord(double v, double lo, double inv, int dim) {
-    int i = (int)((v - lo) * inv);
-    return max(0, min(i, dim - 1));
+// the bucket of coordinate v along one axis: the largest i < dim with
+// edge[i] <= v (0 below the first line)
+__device__ __forceinline__ int bucket_coord(double v, const double *edge, int dim) {
+    int lo = 0, hi = dim - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(edge + mid) <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 __global__ void bucket_count_kernel(const double *S, int64_t M, BucketGrid bg, int *bidx, int64_t *cnt) {
     for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
-        const int i = bucket_coord(S[3 * m], bg.lo[0], bg.inv[0], bg.dim[0]);
-        const int j = bucket_coord(S[3 * m + 1], bg.lo[1], bg.inv[1], bg.dim[1]);
-        const int k = bucket_coord(S[3 * m + 2], bg.lo[2], bg.inv[2], bg.dim[2]);
+        const int i = bucket_coord(S[3 * m], bg.edge[0], bg.dim[0]);
+        const int j = bucket_coord(S[3 * m + 1], bg.edge[1], bg.dim[1]);
+        const int k = bucket_coord(S[3 * m + 2], bg.edge[2], bg.dim[2]);
         const int b = (i * bg.dim[1] + j) * bg.dim[2] + k;
         bidx[m] = b;
         atomicAdd(reinterpret_cast<unsigned long long *>(&cnt[b]), 1ull);
@@ -315,9 +323,11 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
             return __double2float_ru(reach * reach * (1.0 + 0x1p-17));
         };
         float R2f = reach2f(rmax);
-        const int bi = bucket_coord(px, bg.lo[0], bg.inv[0], bg.dim[0]);
-        const int bj = bucket_coord(py, bg.lo[1], bg.inv[1], bg.dim[1]);
-        const int bk = bucket_coord(pz, bg.lo[2], bg.inv[2], bg.dim[2]);
+        const int bi = bucket_coord(px, bg.edge[0], bg.dim[0]);
+        const int bj = bucket_coord(py, bg.edge[1], bg.dim[1]);
+        const int bk = bucket_coord(pz, bg.edge[2], bg.dim[2]);
+        const int bc[3] = {bi, bj, bk};
+        const double pc[3] = {px, py, pz};
         const int smax = max(bg.dim[0], max(bg.dim[1], bg.dim[2]));
         int fail = 0;
         for (int s = 0; s <= smax && !fail; s++) {
@@ -355,8 +365,17 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                     }
                 }
             }
-            // every unvisited site is at least s bucket widths away
-            if (2.0 * rmax + 4.0 * eps < (double)s * bg.wmin) break;
+            // every unvisited site lies beyond one of the grid lines that
+            // bound rings 0..s (a site in bucket i has edge[i] <= v <
+            // edge[i + 1]), so it is at least the smallest gap from the
+            // site to those lines away; there are no sites past the last
+            // bucket on either side
+            double gap = 1e300;
+            for (int c = 0; c < 3; c++) {
+                if (bc[c] + s + 1 <= bg.dim[c] - 1) gap = fmin(gap, __ldg(bg.edge[c] + bc[c] + s + 1) - pc[c]);
+                if (bc[c] - s >= 1) gap = fmin(gap, pc[c] - __ldg(bg.edge[c] + bc[c] - s));
+            }
+            if (2.0 * rmax + 4.0 * eps < gap) break;
         }
         // faces of positive area -> neighbours; volume as pyramids from the site; bounding box
         int cnt = 0;
@@ -410,23 +429,34 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     BucketGrid bg;
     const double target = std::max(1.0, 0.5 * (double)M);  // about two sites per bucket
     const double w = std::cbrt(ext[0] * ext[1] * ext[2] / target);
-    bg.wmin = 1e300;
     int64_t K = 1;
-    for (int c = 0; c < 3; c++) {
-        bg.dim[c] = (int)std::min<long>(std::max<long>(std::lround(ext[c] / w), 1), 512);
-        bg.lo[c] = box[c];
-        bg.inv[c] = bg.dim[c] / ext[c];
-        bg.wmin = std::min(bg.wmin, ext[c] / bg.dim[c]);
-        K *= bg.dim[c];
+    // grid lines at quantiles of each coordinate, from every stride-th site
+    // (at most 2^16 of them; deterministic)
+    std::vector<double> edges;
+    {
+        const int64_t stride = std::max<int64_t>(1, M >> 16);
+        std::vector<double> v;
+        for (int c = 0; c < 3; c++) {
+            bg.dim[c] = (int)std::min<long>(std::max<long>(std::lround(ext[c] / w), 1), 512);
+            K *= bg.dim[c];
+            v.clear();
+            for (int64_t m = 0; m < M; m += stride) v.push_back(S[3 * m + c]);
+            std::sort(v.begin(), v.end());
+            const int64_t n = (int64_t)v.size();
+            edges.push_back(box[c]);
+            for (int i = 1; i < bg.dim[c]; i++)
+                edges.push_back(std::max(edges.back(), std::min(box[3 + c], v[(size_t)(i * n / bg.dim[c])])));
+            edges.push_back(box[3 + c]);
+        }
     }
-    double *dS = nullptr;
+    double *dS = nullptr, *dE = nullptr;
     float4 *dSf = nullptr;
     int prefilter = 1;
     int *bidx = nullptr, *bsites = nullptr, *cnt = nullptr, *nbr = nullptr, *fail = nullptr;
     int64_t *boff = nullptr, *cursor = nullptr, *tmp = nullptr;
     double *vol = nullptr, *bbox = nullptr;
     auto cleanup = [&]() {
-        void *ptrs[] = {dS, dSf, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
+        void *ptrs[] = {dS, dE, dSf, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     };
@@ -448,6 +478,12 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     if ((e = cudaMalloc(&vol, sizeof(double) * M)) != cudaSuccess) return bad(e, "alloc");
     if ((e = cudaMalloc(&bbox, sizeof(double) * 6 * M)) != cudaSuccess) return bad(e, "alloc");
     if ((e = cudaMemcpy(dS, S, sizeof(double) * 3 * M, cudaMemcpyHostToDevice)) != cudaSuccess) return bad(e, "upload");
+    if ((e = cudaMalloc(&dE, sizeof(double) * edges.size())) != cudaSuccess) return bad(e, "alloc");
+    if ((e = cudaMemcpy(dE, edges.data(), sizeof(double) * edges.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bad(e, "upload");
+    bg.edge[0] = dE;
+    bg.edge[1] = dE + bg.dim[0] + 1;
+    bg.edge[2] = bg.edge[1] + bg.dim[1] + 1;
     {
         // float copies of the sites; the prefilter's bound needs them exact
         // (sites are float32 values; it is off otherwise)
