@@ -12,9 +12,10 @@
 // buckets are small: a density that is a product of functions of x, y and z
 // gives every bucket about the same number of sites. One thread builds one cell: a convex polyhedron in
 // float64 with shared vertices and faces as vertex loops, cut plane by plane
-// while the buckets are visited ring by ring around the site. Fixed
-// capacities keep the polyhedron in local memory; a cell that would overflow
-// them is flagged and rebuilt by the host builder.
+// while the buckets are visited ring by ring around the site, the sites of
+// each ring nearest first. Fixed capacities keep the polyhedron in local
+// memory; a cell that would overflow them is flagged and rebuilt by the
+// host builder.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -330,6 +331,45 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
         const double pc[3] = {px, py, pz};
         const int smax = max(bg.dim[0], max(bg.dim[1], bg.dim[2]));
         int fail = 0;
+        // each shell's candidates within reach are cut nearest first (up to
+        // kBuf at a time, picked by float32 distance, ties by index): the
+        // near planes shrink the polyhedron, and with it the reach, so that
+        // more of the far candidates drop out before they are cut. The
+        // result is the same polyhedron up to rounding; only the work to
+        // reach it changes.
+        constexpr int kBuf = 384;
+        float bd[kBuf];
+        int bq[kBuf];
+        int nb = 0;
+        auto flush = [&]() -> int {
+            while (nb > 0) {
+                int k = 0;
+                for (int i = 1; i < nb; i++)
+                    if (bd[i] < bd[k] || (bd[i] == bd[k] && bq[i] < bq[k])) k = i;
+                const float d2k = bd[k];
+                const int jj = bq[k];
+                nb--;
+                bd[k] = bd[nb];
+                bq[k] = bq[nb];
+                if (prefilter && d2k > R2f) {
+                    nb = 0;  // the nearest left is out of reach: so are the others
+                    break;
+                }
+                const double qx = S[3 * (int64_t)jj], qy = S[3 * (int64_t)jj + 1], qz = S[3 * (int64_t)jj + 2];
+                const double dx = qx - px, dy = qy - py, dz = qz - pz;
+                const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+                if (dist > 2.0 * rmax + 4.0 * eps) continue;
+                const double nx = dx / dist, ny = dy / dist, nz = dz / dist;
+                const double d = nx * 0.5 * (qx + px) + ny * 0.5 * (qy + py) + nz * 0.5 * (qz + pz);
+                const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps, Bscreen);
+                if (rc < 0) return 1;
+                if (rc > 0) {
+                    rmax = sqrt(poly_rmax2(P, px, py, pz));
+                    R2f = reach2f(rmax);
+                }
+            }
+            return 0;
+        };
         for (int s = 0; s <= smax && !fail; s++) {
             for (int di = -s; di <= s && !fail; di++) {
                 const int i = bi + di;
@@ -348,23 +388,18 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                             const float4 qf = Sf[jj];
                             const float fx = __fsub_rn(qf.x, pf.x), fy = __fsub_rn(qf.y, pf.y),
                                         fz = __fsub_rn(qf.z, pf.z);
-                            if (prefilter && __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx))) > R2f) continue;
-                            const double qx = S[3 * (int64_t)jj], qy = S[3 * (int64_t)jj + 1], qz = S[3 * (int64_t)jj + 2];
-                            const double dx = qx - px, dy = qy - py, dz = qz - pz;
-                            const double dist = sqrt(dx * dx + dy * dy + dz * dz);
-                            if (dist > 2.0 * rmax + 4.0 * eps) continue;
-                            const double nx = dx / dist, ny = dy / dist, nz = dz / dist;
-                            const double d = nx * 0.5 * (qx + px) + ny * 0.5 * (qy + py) + nz * 0.5 * (qz + pz);
-                            const int rc = poly_cut(P, W, nx, ny, nz, d, jj, eps, Bscreen);
-                            if (rc < 0) { fail = 1; break; }
-                            if (rc > 0) {
-                                rmax = sqrt(poly_rmax2(P, px, py, pz));
-                                R2f = reach2f(rmax);
-                            }
+                            const float d2f = __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+                            if (prefilter && d2f > R2f) continue;
+                            if (nb == kBuf) fail = flush();
+                            if (fail) break;
+                            bd[nb] = d2f;
+                            bq[nb] = jj;
+                            nb++;
                         }
                     }
                 }
             }
+            if (!fail) fail = flush();
             // every unvisited site lies beyond one of the grid lines that
             // bound rings 0..s (a site in bucket i has edge[i] <= v <
             // edge[i + 1]), so it is at least the smallest gap from the
