@@ -543,11 +543,17 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
     if (e == cudaSuccess) e = cudaMemcpy(g->d_dens, dens.data(), sizeof(float) * dens.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         const float fnan = std::numeric_limits<float>::quiet_NaN();
-        std::vector<float> brec(4 * ((size_t)boff[nblk] + 2));
-        for (size_t q = 0; q < brec.size() / 4; q++) {
+        // every entry is written below (the lists in parallel, each with its
+        // NaN padding, then the two entries past the end), so the buffer is
+        // allocated without a fill
+        const size_t nbrec = (size_t)boff[nblk] + 2;
+        std::unique_ptr<float[]> brec(new float[4 * nbrec]);
+        auto put_nan = [&](size_t q) {
             brec[4 * q + 0] = brec[4 * q + 1] = brec[4 * q + 2] = fnan;
             put_int(&brec[4 * q + 3], -1);
-        }
+        };
+        put_nan(nbrec - 2);
+        put_nan(nbrec - 1);
         // each list ordered by the sites' distance from its block's centre,
         // flo_hi + (i + 1/2) fbw per axis in float32 (the operations the
         // start-cell search repeats), ties by cell: the search stops once the
@@ -587,9 +593,11 @@ int vgrid_create(const double *sites, int64_t M, const double bbox[6], const vgr
                     r[2] = (float)Si[3 * (int64_t)c + 2];
                     put_int(r + 3, c);
                 }
+                const size_t len = (size_t)(g->blocks.off[b + 1] - g->blocks.off[b]);
+                for (size_t q = (size_t)boff[b] + len; q < (size_t)boff[b + 1]; q++) put_nan(q);
             }
         });
-        e = cudaMemcpy(g->d_blk_rec, brec.data(), sizeof(float) * brec.size(), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(g->d_blk_rec, brec.get(), sizeof(float) * 4 * nbrec, cudaMemcpyHostToDevice);
     }
 
     if (e == cudaSuccess) {
