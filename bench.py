@@ -825,8 +825,8 @@ def run_extra(args):
 def run_next(args, base, flush, sampler):
     """One line per row built after the hot path: Monte Carlo interaction
     sampling along the path, rays entering from outside the box, a spherical
-    domain, and C(r) at uniform points for the grid-quality measure
-    (Table 1)."""
+    domain, C(r) at uniform points for the grid-quality measure (Table 1),
+    and the cell construction on the GPU."""
     import torch
 
     import gen
@@ -914,6 +914,39 @@ def run_next(args, base, flush, sampler):
                                     "float64 recheck", "sites": g5.sites.shape[0], "points": P.shape[0],
                         "l2": "flushed between timed steps"},
                 quality={"std_rho_t_minus_rho_g": q["std"], "mean": q["mean"], "points": q["points"]},
+                roofline=None, e2e=None)
+    print(json.dumps(line), flush=True)
+
+    # f4: the cells of the 1e6-site clumpy grid built on the GPU (the whole
+    # vgrid_create, host phases included, wall clock); the host builder once
+    # beside it
+    del v5, P
+    g3, _ = gen.config3(n_rays=1)
+    reps = max(1, min(args.steps, 3))
+    VoronoiGrid(g3.sites, g3.box, gpu_build=True)  # warm-up
+    sampler.start()
+    n0 = kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        vg3 = VoronoiGrid(g3.sites, g3.box, gpu_build=True)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    nk = (kernel_launches() - n0) // reps
+    clocks = sampler.stop()
+    info = vg3.info()
+    t0 = time.perf_counter()
+    VoronoiGrid(g3.sites, g3.box)
+    host_sec = time.perf_counter() - t0
+    M3 = g3.sites.shape[0]
+    line = dict(base, metric="Voronoi cells built/sec (GPU cell construction, whole vgrid_create)", unit="cells/s",
+                value=M3 / sec, ms_per_step=sec * 1e3, steps=reps, higher_is_better=True, gpu_launches=nk,
+                clocks=clocks, dtype="f64",
+                config={"workload": "clumpy 1e6 sites (2,000 clumps): neighbour lists, volumes and bounding boxes "
+                                    "cut on the GPU, then the device layout", "sites": M3,
+                        "phase_seconds": [round(x, 4) for x in info["phase_seconds"]],
+                        "cell_kernel_cells_per_s": M3 / max(info["phase_seconds"][2], 1e-9),
+                        "host_fallback_cells": info["host_fallback_cells"],
+                        "host_builder_seconds": round(host_sec, 3), "timing": "wall clock, host and device"},
                 roofline=None, e2e=None)
     print(json.dumps(line), flush=True)
 
