@@ -711,3 +711,39 @@ def test_tie_examples(case):
     cells, lens = tr.segments(0)
     assert [int(c) for c in cells] == [e[0] for e in case["segments"]]
     np.testing.assert_allclose(lens, [e[1] for e in case["segments"]], rtol=1e-12)
+
+
+def test_degenerate_fuzz_cases_hold_the_invariants():
+    """The oracle on the seeded degenerate grids of the GPU fuzz test
+    (lattices, coplanar sites, near-duplicate pairs, sites on the walls,
+    odd boxes; rays from sites, from walls and along the axes): every path
+    ends on the box (summed length = slab length, numpy ray-box test), and
+    away from near ties every segment's midpoint is nearest (numpy brute
+    force) to the site of its cell, with the cells summing to the box's
+    volume."""
+    from tests import fuzz_cases
+    for i in range(0, 120, 3):
+        kind, g, rays = fuzz_cases.case(i)
+        c = oracle.cells(g.sites, g.box)
+        np.testing.assert_allclose(c.vol.sum(), np.prod(g.box[3:] - g.box[:3]), rtol=1e-10)
+        off, idx = oracle.csr(c, len(g.sites))
+        tr = oracle.trace(g.sites, g.box, g.rho.astype(np.float64), rays.origin, rays.dir, off=off, idx=idx)
+        assert np.all(tr.status == 0), (i, kind)
+        diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+        np.testing.assert_allclose(tr.length, slab_length(g.box, rays.origin, rays.dir), rtol=0, atol=1e-12 * diag,
+                                   err_msg=f"case {i} ({kind})")
+        mids, owners = [], []
+        for r in np.nonzero(tr.near_tie == 0)[0]:
+            cells, lens = tr.segments(r)
+            t = np.concatenate([[0.0], np.cumsum(lens)])
+            for a in range(cells.size):
+                if lens[a] > 1e-9 * diag:
+                    mids.append(rays.origin[r] + 0.5 * (t[a] + t[a + 1]) * rays.dir[r])
+                    owners.append(cells[a])
+        if mids:
+            got = nearest_site(g.sites, np.array(mids))
+            own = np.array(owners)
+            # an equidistant midpoint (a segment along a face) may pick either site
+            d_got = np.linalg.norm(np.array(mids) - g.sites[got], axis=1)
+            d_own = np.linalg.norm(np.array(mids) - g.sites[own], axis=1)
+            assert np.all((got == own) | (d_own - d_got <= 1e-12 * diag)), f"case {i} ({kind})"
