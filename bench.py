@@ -248,9 +248,9 @@ def _rel_stats(x):
     return {"max": float(x.max()), "p99": float(np.quantile(x, 0.99)), "mean": float(x.mean())}
 
 
-def cpu_baseline(g, rays, tau32, tau64, target_s=10.0):
+def cpu_baseline(g, rays, tau32, tau64, target_s=10.0, tau32x=None):
     """The oracle timed on a bounded seeded sample of the workload's rays
-    (about target_s of CPU time, all rays if they fit), and the tau of both
+    (about target_s of CPU time, all rays if they fit), and the tau of the
     GPU forms on those rays against the oracle's."""
     off, idx, setup_s = oracle_setup(g)
     n = 2000
@@ -277,6 +277,9 @@ def cpu_baseline(g, rays, tau32, tau64, target_s=10.0):
            "fp32_tau_rel_err_incl_near_ties": _rel_stats(rel32[pos]),
            "fp32_rays_over_1e-5": int((rel32[ok] > TAU32_REL).sum()),
            "oracle_fallbacks": int(tr.nfallback.sum())}
+    if tau32x is not None:
+        relx = np.abs(tau32x[sel].astype(np.float64) - tr.tau) / np.maximum(tr.tau, 1e-300)
+        acc["fp32_exact_tau_rel_err"] = _rel_stats(relx[ok])
     return base, acc
 
 
@@ -447,6 +450,10 @@ def main():
     gpu_launches = timed.kernels
     k64 = max(3, args.steps // 4)
     step64_ms, _, tr64_ms, launches64 = timed("fp64", tau64, k64, 2)
+    # the float32 form with exact lengths (same decisions, float-pair lengths)
+    tau32x = torch.empty(N, dtype=torch.float32, device=dev)
+    kx = max(3, args.steps // 2)
+    stepx_ms, _, trx_ms, launchesx = timed("fp32_exact", tau32x, kx, 2)
 
     # accuracy of the float32 form against the float64 form on these rays
     t32 = tau.double()
@@ -495,6 +502,7 @@ def main():
 
     step_ms_max = reduce_max(step_ms)
     step64_max = reduce_max(step64_ms)
+    stepx_max = reduce_max(stepx_ms)
     e2e_max = reduce_max(e2e_ms)
     seg_all = reduce_sum(float(crossings))
     rays_all = reduce_sum(float(N))
@@ -525,6 +533,10 @@ def main():
         "fp64_form": {"value": value64, "unit": UNIT, "ms_per_step": step64_max / k64,
                       "trace_ms_per_launch": tr64_ms / max(launches64, 1)},
         "fp32_over_fp64": value / value64,
+        "fp32_exact_form": {"value": seg_all * kx / (stepx_max / 1e3), "unit": UNIT, "ms_per_step": stepx_max / kx,
+                            "trace_ms_per_launch": trx_ms / max(launchesx, 1),
+                            "lengths": "float32 decisions, each crossing's length from the exact site difference "
+                                       "in float-pair arithmetic"},
         "tau_rel_err_vs_fp64": tau_err,
         "stats_per_step": st32,
         "recheck_rate": st32["rechecks"] / max(st32["decisions"], 1),
@@ -535,13 +547,13 @@ def main():
         "clocks": clocks,
     }
     if ws == 1 and not args.no_cpu_baseline:
-        base, acc = cpu_baseline(g, rays, tau.cpu().numpy(), tau64.cpu().numpy())
+        base, acc = cpu_baseline(g, rays, tau.cpu().numpy(), tau64.cpu().numpy(), tau32x=tau32x.cpu().numpy())
         acc.update({"gpu_recheck_rate": st32["rechecks"] / max(st32["decisions"], 1),
                     "gpu_fallbacks_fp32": st32["fallbacks"], "gpu_fallbacks_fp64": st64["fallbacks"]})
         line["cpu_baseline"] = base
         line["accuracy"] = acc
     if ws == 1 and not args.no_other_configs:
-        del O, D, tau, tau64, Oh, Dh, Th
+        del O, D, tau, tau64, tau32x, Oh, Dh, Th
         del vg
         torch.cuda.empty_cache()
         other = {}

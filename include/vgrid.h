@@ -54,10 +54,18 @@ enum {
 
 /* arithmetic of the exit search */
 enum {
-    VGRID_FP64 = 0,        /* Eq. 1-5 in float64, as written */
-    VGRID_FP32_RECHECK = 1 /* float32 plane tests with error bounds; a crossing
-                              whose two nearest exits are not separated by the
-                              bounds is recomputed in float64 */
+    VGRID_FP64 = 0,         /* Eq. 1-5 in float64, as written */
+    VGRID_FP32_RECHECK = 1, /* float32 plane tests with error bounds; a crossing
+                               whose two nearest exits are not separated by the
+                               bounds is recomputed in float64. A crossing's
+                               length is num/den in float32, its end point
+                               placed to within about 12 u N^2 / (n.k) (u =
+                               2^-24, N the cell's largest |n|_1) */
+    VGRID_FP32_EXACT = 2    /* the decisions of VGRID_FP32_RECHECK, and each
+                               crossing's length from the exact site
+                               difference in float-pair arithmetic (within a
+                               few u); vgrid_trace only, one lane per ray
+                               (the launch's lanes_per_ray is not used) */
 };
 
 /* what vgrid_trace writes */
@@ -240,7 +248,8 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
  *   origin, dir   device float64[N*3]; every dir must have unit length
  *                 within 1e-6 (checked on the device: such a ray gets tau 0,
  *                 no segments and status VGRID_RAY_BAD_DIR).
- *   precision     VGRID_FP64 or VGRID_FP32_RECHECK.
+ *   precision     VGRID_FP64, VGRID_FP32_RECHECK or VGRID_FP32_EXACT (the
+ *                 latter's tau and lengths are float32, as FP32_RECHECK's).
  *   output        VGRID_TAU or VGRID_SEGMENTS, optionally | VGRID_ENTER
  *                 (segments, tau and lengths then start at the entry point;
  *                 needs a work buffer of N*3 doubles, grown like the others).

@@ -23,7 +23,7 @@ from ._lib import VGridError, check, load
 
 __all__ = ["VoronoiGrid", "Batch", "TraceResult", "optical_depth", "probe_l2", "VGridError", "load"]
 
-_PREC = {"fp64": _lib.FP64, "fp32": _lib.FP32_RECHECK}
+_PREC = {"fp64": _lib.FP64, "fp32": _lib.FP32_RECHECK, "fp32_exact": _lib.FP32_EXACT}
 
 
 def _stream(stream=None):

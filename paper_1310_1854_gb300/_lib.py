@@ -31,6 +31,7 @@ ERROR_NAMES = {ERR_ARG: "ARG", ERR_DUP_SITE: "DUP_SITE", ERR_OUTSIDE: "OUTSIDE",
 
 FP64 = 0
 FP32_RECHECK = 1
+FP32_EXACT = 2
 TAU = 0
 SEGMENTS = 1
 ENTER = 0x100

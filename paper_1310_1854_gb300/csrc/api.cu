@@ -1052,7 +1052,8 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
                 vgrid_stats *stats, vgrid_stream_t stream) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
-    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK && precision != VGRID_FP32_EXACT)
+        return fail(VGRID_ERR_ARG, "bad precision");
     const bool enter = (output & VGRID_ENTER) != 0;
     output &= ~VGRID_ENTER;
     if (output != VGRID_TAU && output != VGRID_SEGMENTS) return fail(VGRID_ERR_ARG, "bad output");
@@ -1078,13 +1079,16 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     const int fp64 = precision == VGRID_FP64;
     vgrid_launch L = g->launch;
     if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+    if (precision == VGRID_FP32_EXACT) L.lanes_per_ray = 1;
     const vg::KernelSet &ks = kernels(L.lanes_per_ray);
+    // the kernel table's row: float32, float64, float32 with exact lengths
+    const int row = precision == VGRID_FP32_EXACT ? 2 : fp64;
     RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
     {
-        const void *fn = ks.fn[fp64][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_SEGS];
+        const void *fn = ks.fn[row][output == VGRID_TAU ? vg::MODE_TAU : vg::MODE_SEGS];
         if ((rc = locate_start(g, fn, L, N, &order, s, fp64 != 0))) return rc;
     }
     mark(g, 0, 1, s);
@@ -1100,7 +1104,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     a.s1 = set;
     if (output == VGRID_TAU) {
         mark(g, 1, 0, s);
-        if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], L, g->sms, N, a, s))) return rc;
+        if ((rc = launch_trace(ks.fn[row][vg::MODE_TAU], L, g->sms, N, a, s))) return rc;
         mark(g, 1, 1, s);
         if (stats) return read_stats(g->d_stats, stats, s);
         return VGRID_OK;
@@ -1111,7 +1115,7 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     // fills or starts (at most cap / kSegChunk + min(N, cap) when the total
     // fits the capacity) plus the page each warp may leave unused, so it
     // never runs out when the segments fit the caller's buffers.
-    const void *fn = ks.fn[fp64][vg::MODE_SEGS];
+    const void *fn = ks.fn[row][vg::MODE_SEGS];
     int64_t chunks = 0;
     if (seg_capacity > 0) {
         const int64_t warps = (int64_t)persistent_blocks(fn, L, g->sms, N) * L.block / 32;

@@ -52,7 +52,9 @@ struct TraceArgs {
 // fn[fp64][mode]: single-grid trace kernels of one lanes-per-ray value
 // (nullptr if absent); batch: the float32 tau kernel over many grids
 struct KernelSet {
-    const void *fn[2][NUM_MODES];
+    // fn[0]: float32 form, fn[1]: float64 form, fn[2]: float32 form with
+    // exact lengths (one lane per ray only)
+    const void *fn[3][NUM_MODES];
     const void *batch;
 };
 

@@ -118,6 +118,66 @@ __device__ __forceinline__ float local_coord(float R0h, float R0l, float Kh, flo
     return __fadd_rn(__fadd_rn(ah, bh), small);
 }
 
+// a b = p + e exactly (fused multiply-add)
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (hi, lo) += (xh, xl)
+__device__ __forceinline__ void ff_add2(float &hi, float &lo, float xh, float xl) {
+    float s, e;
+    two_sum(hi, xh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, xl));
+    fast_two_sum(s, e, hi, lo);
+}
+
+// The length of a crossing through the bisector of the current site p and
+// the winner's site q (Eq. 4), for the float32 form with exact lengths:
+// n = q - p exactly as float pairs (both are float32 values), r = (R0 + t K)
+// - p, w = n/2 - r and the dot products n.w and n.k in float-pair
+// arithmetic, then one corrected division. The result is within a few u of
+// the exact length unless n.w cancels to a few u^2 |n||w| (a step that
+// starts on the plane), where it is within that absolute amount.
+__device__ __forceinline__ void exact_length(float4 q, float px, float py, float pz, const float *R0h,
+                                             const float *R0l, const float *Kh, const float *Kl, float th, float tl,
+                                             float &len_h, float &len_l) {
+    const float qc[3] = {q.x, q.y, q.z}, pc[3] = {px, py, pz};
+    float numh = 0.f, numl = 0.f, denh = 0.f, denl = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float nh, nl;
+        two_sum(qc[c], -pc[c], nh, nl);                    // n = q - p, exact
+        float ah, al, bh, bl, sh, se;
+        two_sum(R0h[c], -pc[c], ah, al);                   // R0_hi - p, exact
+        two_prod(th, Kh[c], bh, bl);                       // t_hi K_hi, exact
+        two_sum(ah, bh, sh, se);
+        const float small = __fadd_rn(__fadd_rn(__fadd_rn(al, bl), R0l[c]),
+                                      __fmaf_rn(th, Kl[c], __fmul_rn(tl, Kh[c])));
+        float rh, rl;
+        fast_two_sum(sh, __fadd_rn(se, small), rh, rl);    // r
+        float wh, we;
+        two_sum(__fmul_rn(0.5f, nh), -rh, wh, we);          // w = n/2 - r
+        float wl;
+        fast_two_sum(wh, __fadd_rn(we, __fsub_rn(__fmul_rn(0.5f, nl), rl)), wh, wl);
+        float ph, pe;
+        two_prod(nh, wh, ph, pe);                          // n.w term
+        pe = __fadd_rn(pe, __fmaf_rn(nh, wl, __fmul_rn(nl, wh)));
+        ff_add2(numh, numl, ph, pe);
+        two_prod(nh, Kh[c], ph, pe);                       // n.k term
+        pe = __fadd_rn(pe, __fmaf_rn(nh, Kl[c], __fmul_rn(nl, Kh[c])));
+        ff_add2(denh, denl, ph, pe);
+    }
+    const float q1 = __fdiv_rn(numh, denh);
+    float rem = __fmaf_rn(-q1, denh, numh);
+    rem = __fadd_rn(rem, __fmaf_rn(-q1, denl, numl));
+    fast_two_sum(q1, __fdiv_rn(rem, denh), len_h, len_l);
+    if (!(len_h > 0.0f)) {
+        len_h = 0.0f;
+        len_l = 0.0f;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // cell blocks
 // ---------------------------------------------------------------------------
@@ -688,14 +748,17 @@ __device__ __forceinline__ int find_set(const RaySetDev *sets, int nsets, int64_
 // by the FP64 pipe, is left alone (80 registers; held to 72 it was slower).
 // The per-ray values that a crossing of the float32 form reads once live in
 // shared memory, which is what lets the float32 instances fit.
-template <bool FP64, int MODE, bool BATCH>
+template <bool FP64, int MODE, bool BATCH, bool XL>
 constexpr int trace_max_regs() {
-    return FP64 ? (MODE == MODE_SEGS ? 80 : 255) : (BATCH || MODE == MODE_SEGS) ? 80 : 72;
+    return FP64 ? (MODE == MODE_SEGS ? 80 : 255) : (BATCH || MODE == MODE_SEGS || XL) ? 80 : 72;
 }
 
-template <int LPR, bool FP64, int MODE, bool BATCH>
-__global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, BATCH>())) trace_kernel(TraceArgs a) {
+// XL: the float32 form with exact lengths (one lane per ray): decisions as
+// in the float32 form, each crossing's length from exact_length.
+template <int LPR, bool FP64, int MODE, bool BATCH, bool XL = false>
+__global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, BATCH, XL>())) trace_kernel(TraceArgs a) {
     static_assert(LPR == 1 || LPR == 2 || LPR == 4 || LPR == 8, "lanes per ray");
+    static_assert(!XL || (LPR == 1 && !FP64 && !BATCH), "exact lengths: float32 form, one lane per ray");
     const int lane = threadIdx.x & 31;
     const int gl = lane & (LPR - 1);
     const int gbase = lane & ~(LPR - 1);
@@ -946,6 +1009,7 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
         double s64 = 0.0;      // float64 length (float64 form or recheck)
         bool from64 = FP64;
         float len = 0.f;
+        float len_lo = 0.f;    // exact lengths: the low word of the length
         bool found = false;    // an exit was found
         bool to_wall = false;  // ... and it is a wall
         int nextB = 0;         // block offset of the next cell (same form as B)
@@ -1028,8 +1092,15 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
                     len = fmaxf(sw, 0.0f);
                     to_wall = true;
                 } else {
-                    // den > dden > 0 here; 2-ulp division (the length only feeds tau and t)
-                    len = __fdividef(fmaxf(w1.num, 0.0f), w1.den);
+                    if (XL) {
+                        // the winner's site heads its block
+                        const float R0h[3] = {R0h_(0), R0h_(1), R0h_(2)}, R0l[3] = {R0l_(0), R0l_(1), R0l_(2)};
+                        const float Kl[3] = {Kl_(0), Kl_(1), Kl_(2)};
+                        exact_length(__ldg(h.rel + rec_w(qw)), pmx, pmy, pmz, R0h, R0l, Kh, Kl, th, tl, len, len_lo);
+                    } else {
+                        // den > dden > 0 here; 2-ulp division (the length only feeds tau and t)
+                        len = __fdividef(fmaxf(w1.num, 0.0f), w1.den);
+                    }
                     nextB = rec_w(qw);
                 }
             } else {
@@ -1092,7 +1163,8 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
             tauc = __fsub_rn(__fsub_rn(tt, tau32), y);
             tau32 = tt;
             zrun = 0;
-            ff_add(th, tl, len);
+            if (XL) ff_add2(th, tl, len, len_lo);
+            else ff_add(th, tl, len);
             B = nextB;
             continue;
         }
@@ -1155,6 +1227,8 @@ __global__ void __launch_bounds__(256) __maxnreg__((trace_max_regs<FP64, MODE, B
                 for (int c = 0; c < 3; c++) r64[c] = __dadd_rn(r64[c], __dmul_rn(s64, k64[c]));
             } else if (from64) {
                 ff_add_double(th, tl, s64);
+            } else if (XL) {
+                ff_add2(th, tl, len, len_lo);
             } else {
                 ff_add(th, tl, len);
             }

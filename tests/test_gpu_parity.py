@@ -1124,3 +1124,44 @@ def test_fuzz_gpu_cell_construction():
         ok = np.nonzero(ref.near_tie == 0)[0]
         t32 = vg.trace(dev(rays.origin), dev(rays.dir), precision="fp32").tau.cpu().numpy().astype(np.float64)[ok]
         assert np.all(np.abs(t32 - ref.tau[ok]) <= TAU32_REL * ref.tau[ok]), f"case {i} ({kind})"
+
+
+def test_fp32_exact_lengths():
+    """The float32 form with exact lengths: the float32 form's decisions (the
+    same cells) and each crossing's length from the exact site difference in
+    float-pair arithmetic, so that tau and every length are within 1e-6 of
+    the oracle's (relative; 1e-12 of the diagonal for lengths below 1e-6 of
+    it), on the first workload, small disk and clumpy grids and the seeded
+    degenerate grids, including the grazing exit that puts the plain float32
+    form's tau 1.8e-5 off."""
+    from tests import fuzz_cases
+    cases = [("config1",) + gen.config1(3000), ("disk", gen.make_disk_grid(20_000, 101), gen.disk_rays(3000, 102)),
+             ("clumpy", gen.make_clumpy_grid(20_000, 103, n_clumps=40), gen.uniform_rays(3000, 104))]
+    cases += [("fuzz %d" % i,) + fuzz_cases.case(i)[1:] for i in range(0, 120, 4)] + [("fuzz 17",) + fuzz_cases.case(17)[1:]]
+    worst = 0.0
+    for name, g, rays in cases:
+        ref = oracle_full(g, rays)
+        vg = make(g)
+        diag = float(np.linalg.norm(g.box[3:] - g.box[:3]))
+        O, D = dev(rays.origin), dev(rays.dir)
+        ok = np.nonzero(ref.near_tie == 0)[0]
+        rx = vg.trace(O, D, precision="fp32_exact", segments=True, status=True)
+        r32 = vg.trace(O, D, precision="fp32", segments=True)
+        np.testing.assert_array_equal(rx.status.cpu().numpy(), ref.status, err_msg=name)
+        try:
+            check_segments(ref, ok, rx.seg_off, rx.seg_cell, rx.seg_len, diag, 1e-6)
+        except AssertionError as e:
+            raise AssertionError(f"{name}: {e}")
+        # the same decisions as the float32 form: the same cells on every ray
+        np.testing.assert_array_equal(rx.seg_off.cpu().numpy(), r32.seg_off.cpu().numpy(), err_msg=name)
+        np.testing.assert_array_equal(rx.seg_cell.cpu().numpy(), r32.seg_cell.cpu().numpy(), err_msg=name)
+        tx = rx.tau.cpu().numpy().astype(np.float64)[ok]
+        rt = ref.tau[ok]
+        err = np.abs(tx - rt) / np.maximum(rt, 1e-300)
+        assert np.all(err[rt > 0] <= 1e-6), f"{name}: max rel tau error {err.max()}"
+        worst = max(worst, float(err[rt > 0].max(initial=0.0)))
+    assert tx.dtype == np.float64 and worst <= 1e-6
+    # only vgrid_trace takes it
+    from paper_1310_1854_gb300 import VGridError
+    with pytest.raises(VGridError):
+        vg.locate(O, precision="fp32_exact")
