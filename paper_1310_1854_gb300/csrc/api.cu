@@ -1038,9 +1038,8 @@ int vgrid_locate(vgrid_t *g, const double *pts, int64_t N, int precision, int32_
     if (N == 0) return VGRID_OK;
     DeviceGuard dg(g->device);
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = ensure_start(g, N);
-    if (rc) return rc;
-    RaySetDev set{pts, pts, nullptr, nullptr, g->d_start, N, 0, 0, 0};
+    // the cells go straight to `cell`: no start records
+    RaySetDev set{pts, pts, nullptr, nullptr, nullptr, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     VG_CUDA(vg::launch_locate(g->d_desc, g->d_set, 1, N,
                               precision == VGRID_FP32_RECHECK ? vg::PREP_CELL32 : vg::PREP_CELL64, cell, g->sms, s));

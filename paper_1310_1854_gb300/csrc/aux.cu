@@ -40,7 +40,8 @@ cudaError_t launch_prepare(RaySetDev *d_set, const RaySetDev &set, unsigned long
 }
 
 // Start records for every ray of every set. PREP_CELL32 / PREP_CELL64: C(r0)
-// only (the cell), with float32 (rechecked) or float64 distances;
+// only, written as the caller's id to out_caller (no start record), with
+// float32 (rechecked) or float64 distances;
 // PREP_FP32: float32 form (cell, direction check, wall exit of Eq. 5 and the
 // float pairs of origin and direction); PREP_FP64: float64 form (cell and
 // direction check). The caller's id of the cell goes to out_caller if given.
@@ -62,16 +63,13 @@ __global__ void __launch_bounds__(256, 5) locate_kernel(const GridDev *grids, co
         const GridDev *gp = grids + rs.grid;
         const double *o = rs.origin + 3 * li;
         const LocPt P = loc_point(__ldg(o), __ldg(o + 1), __ldg(o + 2));
-        RayPrep *out = rs.start + li;
         // float32 distances with the proven float64 fallback give exactly the
         // float64 argmin, so both traversal forms start that way; only
         // vgrid_locate's float64 mode (PREP_CELL64) scans in float64
         int m = locate_point<true>(gp, P, prep != PREP_CELL64, nullptr);
         if (out_caller) out_caller[w] = m >= 0 ? __ldg(&gp->perm[m]) : -1;
-        if (prep == PREP_CELL32 || prep == PREP_CELL64) {
-            out->cell = m;
-            continue;
-        }
+        if (prep == PREP_CELL32 || prep == PREP_CELL64) continue;
+        RayPrep *out = rs.start + li;
         const double *d = rs.dir + 3 * li;
         const double k[3] = {__ldg(d), __ldg(d + 1), __ldg(d + 2)};
         RayPrep p;
