@@ -64,8 +64,10 @@ enum {
     VGRID_FP32_EXACT = 2    /* the decisions of VGRID_FP32_RECHECK, and each
                                crossing's length from the exact site
                                difference in float-pair arithmetic (within a
-                               few u); vgrid_trace only, one lane per ray
-                               (the launch's lanes_per_ray is not used) */
+                               few u); float32 results as FP32_RECHECK's.
+                               vgrid_trace, vgrid_trace_host and
+                               vgrid_trace_noalloc take it, with one lane per
+                               ray (the launch's lanes_per_ray is not used) */
 };
 
 /* what vgrid_trace writes */
@@ -305,8 +307,8 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
  * traversal runs. Host buffers should be page-locked for the copies to
  * overlap; pageable buffers work, serialised.
  *   origin, dir   host float64[N*3], unit directions as for vgrid_trace
- *   precision     VGRID_FP64 or VGRID_FP32_RECHECK
- *   tau           host float64[N] (FP64) or float32[N] (FP32_RECHECK)
+ *   precision     VGRID_FP64, VGRID_FP32_RECHECK or VGRID_FP32_EXACT
+ *   tau           host float64[N] (FP64) or float32[N] (the float32 forms)
  *   ray_status    host int32[N] or NULL
  *   chunk         rays per chunk; 0 = N. A traversal launch lasts at least
  *                 as long as its longest ray, so chunks only pay off for rays
@@ -447,7 +449,7 @@ int vgrid_read_timing(vgrid_t *g, double *locate_ms, double *trace_ms, int64_t *
  * has no counterpart; this is a variant of vgrid_trace in VGRID_TAU mode.
  *
  * Same arguments and results as vgrid_trace with output VGRID_TAU (tau is
- * float64[N] for VGRID_FP64, float32[N] for VGRID_FP32_RECHECK; ray_status
+ * float64[N] for VGRID_FP64, float32[N] for the float32 forms; ray_status
  * nullable), but its work buffers (start cells, work counter, counters) live
  * in one fixed device array of VGRID_NOALLOC_SCRATCH_BYTES inside the
  * library, which every GPU that loads the library holds until the process

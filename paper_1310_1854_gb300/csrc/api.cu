@@ -932,20 +932,35 @@ int locate_start(vgrid_t *g, const void *fn, const vgrid_launch &l, int64_t N, c
     return VGRID_OK;
 }
 
+// the kernel table's row for a precision (float32, float64, float32 with
+// exact lengths) and the launch shape it runs with
+static int precision_row(int precision, vgrid_launch &L) {
+    if (precision == VGRID_FP64) {
+        if (L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+        return 1;
+    }
+    if (precision == VGRID_FP32_EXACT) {
+        L.lanes_per_ray = 1;
+        return 2;
+    }
+    return 0;
+}
+
 // tau (and status) of n device-resident rays on s; the counters restart
 // only if reset_stats
-int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t n, int fp64, void *tau,
+int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t n, int precision, void *tau,
                     int32_t *status, bool reset_stats, cudaStream_t s) {
     int rc = ensure_start(g, n);
     if (rc) return rc;
     vgrid_launch L = g->launch;
-    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
+    const int fp64 = precision == VGRID_FP64;
+    const int row = precision_row(precision, L);
     const vg::KernelSet &ks = kernels(L.lanes_per_ray);
     RaySetDev set{origin, dir, tau, status, g->d_start, n, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, reset_stats ? g->d_stats : nullptr, s));
     mark(g, 0, 0, s);
     const int32_t *order = nullptr;
-    if ((rc = locate_start(g, ks.fn[fp64][vg::MODE_TAU], L, n, &order, s, fp64 != 0))) return rc;
+    if ((rc = locate_start(g, ks.fn[row][vg::MODE_TAU], L, n, &order, s, fp64 != 0))) return rc;
     mark(g, 0, 1, s);
     vg::TraceArgs a{};
     a.grids = g->d_desc;
@@ -958,7 +973,7 @@ int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t
     a.s1 = set;
     a.order = order;
     mark(g, 1, 0, s);
-    if ((rc = launch_trace(ks.fn[fp64][vg::MODE_TAU], L, g->sms, n, a, s))) return rc;
+    if ((rc = launch_trace(ks.fn[row][vg::MODE_TAU], L, g->sms, n, a, s))) return rc;
     mark(g, 1, 1, s);
     return VGRID_OK;
 }
@@ -969,11 +984,12 @@ int trace_tau_chunk(vgrid_t *g, const double *origin, const double *dir, int64_t
 // pass of one chunk can thus run while the previous chunk is traced, in the
 // SMs that traversal frees in its tail. The counters are not reset (calls
 // that read them take trace_tau_chunk instead).
-int trace_chunk_slot(vgrid_t *g, int k, const double *origin, const double *dir, int64_t n, int fp64, void *tau,
+int trace_chunk_slot(vgrid_t *g, int k, const double *origin, const double *dir, int64_t n, int precision, void *tau,
                      int32_t *status, cudaStream_t s) {
     vgrid_launch L = g->launch;
-    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
-    const void *fn = kernels(L.lanes_per_ray).fn[fp64][vg::MODE_TAU];
+    const int fp64 = precision == VGRID_FP64;
+    const int row = precision_row(precision, L);
+    const void *fn = kernels(L.lanes_per_ray).fn[row][vg::MODE_TAU];
     cudaStream_t t = g->s_loc;
     VG_CUDA(cudaStreamWaitEvent(t, g->ev_in[k], 0));
     VG_CUDA(cudaStreamWaitEvent(t, g->ev_k[k], 0));
@@ -1077,11 +1093,8 @@ int vgrid_trace(vgrid_t *g, const double *origin, const double *dir, int64_t N, 
     }
     const int fp64 = precision == VGRID_FP64;
     vgrid_launch L = g->launch;
-    if (fp64 && L.fp64_lanes_per_ray) L.lanes_per_ray = L.fp64_lanes_per_ray;
-    if (precision == VGRID_FP32_EXACT) L.lanes_per_ray = 1;
+    const int row = precision_row(precision, L);
     const vg::KernelSet &ks = kernels(L.lanes_per_ray);
-    // the kernel table's row: float32, float64, float32 with exact lengths
-    const int row = precision == VGRID_FP32_EXACT ? 2 : fp64;
     RaySetDev set{origin, dir, tau, ray_status, g->d_start, N, 0, 0, 0};
     VG_CUDA(vg::launch_prepare(g->d_set, set, g->d_queue, g->d_stats, s));
     mark(g, 0, 0, s);
@@ -1158,7 +1171,8 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
                      int32_t *ray_status, int64_t chunk, vgrid_stats *stats, vgrid_stream_t stream) {
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (g->device < 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
-    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK && precision != VGRID_FP32_EXACT)
+        return fail(VGRID_ERR_ARG, "bad precision");
     if (N < 0 || (N > 0 && (!origin || !dir || !tau))) return fail(VGRID_ERR_ARG, "bad rays or tau");
     if (chunk < 0) return fail(VGRID_ERR_ARG, "negative chunk");
     DeviceGuard dg(g->device);
@@ -1246,8 +1260,8 @@ int vgrid_trace_host(vgrid_t *g, const double *origin, const double *dir, int64_
         int32_t *out_st = direct ? (st_dev ? st_dev + first : nullptr) : (ray_status ? g->d_hst[k] : nullptr);
         // without counters to read, the chunk's start records are prepared
         // beside the previous chunk's traversal (trace_chunk_slot)
-        int rc = stats ? trace_tau_chunk(g, dO, dD, n, fp64, out_tau, out_st, c == 0, s)
-                       : trace_chunk_slot(g, k, dO, dD, n, fp64, out_tau, out_st, s);
+        int rc = stats ? trace_tau_chunk(g, dO, dD, n, precision, out_tau, out_st, c == 0, s)
+                       : trace_chunk_slot(g, k, dO, dD, n, precision, out_tau, out_st, s);
         if (rc) return rc;
         VG_CUDA(cudaEventRecord(g->ev_k[k], s));
         if (direct) continue;

@@ -61,7 +61,8 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
     vg::GridView v;
     if (!g) return fail(VGRID_ERR_ARG, "null grid");
     if (vg::grid_view(g, &v) != 0) return fail(VGRID_ERR_ARG, "grid was built with host_only");
-    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK) return fail(VGRID_ERR_ARG, "bad precision");
+    if (precision != VGRID_FP64 && precision != VGRID_FP32_RECHECK && precision != VGRID_FP32_EXACT)
+        return fail(VGRID_ERR_ARG, "bad precision");
     if (N < 0 || (N > 0 && (!origin || !dir || !tau))) return fail(VGRID_ERR_ARG, "bad rays or tau");
     if (N > VGRID_NOALLOC_MAX_RAYS)
         return fail(VGRID_ERR_ARG, "N = " + std::to_string(N) + " exceeds VGRID_NOALLOC_MAX_RAYS = " +
@@ -93,6 +94,7 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
             break;
         }
         if (fp64) v.lanes_per_ray = v.fp64_lanes_per_ray;
+        if (precision == VGRID_FP32_EXACT) v.lanes_per_ray = 1;  // its kernels take one lane per ray
         vg::KernelSet ks{};
         switch (v.lanes_per_ray) {
             case 1: vg::kernel_table_lpr1(ks); break;
@@ -100,7 +102,7 @@ extern "C" int vgrid_trace_noalloc(vgrid_t *g, const double *origin, const doubl
             case 8: vg::kernel_table_lpr8(ks); break;
             default: vg::kernel_table_lpr4(ks); break;
         }
-        const void *fn = ks.fn[fp64][vg::MODE_TAU];
+        const void *fn = ks.fn[precision == VGRID_FP32_EXACT ? 2 : fp64][vg::MODE_TAU];
         int per_sm = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, v.block, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;

@@ -699,15 +699,15 @@ def test_host_pipelined_trace_matches_device_trace():
     """vgrid_trace_host (rays and results in host memory, copies overlapped
     with the traversal) gives the tau, status and counters of vgrid_trace on
     the same rays: one chunk, several with a ragged last one, pageable
-    buffers, pinned rays with a pageable result, the float64 form, and calls
-    queued back to back."""
+    buffers, pinned rays with a pageable result, the float64 form and the
+    float32 form with exact lengths, and calls queued back to back."""
     g, rays = gen.config2(n_rays=300_000)
     vg = make(g)
     N = len(rays.origin)
     O, D = dev(rays.origin), dev(rays.dir)
     Oh = torch.from_numpy(rays.origin).pin_memory()
     Dh = torch.from_numpy(rays.dir).pin_memory()
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64", "fp32_exact"):
         ref = vg.trace(O, D, precision=prec, status=True, stats=True)
         rt, rs = ref.tau.cpu().numpy(), ref.status.cpu().numpy()
         for chunk in (0, 70_001, N):

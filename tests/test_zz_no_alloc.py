@@ -6,7 +6,7 @@ latency-bound loops that must not take the implicit synchronisation of
 cudaMalloc/cudaFree). Its work buffers live in a fixed device array inside
 the library. Called through the C-ABI, it must give what vgrid_trace gives
 in tau mode, to the bit, on two calls in a row (the second one sees the
-array as the first left it), in both arithmetic forms.
+array as the first left it), in every arithmetic form.
 """
 import ctypes
 
@@ -25,7 +25,7 @@ def _p(t):
 
 def test_noalloc_matches_trace_on_two_calls():
     """Same kernel, same start records: tau and status equal vgrid_trace's to
-    the bit, in both forms, on two calls in a row (the second sees the array
+    the bit, in every form, on two calls in a row (the second sees the array
     as the first left it), once without a status buffer."""
     from paper_1310_1854_gb300 import VoronoiGrid, _lib
     lib = _lib.load()
@@ -35,7 +35,8 @@ def test_noalloc_matches_trace_on_two_calls():
     O = torch.from_numpy(rays.origin).cuda()
     D = torch.from_numpy(rays.dir).cuda()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for prec, name, dt in ((_lib.FP32_RECHECK, "fp32", torch.float32), (_lib.FP64, "fp64", torch.float64)):
+    for prec, name, dt in ((_lib.FP32_RECHECK, "fp32", torch.float32), (_lib.FP64, "fp64", torch.float64),
+                           (_lib.FP32_EXACT, "fp32_exact", torch.float32)):
         # two calls in a row: all rays, then a shifted subset, so the second
         # call starts from the array the first one left behind; the second
         # passes no status buffer (NULL is allowed)
