@@ -380,14 +380,18 @@ class _OpticalDepth(torch.autograd.Function):
     """tau(rho) for fixed rays. Backward is the adjoint from the segment lists
     kept by forward (keep_segments), else the library's adjoint traversal.
     The adjoint uses the kappa of this forward call, whatever the grid holds
-    by the time backward runs (the paths do not depend on rho or kappa)."""
+    by the time backward runs (the paths do not depend on rho or kappa).
+    With precision "fp32_exact" the lengths of both passes come from the
+    float32 form with exact lengths (backward traces again with it when the
+    lists were not kept)."""
 
     @staticmethod
-    def forward(ctx, rho, grid, origin, direction, kappa, keep_segments):
+    def forward(ctx, rho, grid, origin, direction, kappa, keep_segments, precision):
         grid.set_density(rho.detach().to(torch.float32).contiguous(), kappa)
-        res = grid.trace(origin, direction, precision="fp32", segments=keep_segments)
+        res = grid.trace(origin, direction, precision=precision, segments=keep_segments)
         ctx.grid = grid
         ctx.kappa = float(kappa)
+        ctx.precision = precision
         ctx.res = res if keep_segments else None
         ctx.save_for_backward(origin, direction)
         return res.tau
@@ -400,7 +404,10 @@ class _OpticalDepth(torch.autograd.Function):
             d = grid.segments_grad(ctx.res, g, kappa=kappa)
         else:
             origin, direction = ctx.saved_tensors
-            if grid.kappa == kappa:
+            if ctx.precision != "fp32":
+                d = grid.segments_grad(grid.trace(origin, direction, precision=ctx.precision, segments=True), g,
+                                       kappa=kappa)
+            elif grid.kappa == kappa:
                 d = grid.trace_grad(origin, direction, g)
             elif grid.kappa != 0.0:
                 # the adjoint traversal multiplies by the grid's kappa
@@ -408,14 +415,18 @@ class _OpticalDepth(torch.autograd.Function):
             else:
                 d = grid.segments_grad(grid.trace(origin, direction, precision="fp32", segments=True), g,
                                        kappa=kappa)
-        return d, None, None, None, None, None
+        return d, None, None, None, None, None, None
 
 
 def optical_depth(grid: VoronoiGrid, rho: torch.Tensor, origin: torch.Tensor, direction: torch.Tensor,
-                  kappa: float = 1.0, keep_segments: bool = True) -> torch.Tensor:
+                  kappa: float = 1.0, keep_segments: bool = True, precision: str = "fp32") -> torch.Tensor:
     """Differentiable tau per ray with respect to the per-cell densities rho.
 
     With keep_segments (default) forward keeps the segment lists (8 bytes per
     segment on the device until backward) and backward reads them instead of
-    tracing the rays again; without, backward traces again."""
-    return _OpticalDepth.apply(rho, grid, origin, direction, kappa, bool(keep_segments))
+    tracing the rays again; without, backward traces again. precision:
+    "fp32" (the float32 form) or "fp32_exact" (the same cells, every length
+    from the exact site difference)."""
+    if precision not in ("fp32", "fp32_exact"):
+        raise ValueError("optical_depth takes precision 'fp32' or 'fp32_exact'")
+    return _OpticalDepth.apply(rho, grid, origin, direction, kappa, bool(keep_segments), precision)

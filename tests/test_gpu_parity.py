@@ -399,6 +399,19 @@ def test_gradient_matches_oracle():
     ((torch.exp(-tau2) - t) ** 2).sum().backward()
     gg2 = rho2.grad.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(gg2 - want) <= 1e-3 * wabs + 1e-30)
+    # with exact lengths: the oracle's tau to 1e-6 and the same gradient, the
+    # lists kept or traced again
+    for keep in (True, False):
+        rho3 = dev(g.rho).requires_grad_(True)
+        tau3 = optical_depth(vg, rho3, O, D, float(g.kappa), keep_segments=keep, precision="fp32_exact")
+        ok = ref.near_tie == 0
+        t3 = tau3.detach().cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(t3[ok] - ref.tau[ok]) <= 1e-6 * ref.tau[ok])
+        ((torch.exp(-tau3) - t) ** 2).sum().backward()
+        gg3 = rho3.grad.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gg3 - want) <= 1e-3 * wabs + 1e-30)
+    with pytest.raises(ValueError):
+        optical_depth(vg, rho3, O, D, 1.0, precision="fp64")
 
 
 def test_gradient_uses_the_forward_kappa():
