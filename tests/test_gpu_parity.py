@@ -892,6 +892,11 @@ def test_rays_entering_from_outside():
     t = t32.tau.cpu().numpy().astype(np.float64)[ok]
     assert np.all(np.abs(t - ref.tau[ok]) <= TAU32_REL * ref.tau[ok])
     assert np.all(t32.tau.cpu().numpy()[~hit] == 0)
+    # exact lengths from the entry points too
+    rx = vg.trace(dev(O), dev(D), precision="fp32_exact", segments=True, enter=True)
+    check_segments(ref, ok, rx.seg_off, rx.seg_cell, rx.seg_len, diag, 1e-6)
+    tx = rx.tau.cpu().numpy().astype(np.float64)[ok]
+    assert np.all(np.abs(tx - ref.tau[ok]) <= 1e-6 * ref.tau[ok])
 
 
 def test_sphere_domain_parity():
@@ -909,6 +914,12 @@ def test_sphere_domain_parity():
     L = np.add.reduceat(r64.seg_len.cpu().numpy(), so[:-1])
     end = rays.origin + L[:, None] * rays.dir
     np.testing.assert_allclose(np.linalg.norm(end, axis=1), 1.0, rtol=0, atol=1e-12)
+    # exact lengths in the ball too (the sphere's exit as the wall candidate)
+    rx = vg.trace(dev(rays.origin), dev(rays.dir), precision="fp32_exact", segments=True)
+    ok = np.nonzero(ref.near_tie == 0)[0]
+    check_segments(ref, ok, rx.seg_off, rx.seg_cell, rx.seg_len, 2.0 * np.sqrt(3.0), 1e-6)
+    tx = rx.tau.cpu().numpy().astype(np.float64)[ok]
+    assert np.all(np.abs(tx - ref.tau[ok]) <= 1e-6 * ref.tau[ok])
 
 
 def test_sphere_domain_locate_and_entry():
