@@ -19,6 +19,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# ORACLE_PKG: a folder holding a copy of the oracle package with one planted
+# mistake in its Python layer; it is imported in place of the real one
+if os.environ.get("ORACLE_PKG"):
+    sys.path.insert(0, os.environ["ORACLE_PKG"])
 
 import gen  # noqa: E402
 import oracle  # noqa: E402
@@ -215,9 +219,101 @@ def check_tie_examples():
         _segments_match(tr, 0, case["segments"])
 
 
+def check_exp_loss():
+    """The loss sum (e^-tau - t)^2 and its derivative, against a hand value
+    and central differences in tau."""
+    tau = np.array([0.0, 0.5, 2.0])
+    t = np.array([0.5, 0.25, 0.0])
+    loss, dL = oracle.exp_loss(tau, t)
+    e = np.exp(-tau)
+    np.testing.assert_allclose(loss, (1 - 0.5) ** 2 + (e[1] - 0.25) ** 2 + e[2] ** 2, rtol=1e-15)
+    h = 1e-6
+    for i in range(3):
+        tp = tau.copy(); tp[i] += h
+        tm = tau.copy(); tm[i] -= h
+        fd = (oracle.exp_loss(tp, t)[0] - oracle.exp_loss(tm, t)[0]) / (2 * h)
+        assert abs(fd - dL[i]) <= 1e-8, (i, fd, dL[i])
+
+
+def check_tau_grad_fd():
+    """dL/drho of the loss against central differences of the loss in rho
+    (through the traced tau), with kappa != 1; cells no ray crosses get 0."""
+    g, c, off, idx = _grid150()
+    rays = gen.uniform_rays(60, 149)
+    rho = g.rho.astype(np.float64)
+    tr = _trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3)
+    target = np.exp(-0.9 * tr.tau)
+    _, dL = oracle.exp_loss(tr.tau, target)
+    grad = oracle.tau_grad(tr, len(g.sites), dL, kappa=1.3)
+    hit = np.unique(np.concatenate([tr.segments(i)[0] for i in range(60)]))
+    for cidx in gen.rng_for(150).choice(hit, 4, replace=False):
+        hh = 1e-4 * rho[cidx]
+        rp = rho.copy(); rp[cidx] += hh
+        rm = rho.copy(); rm[cidx] -= hh
+        tp = _trace(g.sites, g.box, rp, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3).tau
+        tm = _trace(g.sites, g.box, rm, rays.origin, rays.dir, off=off, idx=idx, kappa=1.3).tau
+        fd = (oracle.exp_loss(tp, target)[0] - oracle.exp_loss(tm, target)[0]) / (2 * hh)
+        assert abs(fd - grad[cidx]) <= 1e-6 * max(abs(fd), 1e-8), (cidx, fd, grad[cidx])
+    assert np.all(grad[np.setdiff1d(np.arange(len(g.sites)), hit)] == 0.0)
+
+
+def check_enter_points():
+    """Entry points on the box by hand (a face, a corner, a ray pointing
+    away, a start inside) and on the unit ball (epsilon past the sphere,
+    along the ray; a ray that misses keeps its origin)."""
+    box = gen.CUBE_BOX
+    O = np.array([[-2.0, 0.1, 0.2], [0.5, 3.0, -0.25], [2.0, 2.0, 2.0], [-3.0, 0.0, 0.0], [0.1, 0.2, 0.3]])
+    D = np.array([[1.0, 0, 0], [0.0, -1, 0], [-1.0, -1, -1], [-1.0, 0, 0], [0.6, 0.8, 0.0]])
+    D = D / np.linalg.norm(D, axis=1)[:, None]
+    E = oracle.enter_points(box, O, D)
+    np.testing.assert_allclose(E[:3], [[-1.0, 0.1, 0.2], [0.5, 1.0, -0.25], [1.0, 1.0, 1.0]], rtol=1e-15)
+    np.testing.assert_array_equal(E[3:], O[3:])
+    big = np.array([-2.0, -2, -2, 2, 2, 2])
+    eps = 1e-12 * np.sqrt(48.0)     # 1e-12 |Dmax - Dmin| (R6) for this box
+    O = np.array([[-1.5, 0.0, 0.0], [1.5, 1.5, 0.0], [0.0, 0.0, 1.5], [0.2, 0.1, 0.0]])
+    D = np.array([[1.0, 0, 0], [1.0, 0, 0], [0.0, 0.6, -0.8], [1.0, 0, 0]])
+    E = oracle.enter_points(big, O, D, sphere=gen.UNIT_BALL)
+    np.testing.assert_allclose(E[0], [-1.0 + eps, 0, 0], rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(E[1], O[1])       # points away from the ball
+    # |(0, 0.6 s, 1.5 - 0.8 s)|^2 = 1 is s^2 - 2.4 s + 1.25 = 0; the ray enters at the smaller root
+    s = (2.4 - np.sqrt(2.4 ** 2 - 4 * 1.25)) / 2
+    np.testing.assert_allclose(E[2], O[2] + (s + eps) * D[2], rtol=0, atol=1e-14)
+    np.testing.assert_array_equal(E[3], O[3])       # already inside
+
+
+def check_interaction():
+    """Interaction sampling: the hand-worked two-cell path, the uniform
+    medium's closed form s = tau_int / (kappa rho), and conservation (what
+    the cells remove is what the packages lose)."""
+    S = np.array([[1.0, 1, 1], [3.0, 1, 1]])
+    box = np.array([0.0, 0, 0, 4, 4, 4])
+    rho = np.array([2.0, 3.0])
+    _, off, idx = _full(S, box)
+    tr = _trace(S, box, rho, np.array([[0.5, 1, 1]] * 2), np.array([[1.0, 0, 0]] * 2), off=off, idx=idx)
+    cell, s, ab, amb = oracle.interact(tr, rho, [4.0, 10.0], weight=[1.0, 2.0])
+    assert list(cell) == [1, -1]
+    np.testing.assert_allclose(s, [1.5 + 1.0 / 3.0, 3.5], rtol=1e-14)
+    np.testing.assert_allclose(ab, [(1 - np.exp(-3)) * 3.0, (np.exp(-3) - np.exp(-4)) + 2 * (np.exp(-3) - np.exp(-9))],
+                               rtol=1e-13)
+    g, c, off, idx = _grid150()
+    rays = gen.uniform_rays(100, 151)
+    rho = np.full(len(g.sites), 0.8)
+    tr = _trace(g.sites, g.box, rho, rays.origin, rays.dir, off=off, idx=idx, kappa=1.5)
+    rng = gen.rng_for(152)
+    tau_int = -np.log(rng.random(100))
+    w = rng.uniform(0.5, 2.0, 100)
+    cell, s, ab, amb = oracle.interact(tr, rho, tau_int, weight=w, kappa=1.5)
+    L = slab_length(g.box, rays.origin, rays.dir)
+    inside = tau_int < 1.2 * L
+    np.testing.assert_allclose(s[inside], tau_int[inside] / 1.2, rtol=1e-12)
+    np.testing.assert_allclose(s[~inside], L[~inside], rtol=1e-12)
+    np.testing.assert_allclose(ab.sum(), (w * (1 - np.exp(-np.minimum(tau_int, 1.2 * L)))).sum(), rtol=1e-12)
+
+
 CHECKS = [check_worked_examples, check_tie_examples, check_fallback_examples, check_sphere_examples, check_sphere_paths_end_on_sphere,
           check_lengths_and_bisectors, check_tau_closed_form, check_locate_brute_force, check_cells_brute_and_volume,
-          check_interior_cells_are_delaunay, check_lattice_is_dda]
+          check_interior_cells_are_delaunay, check_lattice_is_dda, check_exp_loss, check_tau_grad_fd, check_enter_points,
+          check_interaction]
 
 
 def run() -> list:

@@ -4,8 +4,12 @@ Each case plants one mistake in a copy of the oracle's C source (a sign, a
 dropped term, a swapped operand, a wrong index or bound, an off-by-one in a
 limit or a tie-break), builds it the way the oracle is built, and runs the
 fast pins of tests/oracle_checks.py against it in a child process (the
-library is chosen through ORACLE_LIB). Every mutant must fail at least one
-pin; the unchanged source must pass them all. CPU only.
+library is chosen through ORACLE_LIB). The numpy layer of the oracle (the
+gradient, the entry points, interaction sampling, the loss, the CSR lists)
+gets the same treatment: a copy of the package with one change is imported
+in place of the real one (ORACLE_PKG), over the unchanged C library. Every
+mutant must fail at least one pin; the unchanged sources must pass them
+all. CPU only.
 
 One plausible change is left out because no pin can see it: removing the
 clamp of a negative numerator (reading R3). The numerator of a plane ahead
@@ -23,6 +27,7 @@ import oracle
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "voronoi_oracle.c")
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
 
 # (name, text in the source, its replacement); each text occurs exactly once
 MUTANTS = [
@@ -69,11 +74,44 @@ MUTANTS = [
      "if (!((dx * dx + dy * dy) + dz * dz < sph[3] * sph[3])) return 0;"),
 ]
 
+# the same for the numpy layer (oracle/__init__.py)
+PY_MUTANTS = [
+    ("gradient without kappa", "w = (dL[:, None] * kappa * tr.seg_len)[mask]", "w = (dL[:, None] * tr.seg_len)[mask]"),
+    ("slab entry from the far plane", "t_in = max(t_in, min(t1, t2))", "t_in = max(t_in, max(t1, t2))"),
+    ("box test passes with one axis inside", "if np.all((r >= box[:3]) & (r <= box[3:])):",
+     "if np.any((r >= box[:3]) & (r <= box[3:])):"),
+    ("sphere entry at the far root", "t = q / (np.sqrt(disc) - b) + eps", "t = (np.sqrt(disc) - b) + eps"),
+    ("sphere entry without the epsilon", "t = q / (np.sqrt(disc) - b) + eps", "t = q / (np.sqrt(disc) - b)"),
+    ("epsilon from the summed extents, numpy layer", "return 1e-12 * float(np.linalg.norm(box[3:] - box[:3]))",
+     "return 1e-12 * float(np.sum(box[3:] - box[:3]))"),
+    ("interaction distance without 1/(kappa rho)", "s[i] = dist + (part / k if k > 0 else 0.0)",
+     "s[i] = dist + part"),
+    ("absorption not capped at tau_int", "absorbed[c] += w[i] * (np.exp(-tau) - np.exp(-ti[i]))",
+     "absorbed[c] += w[i] * (np.exp(-tau) - np.exp(-(tau + d)))"),
+    ("absorption without the weight", "absorbed[c] += w[i] * (np.exp(-tau) - np.exp(-(tau + d)))",
+     "absorbed[c] += (np.exp(-tau) - np.exp(-(tau + d)))"),
+    ("running distance not advanced", "            dist += l\n", ""),
+    ("loss derivative without the chain factor", "-2.0 * (e - t) * e", "-2.0 * (e - t)"),
+    ("loss derivative with the wrong sign", "-2.0 * (e - t) * e", "2.0 * (e - t) * e"),
+    ("CSR offsets shifted by one", "np.cumsum(deg, out=off[1:])", "np.cumsum(deg, out=off[:-1])"),
+]
 
-def _run_checks(lib):
+
+def _run_checks(lib, pkg=None):
     env = dict(os.environ, ORACLE_LIB=lib, ORACLE_THREADS="1")
+    env.pop("ORACLE_PKG", None)
+    if pkg:
+        env["ORACLE_PKG"] = pkg
     return subprocess.run([sys.executable, "-m", "tests.oracle_checks"], cwd=ROOT, env=env, capture_output=True,
                           text=True, timeout=600)
+
+
+def _py_check(tmpdir, name, text, lib):
+    pkg = os.path.join(tmpdir, name)
+    os.makedirs(os.path.join(pkg, "oracle"))
+    with open(os.path.join(pkg, "oracle", "__init__.py"), "w") as f:
+        f.write(text)
+    return _run_checks(lib, pkg)
 
 
 def _build_and_check(tmpdir, name, text):
@@ -94,18 +132,27 @@ def results(tmp_path_factory):
     for i, (name, old, new) in enumerate(MUTANTS):
         assert src.count(old) == 1, f"mutation site not found once: {name}"
         jobs[name] = src.replace(old, new)
-    workers = max(2, min(len(jobs), os.cpu_count() or 2))
+    py = open(PY_SRC).read()
+    py_jobs = {"py control": py}
+    for name, old, new in PY_MUTANTS:
+        assert py.count(old) == 1, f"mutation site not found once: {name}"
+        py_jobs[name] = py.replace(old, new)
+    lib = os.path.join(tmpdir, "control.so")
+    subprocess.check_call(oracle.compile_command(SRC, lib))
+    workers = max(2, min(len(jobs) + len(py_jobs), os.cpu_count() or 2))
     with concurrent.futures.ThreadPoolExecutor(workers) as ex:
         futs = {name: ex.submit(_build_and_check, tmpdir, f"m{i}", text) for i, (name, text) in enumerate(jobs.items())}
+        futs.update({name: ex.submit(_py_check, tmpdir, f"p{i}", text, lib) for i, (name, text) in enumerate(py_jobs.items())})
         return {name: f.result() for name, f in futs.items()}
 
 
-def test_unchanged_oracle_passes_the_checks(results):
-    r = results["control"]
+@pytest.mark.parametrize("name", ["control", "py control"])
+def test_unchanged_oracle_passes_the_checks(results, name):
+    r = results[name]
     assert r.returncode == 0, r.stdout + r.stderr
 
 
-@pytest.mark.parametrize("name", [m[0] for m in MUTANTS])
+@pytest.mark.parametrize("name", [m[0] for m in MUTANTS + PY_MUTANTS])
 def test_planted_mistake_is_caught(results, name):
     r = results[name]
     assert r.returncode != 0, f"no pin failed for: {name}\n{r.stdout}"
