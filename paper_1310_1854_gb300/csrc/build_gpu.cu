@@ -336,21 +336,37 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
         // near planes shrink the polyhedron, and with it the reach, so that
         // more of the far candidates drop out before they are cut. The
         // result is the same polyhedron up to rounding; only the work to
-        // reach it changes.
+        // reach it changes. A candidate is one 64-bit key, the distance's
+        // bits above the site index (non-negative floats order as their
+        // bits), and the buffer becomes a binary min-heap when it is
+        // drained, so each pick costs a walk down the heap rather than a
+        // scan of the whole buffer.
         constexpr int kBuf = 384;
-        float bd[kBuf];
-        int bq[kBuf];
+        unsigned long long bkey[kBuf];
         int nb = 0;
+        auto sift_down = [&](int i, unsigned long long v) {
+            for (;;) {
+                int c = 2 * i + 1;
+                if (c >= nb) break;
+                unsigned long long cv = bkey[c];
+                if (c + 1 < nb) {
+                    const unsigned long long c2 = bkey[c + 1];
+                    if (c2 < cv) { cv = c2; c++; }
+                }
+                if (v <= cv) break;
+                bkey[i] = cv;
+                i = c;
+            }
+            bkey[i] = v;
+        };
         auto flush = [&]() -> int {
+            for (int i = nb / 2 - 1; i >= 0; i--) sift_down(i, bkey[i]);
             while (nb > 0) {
-                int k = 0;
-                for (int i = 1; i < nb; i++)
-                    if (bd[i] < bd[k] || (bd[i] == bd[k] && bq[i] < bq[k])) k = i;
-                const float d2k = bd[k];
-                const int jj = bq[k];
+                const unsigned long long top = bkey[0];
                 nb--;
-                bd[k] = bd[nb];
-                bq[k] = bq[nb];
+                if (nb > 0) sift_down(0, bkey[nb]);
+                const float d2k = __uint_as_float((unsigned)(top >> 32));
+                const int jj = (int)(unsigned)top;
                 if (prefilter && d2k > R2f) {
                     nb = 0;  // the nearest left is out of reach: so are the others
                     break;
@@ -392,9 +408,7 @@ __global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, 
                             if (prefilter && d2f > R2f) continue;
                             if (nb == kBuf) fail = flush();
                             if (fail) break;
-                            bd[nb] = d2f;
-                            bq[nb] = jj;
-                            nb++;
+                            bkey[nb++] = ((unsigned long long)__float_as_uint(d2f) << 32) | (unsigned)jj;
                         }
                     }
                 }
