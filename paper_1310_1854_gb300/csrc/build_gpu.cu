@@ -168,30 +168,45 @@ __device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, d
         }
         if (!maybe) return 0;
     }
-    bool any_out = false;
+    // each vertex classified once: above the plane (fv > eps) and strictly
+    // below it (fv < -eps) as bits of two 128-bit masks held in registers,
+    // so that the face walk below reads neither fv nor the float64 pipe
+    static_assert(kNV <= 128, "vertex masks hold 128 bits");
+    unsigned long long out0 = 0ull, out1 = 0ull, str0 = 0ull, str1 = 0ull;
     for (int i = 0; i < P.nv; i++) {
-        W.fv[i] = nx * P.x[i] + ny * P.y[i] + nz * P.z[i] - d;
-        any_out |= W.fv[i] > eps;
+        const double f = nx * P.x[i] + ny * P.y[i] + nz * P.z[i] - d;
+        W.fv[i] = f;
+        const unsigned long long bit = 1ull << (i & 63);
+        const unsigned long long ob = f > eps ? bit : 0ull, sb = f < -eps ? bit : 0ull;
+        if (i < 64) {
+            out0 |= ob;
+            str0 |= sb;
+        } else {
+            out1 |= ob;
+            str1 |= sb;
+        }
     }
-    if (!any_out) return 0;
+    if (!(out0 | out1)) return 0;
+    auto is_out = [&](int v) { return ((v < 64 ? out0 >> v : out1 >> (v - 64)) & 1ull) != 0ull; };
+    auto is_strict = [&](int v) { return ((v < 64 ? str0 >> v : str1 >> (v - 64)) & 1ull) != 0ull; };
     int ne = 0, nseg = 0, nf2 = 0, nl2 = 0, nv = P.nv;
     for (int f = 0; f < P.nf; f++) {
         const int b = P.fbeg[f], k = P.flen[f];
         int out_count = 0;
-        for (int i = 0; i < k; i++) out_count += W.fv[P.L[b + i]] > eps;
+        for (int i = 0; i < k; i++) out_count += is_out(P.L[b + i]);
         if (out_count == k) continue;
         if (nf2 >= kNF) return -1;
         const int start = nl2;
         int entry = -1, exit_ = -1;
         for (int i = 0; i < k; i++) {
             const int va = P.L[b + i], vb = P.L[b + (i + 1) % k];
-            const bool ao = W.fv[va] > eps, bo = W.fv[vb] > eps;
+            const bool ao = is_out(va), bo = is_out(vb);
             if (!ao) {
                 if (nl2 >= kNL) return -1;
                 W.L[nl2++] = (unsigned char)va;
             }
             if (ao != bo) {
-                const bool strict = !ao ? W.fv[va] < -eps : W.fv[vb] < -eps;
+                const bool strict = !ao ? is_strict(va) : is_strict(vb);
                 int x = !ao ? va : vb;
                 if (strict) {
                     // the vertex on edge (va, vb), made once from the lower index
@@ -294,8 +309,10 @@ __device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, d
 
 // Persistent threads: each takes its next cell from a global counter as soon
 // as it has finished one, so a thread whose cell needed few cuts does not
-// wait for the slowest cell of its block.
-__global__ void __launch_bounds__(128) cells_kernel(const double *S, int64_t M, BucketGrid bg, const int64_t *boff,
+// wait for the slowest cell of its block. Eight blocks of 128 per SM (64
+// registers): the kernel waits on its local-memory polyhedra and gains more
+// from the extra warps than it loses to the few more spills.
+__global__ void __launch_bounds__(128, 8) cells_kernel(const double *S, int64_t M, BucketGrid bg, const int64_t *boff,
                                                     const int *bsites, double box0, double box1, double box2,
                                                     double box3, double box4, double box5, double eps, int *out_cnt,
                                                     int *out_nbr, double *out_vol, double *out_bbox, int *out_fail,
