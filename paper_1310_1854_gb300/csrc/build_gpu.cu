@@ -444,6 +444,8 @@ __global__ void __launch_bounds__(128, 8) cells_kernel(const double *S, int64_t 
             if (2.0 * rmax + 4.0 * eps < gap) break;
         }
         // faces of positive area -> neighbours; volume as pyramids from the site; bounding box
+        static_assert(kNE >= kCap, "the edge keys hold the neighbour list");
+        int *const ids = W.ekey;  // free once the cuts are done
         int cnt = 0;
         double vol = 0.0;
         double bb[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
@@ -466,8 +468,7 @@ __global__ void __launch_bounds__(128, 8) cells_kernel(const double *S, int64_t 
             const double area2 = sx * sx + sy * sy + sz * sz;
             if (area2 > 0.0) {
                 if (cnt >= kCap) { fail = 1; break; }
-                out_nbr[m * kCap + cnt] = P.fid[f];
-                cnt++;
+                ids[cnt++] = P.fid[f];
             }
         }
         for (int i = 0; i < P.nv; i++) {
@@ -478,10 +479,34 @@ __global__ void __launch_bounds__(128, 8) cells_kernel(const double *S, int64_t 
             bb[4] = fmax(bb[4], P.y[i]);
             bb[5] = fmax(bb[5], P.z[i]);
         }
-        out_cnt[m] = cnt;
+        // the list in ascending order without repeats (insertion sort: a few
+        // dozen ids), as the host's CSR holds it
+        for (int a = 1; a < cnt; a++) {
+            const int v = ids[a];
+            int b = a - 1;
+            while (b >= 0 && ids[b] > v) {
+                ids[b + 1] = ids[b];
+                b--;
+            }
+            ids[b + 1] = v;
+        }
+        int u = 0;
+        for (int a = 0; a < cnt; a++)
+            if (u == 0 || ids[a] != ids[u - 1]) ids[u++] = ids[a];
+        for (int a = 0; a < u; a++) out_nbr[m * kCap + a] = ids[a];
+        out_cnt[m] = u;
         out_vol[m] = vol;
         for (int c = 0; c < 6; c++) out_bbox[6 * m + c] = bb[c];
         out_fail[m] = fail;
+    }
+}
+
+// the cells' lists into one CSR array (offsets computed on the host)
+__global__ void gather_lists_kernel(const int *nbr, const int *cnt, const int64_t *off, int64_t M, int *idx) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < M; m += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = off[m];
+        const int c = cnt[m];
+        for (int a = 0; a < c; a++) idx[o + a] = nbr[m * kCap + a];
     }
 }
 
@@ -582,14 +607,43 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
                                    nbr, vol, bbox, fail, reinterpret_cast<unsigned long long *>(cursor), dSf, prefilter);
     count_launches(4);  // bucket count, fill, sort, cells (the scan counts its own)
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cells kernel");
-    std::vector<int> hcnt(M), hfail(M), hnbr((size_t)kCap * M);
+    std::vector<int> hcnt(M), hfail(M);
     out.vol.assign(M, 0.0);
     out.bbox.assign(6 * M, 0.0);
     if ((e = cudaMemcpy(hcnt.data(), cnt, sizeof(int) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
         (e = cudaMemcpy(hfail.data(), fail, sizeof(int) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
-        (e = cudaMemcpy(hnbr.data(), nbr, sizeof(int) * kCap * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
         (e = cudaMemcpy(out.vol.data(), vol, sizeof(double) * M, cudaMemcpyDeviceToHost)) != cudaSuccess ||
         (e = cudaMemcpy(out.bbox.data(), bbox, sizeof(double) * 6 * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bad(e, "download");
+    if (std::find(hfail.begin(), hfail.end(), 1) == hfail.end()) {
+        // every cell was built here: its list is sorted already, so only the
+        // CSR is gathered on the device and read back
+        out.off.assign(M + 1, 0);
+        for (int64_t m = 0; m < M; m++) out.off[m + 1] = out.off[m] + hcnt[m];
+        out.idx.resize(out.off[M]);
+        if (host_fallback_cells) *host_fallback_cells = 0;
+        int64_t *doff = nullptr;
+        int *didx = nullptr;
+        auto done = [&](cudaError_t ce, const char *what) {
+            if (doff) cudaFree(doff);
+            if (didx) cudaFree(didx);
+            return ce == cudaSuccess ? 0 : bad(ce, what);
+        };
+        if ((e = cudaMalloc(&doff, sizeof(int64_t) * (M + 1))) != cudaSuccess) return done(e, "alloc");
+        if ((e = cudaMalloc(&didx, sizeof(int) * std::max<int64_t>(1, out.off[M]))) != cudaSuccess)
+            return done(e, "alloc");
+        if ((e = cudaMemcpy(doff, out.off.data(), sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return done(e, "upload");
+        gather_lists_kernel<<<blocks, 256>>>(nbr, cnt, doff, M, didx);
+        count_launches(1);
+        if ((e = cudaMemcpy(out.idx.data(), didx, sizeof(int) * out.off[M], cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return done(e, "download");
+        const int rc = done(cudaSuccess, "");
+        cleanup();
+        return rc;
+    }
+    std::vector<int> hnbr((size_t)kCap * M);
+    if ((e = cudaMemcpy(hnbr.data(), nbr, sizeof(int) * kCap * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return bad(e, "download");
     cleanup();
     // each cell's list sorted and made unique in place (parallel over
