@@ -1008,6 +1008,38 @@ def test_grid_quality_in_a_spherical_domain():
     assert q["std"] == pytest.approx(float(d.std()), rel=1e-12)
 
 
+def test_gpu_cell_construction_host_fallback():
+    """A cell beyond the GPU builder's fixed capacities (a site with 80
+    neighbours on a sphere around it: more faces and vertices than one
+    thread's polyhedron holds) is rebuilt by the host builder, and the grid
+    still matches the host-built one."""
+    from paper_1310_1854_gb300 import VoronoiGrid
+    n = 80
+    k = np.arange(n) + 0.5
+    th = np.arccos(1.0 - 2.0 * k / n)
+    ph = np.pi * (1.0 + 5.0 ** 0.5) * k
+    shell = 0.5 * np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    rng = gen.rng_for(335)
+    far = rng.uniform(-1.0, 1.0, (3000, 3))
+    far = far[np.linalg.norm(far, axis=1) > 0.75][:300]
+    S = np.float32(np.concatenate([[[0.0, 0.0, 0.0]], shell, far])).astype(np.float64)
+    host = VoronoiGrid(S, gen.CUBE_BOX, host_only=True)
+    dev_ = VoronoiGrid(S, gen.CUBE_BOX, gpu_build=True)
+    assert dev_.info()["host_fallback_cells"] >= 1
+    ho, hi = host.neighbors()
+    do, di = dev_.neighbors()
+    assert set(di[do[0]:do[1]].tolist()) == set(hi[ho[0]:ho[1]].tolist())
+    assert do[1] - do[0] == n
+    for m in range(len(S)):
+        a, b = set(hi[ho[m]:ho[m + 1]].tolist()), set(di[do[m]:do[m + 1]].tolist())
+        assert len(a ^ b) <= 2, m   # at most planes that only touch the cell (R7)
+    hv, hb = host.cells()
+    dv, db = dev_.cells()
+    np.testing.assert_allclose(dv, hv, rtol=1e-10)
+    np.testing.assert_allclose(db, hb, rtol=0, atol=1e-12 * np.linalg.norm(gen.CUBE_BOX[3:] - gen.CUBE_BOX[:3]))
+    np.testing.assert_allclose(dv.sum(), 8.0, rtol=1e-12)
+
+
 @pytest.mark.parametrize("kind", ["uniform", "disk", "clumpy", "lattice"])
 def test_gpu_cell_construction_matches_host(kind):
     from paper_1310_1854_gb300 import VoronoiGrid
