@@ -544,10 +544,11 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
     float4 *dSf = nullptr;
     int prefilter = 1;
     int *bidx = nullptr, *bsites = nullptr, *cnt = nullptr, *nbr = nullptr, *fail = nullptr;
-    int64_t *boff = nullptr, *cursor = nullptr, *tmp = nullptr;
+    int64_t *boff = nullptr, *cursor = nullptr, *tmp = nullptr, *doff = nullptr;
+    int *didx = nullptr;
     double *vol = nullptr, *bbox = nullptr;
     auto cleanup = [&]() {
-        void *ptrs[] = {dS, dE, dSf, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox};
+        void *ptrs[] = {dS, dE, dSf, bidx, bsites, cnt, nbr, fail, boff, cursor, tmp, vol, bbox, doff, didx};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     };
@@ -622,25 +623,17 @@ int build_cells_gpu(const double *S, int64_t M, const double *box, int threads, 
         for (int64_t m = 0; m < M; m++) out.off[m + 1] = out.off[m] + hcnt[m];
         out.idx.resize(out.off[M]);
         if (host_fallback_cells) *host_fallback_cells = 0;
-        int64_t *doff = nullptr;
-        int *didx = nullptr;
-        auto done = [&](cudaError_t ce, const char *what) {
-            if (doff) cudaFree(doff);
-            if (didx) cudaFree(didx);
-            return ce == cudaSuccess ? 0 : bad(ce, what);
-        };
-        if ((e = cudaMalloc(&doff, sizeof(int64_t) * (M + 1))) != cudaSuccess) return done(e, "alloc");
+        if ((e = cudaMalloc(&doff, sizeof(int64_t) * (M + 1))) != cudaSuccess) return bad(e, "alloc");
         if ((e = cudaMalloc(&didx, sizeof(int) * std::max<int64_t>(1, out.off[M]))) != cudaSuccess)
-            return done(e, "alloc");
+            return bad(e, "alloc");
         if ((e = cudaMemcpy(doff, out.off.data(), sizeof(int64_t) * (M + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
-            return done(e, "upload");
+            return bad(e, "upload");
         gather_lists_kernel<<<blocks, 256>>>(nbr, cnt, doff, M, didx);
         count_launches(1);
         if ((e = cudaMemcpy(out.idx.data(), didx, sizeof(int) * out.off[M], cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return done(e, "download");
-        const int rc = done(cudaSuccess, "");
+            return bad(e, "download");
         cleanup();
-        return rc;
+        return 0;
     }
     std::vector<int> hnbr((size_t)kCap * M);
     if ((e = cudaMemcpy(hnbr.data(), nbr, sizeof(int) * kCap * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
