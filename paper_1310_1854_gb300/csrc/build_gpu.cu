@@ -170,7 +170,8 @@ __device__ int poly_cut(DPoly &P, Scratch &W, double nx, double ny, double nz, d
     }
     // each vertex classified once: above the plane (fv > eps) and strictly
     // below it (fv < -eps) as bits of two 128-bit masks held in registers,
-    // so that the face walk below reads neither fv nor the float64 pipe
+    // so that the face walk below tests the masks and reads fv only at the
+    // two ends of an edge the plane cuts
     static_assert(kNV <= 128, "vertex masks hold 128 bits");
     unsigned long long out0 = 0ull, out1 = 0ull, str0 = 0ull, str1 = 0ull;
     for (int i = 0; i < P.nv; i++) {
