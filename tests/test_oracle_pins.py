@@ -499,6 +499,30 @@ def test_interaction_hand_worked():
     assert not amb.any()
 
 
+def test_interaction_through_empty_cells():
+    """A cell of zero density adds length but no optical depth, and takes
+    nothing from the package. Three sites at x = 1, 3, 5 in [0,6] x [0,2]^2
+    with rho 0, 3, 0 and kappa 2; a ray from (0.5, 1, 1) along +x crosses
+    1.5 of cell 0, 2 of cell 1 (tau 12) and 2 of cell 2. tau_int = 6 is
+    reached 1 into cell 1 (s = 2.5); tau_int = 20 is never reached, and
+    the ray leaves after 5.5 having lost 1 - e^-12, all in cell 1."""
+    S = np.array([[1.0, 1, 1], [3.0, 1, 1], [5.0, 1, 1]])
+    box = np.array([0.0, 0, 0, 6, 2, 2])
+    rho = np.array([0.0, 3.0, 0.0])
+    c, off, idx = _full(S, box)
+    tr = oracle.trace(S, box, rho, np.array([[0.5, 1, 1]] * 2), np.array([[1.0, 0, 0]] * 2), off=off, idx=idx,
+                      kappa=2.0)
+    np.testing.assert_allclose(tr.tau, [12.0, 12.0], rtol=1e-15)
+    cell, s, ab, amb = oracle.interact(tr, rho, [6.0, 20.0], kappa=2.0)
+    assert list(cell) == [1, -1]
+    np.testing.assert_allclose(s, [2.5, 5.5], rtol=1e-14)
+    np.testing.assert_allclose(ab, [0.0, (1 - np.exp(-6)) + (1 - np.exp(-12)), 0.0], rtol=1e-14, atol=0)
+    assert not amb.any()
+    grad = oracle.tau_grad(tr, 3, [1.0, 1.0], kappa=2.0)
+    # dtau/drho_c = kappa l_c, whatever rho_c is
+    np.testing.assert_allclose(grad, [2 * 2 * 1.5, 2 * 2 * 2.0, 2 * 2 * 2.0], rtol=1e-14)
+
+
 def test_interaction_uniform_closed_form_and_conservation(grid300):
     g, c, off, idx = grid300
     rays = gen.uniform_rays(400, 61)
