@@ -94,6 +94,10 @@ PY_MUTANTS = [
     ("loss derivative without the chain factor", "-2.0 * (e - t) * e", "-2.0 * (e - t)"),
     ("loss derivative with the wrong sign", "-2.0 * (e - t) * e", "2.0 * (e - t) * e"),
     ("CSR offsets shifted by one", "np.cumsum(deg, out=off[1:])", "np.cumsum(deg, out=off[:-1])"),
+    ("a ray's segments cut one short", "return self.seg_cell[i, :n], self.seg_len[i, :n]",
+     "return self.seg_cell[i, :n - 1], self.seg_len[i, :n - 1]"),
+    ("gradient summed over one segment too many", "mask = np.arange(cap)[None, :] < tr.nseg[:, None]",
+     "mask = np.arange(cap)[None, :] <= tr.nseg[:, None]"),
 ]
 
 
